@@ -1,0 +1,249 @@
+/*
+ * gofd.h -- C ABI of the GB300 grid-overlay finite-difference (GoFD) library.
+ *
+ * The library discretises the homogeneous Dirichlet problem for the
+ * fractional Laplacian,
+ *     (-Delta)^s u = f in Omega,  u = 0 outside Omega,   s = alpha/2 in (0,1)
+ * (Huang & Shen, arXiv 2307.14437, Section 1, eq. (FL-1)) on an unstructured
+ * simplicial mesh T_h overlaid by a uniform grid T_FD (Section 3.1).  Its hot
+ * path is the stiffness product of the SPD system (GoFD-2),
+ *     y = S u,   S = (I_h^FD)^T A_FD I_h^FD       (Section 3.2, eq. (GoFD-2))
+ * where I_h^FD is piecewise-linear interpolation from mesh vertices to grid
+ * nodes (eq. (IhFD-1)) and A_FD is the multilevel-Toeplitz FD matrix of
+ * eqs. (T-1), (A-1), (AFD-1), applied by zero-padded circulant FFT
+ * convolution (Section 2.2, eq. (AU-1)).
+ *
+ * Conventions shared by every call
+ *  - Every call returns a gofd_status; nothing is thrown across the ABI.
+ *    gofd_last_error() gives a message for the last failure on a handle
+ *    (or, with a NULL handle, for the last failed gofd_build of the thread).
+ *  - Host inputs are copied; the caller keeps ownership of everything it
+ *    passes.  A gofd_problem owns all of its device memory and frees it in
+ *    gofd_destroy().  A handle is not thread safe: serialise calls on it.
+ *  - Device vectors are caller-owned device pointers, used in stream order on
+ *    the caller's stream (`stream` is a cudaStream_t cast to void*; NULL is
+ *    the legacy default stream).  The library allocates nothing per call on
+ *    the device except where a function says so.
+ *  - Vertex vectors have N_v entries in the caller's vertex order.  Boundary
+ *    vertices (vertices of facets that belong to exactly one simplex) carry
+ *    the Dirichlet value 0: their input entries are ignored and their output
+ *    entries are written as 0 (Section 3.2, remark on interior unknowns).
+ *  - Grid vectors have n_0*n_1*...*n_{d-1} entries, axis 0 fastest; node k has
+ *    coordinates x_k = box_lo + k*h (one rounded product, one rounded sum).
+ *  - The library runs only on a CUDA GPU of compute capability 10.3 (sm_103a).
+ *    There is no CPU fallback: without such a GPU every call that needs the
+ *    device returns GOFD_E_CUDA.
+ */
+#ifndef GOFD_H
+#define GOFD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gofd_problem gofd_problem;
+
+typedef enum {
+    GOFD_OK = 0,
+    GOFD_E_ARG = 1,                 /* invalid argument (NULL pointer, bad size, bad enum)      */
+    GOFD_E_DEGENERATE_SIMPLEX = 2,  /* a simplex has zero volume (exact orientation test)        */
+    GOFD_E_OUTSIDE_BOX = 3,         /* a mesh vertex lies outside [box_lo, box_hi]                */
+    GOFD_E_GRID = 4,                /* (hi-lo)/h is not an integer, or the grid is too large      */
+    GOFD_E_TOO_FEW_GRID_NODES = 5,  /* fewer grid nodes than mesh vertices (Remark 3.2)           */
+    GOFD_E_ZERO_COLSUM = 6,         /* an interior column sum D_h,j is 0 (Theorem 3.1 hypothesis) */
+    GOFD_E_PRECOND = 7,             /* the incomplete Cholesky factorisation broke down           */
+    GOFD_E_NOT_CONVERGED = 8,       /* the solver hit maxit before reaching tol                   */
+    GOFD_E_TIMEOUT = 9,             /* a bounded device-side wait ran out                          */
+    GOFD_E_CUDA = 10,               /* a CUDA runtime error (message in gofd_last_error)          */
+    GOFD_E_NOMEM = 11               /* device or host allocation failed                            */
+} gofd_status;
+
+typedef enum { GOFD_FP64 = 0, GOFD_FP32 = 1 } gofd_precision;
+
+typedef enum {
+    GOFD_SOLVE_FP64 = 0,   /* PCG with FP64 operator, vectors and scalars                      */
+    GOFD_SOLVE_MIXED = 1   /* FP64 residual refinement around an FP32-operator PCG (FP64 dots)  */
+} gofd_solve_mode;
+
+typedef enum {
+    GOFD_OP_STIFFNESS = 0, /* y = S u                       (GoFD-2)                          */
+    GOFD_OP_FRACLAP = 1    /* y = h^{-2s} D_h^{-1} S u      (Ah-1): the GoFD fractional Laplacian */
+} gofd_op;
+
+typedef enum {
+    GOFD_RHS_GRID = 0,     /* f given on the grid (n^d values): b = h^{2s} I^T (f on located nodes), (GoFD-1)/(GoFD-2) */
+    GOFD_RHS_VERTEX = 1    /* f given on the vertices (N_v values): b = h^{2s} D_h f, (GoFD-3)                    */
+} gofd_rhs;
+
+typedef struct {
+    int precond;               /* 0: none; 5 or 9 (2D), 7 or 27 (3D), 3 (1D): IC(ic_level) of I^T A_FD^(k) I (Ah-4) */
+    int ic_level;              /* level of fill of the incomplete Cholesky factor (paper: 1)                        */
+    int64_t filon_M;           /* finest Filon panel count M; 0 = paper default (2^14 in 1D/2D, 2^11 in 3D), raised
+                                  so that the coarsest Richardson level keeps M/2^(levels-1) >= n                      */
+    int richardson_levels;     /* Filon levels M, M/2, ...; 0 = 4                                                     */
+    uint64_t wait_budget_cycles; /* bound on every device-side spin wait (clock64 cycles); 0 = 2e9                    */
+    double inner_tol;          /* mixed mode: relative reduction of each inner FP32 PCG; 0 = 1e-4                   */
+    int check_every;           /* iterations between host convergence checks; 0 = 8                                  */
+} gofd_options;
+
+typedef struct {
+    int outer_iters;           /* refinement steps (mixed) or 1 (fp64)                                   */
+    int inner_iters;           /* total PCG iterations                                                   */
+    double rel_res_fp64;       /* final ||b - S u||_2 / ||b||_2 with the FP64 operator                   */
+    double ic_shift;           /* diagonal shift used by the IC factorisation (0 if none was needed)     */
+    double a_h;                /* minimum element height                                                 */
+    double min_colsum;         /* min over interior vertices of D_h,j                                    */
+    int h_within_strict_bound; /* h <= a_h / ((d+1) sqrt(d))  (eq. (hFD-1))                               */
+    int h_within_practical_bound; /* h <= a_h  (Remark 3.5)                                              */
+    double t_setup_ms;         /* gofd_build wall time                                                   */
+    double t_solve_ms;         /* this solve's wall time                                                 */
+} gofd_solve_info;
+
+typedef struct {
+    int d;                     /* dimension 1..3                                         */
+    int n[3];                  /* grid nodes per axis                                    */
+    int P;                     /* circulant length per axis (power of two >= 2n-2)      */
+    int64_t n_v, n_e;          /* mesh vertices, simplices                               */
+    int64_t n_interior;        /* interior vertices (unknowns)                           */
+    int64_t n_grid;            /* grid nodes                                             */
+    int64_t n_loc;             /* located grid nodes (rows of the ELL form of I_h^FD)     */
+    int64_t nnz_t;             /* stored entries of I^T over interior vertices           */
+    int64_t n_runs;            /* runs of consecutive located nodes along axis 0         */
+    int64_t filon_M;           /* finest Filon M used                                    */
+    int richardson_levels;
+    double alpha, s, h;
+    double a_h, min_colsum;
+    int64_t precond_nnz;       /* stored entries of the IC factor (0 without preconditioner) */
+    double ic_shift;
+    double t_setup_ms;
+} gofd_info;
+
+/*
+ * gofd_build -- set up the discrete problem (Sections 2.3, 3.1, 3.3).
+ *   d            dimension, 1..3
+ *   vertices     host, N_v*d doubles, row-major (vertex j at vertices[j*d .. j*d+d-1])
+ *   simplices    host, N_e*(d+1) int32, 0-based vertex indices; either orientation
+ *   alpha        = 2s, 0 < alpha < 2 (alpha = 2 is accepted: the standard Laplacian)
+ *   h            overlay spacing h_FD > 0
+ *   box_lo/hi    host, d doubles each; (hi_i-lo_i)/h must be an integer (1e-9 rel.)
+ *   opt          options or NULL for defaults
+ *   out          receives the new handle (NULL on failure)
+ * Work done on the device: exact point location of every grid node (lowest
+ * element index wins on shared facets), the ELL form of I_h^FD, boundary
+ * detection and interior numbering, the transpose I^T, column sums D_h,
+ * element heights and a_h, the FD coefficients T by Filon quadrature with
+ * Richardson extrapolation (Section 2.3), the circulant symbol (Section 2.2),
+ * and, if requested, the IC preconditioner (Section 3.3).
+ * Errors: GOFD_E_ARG, _DEGENERATE_SIMPLEX, _OUTSIDE_BOX, _GRID,
+ * _TOO_FEW_GRID_NODES, _ZERO_COLSUM, _PRECOND, _CUDA, _NOMEM.
+ */
+gofd_status gofd_build(int d, const double* vertices, int64_t n_v,
+                       const int32_t* simplices, int64_t n_e,
+                       double alpha, double h,
+                       const double* box_lo, const double* box_hi,
+                       const gofd_options* opt, gofd_problem** out);
+
+/*
+ * gofd_apply -- y = S u (GOFD_OP_STIFFNESS, eq. (GoFD-2)) or
+ * y = h^{-2s} D_h^{-1} S u (GOFD_OP_FRACLAP, eq. (Ah-1)).
+ *   u_dev, y_dev  device, N_v values of double (GOFD_FP64) or float (GOFD_FP32);
+ *                 they must not overlap.  The precision selects the arithmetic of
+ *                 the gather, FFT convolution and scatter.
+ * Boundary entries of u are ignored; boundary entries of y are set to 0.
+ */
+gofd_status gofd_apply(gofd_problem* p, gofd_op op, gofd_precision prec,
+                       const void* u_dev, void* y_dev, void* stream);
+
+/*
+ * gofd_apply_host -- gofd_apply on host buffers (N_v values each): copies u to
+ * the device, applies, copies y back, and synchronises the stream.  The first
+ * call allocates two N_v device staging vectors that the handle keeps.
+ */
+gofd_status gofd_apply_host(gofd_problem* p, gofd_op op, gofd_precision prec,
+                            const void* u_host, void* y_host, void* stream);
+
+/*
+ * gofd_apply_interior -- the operator on interior-compacted device vectors:
+ * x_dev holds N_int+1 values (interior unknowns in vertex order, then one
+ * slot that must be 0), y_dev receives N_int values of S x.  This is the
+ * product the solver iterates; it does no compaction.
+ */
+gofd_status gofd_apply_interior(gofd_problem* p, gofd_precision prec,
+                                const void* x_dev, void* y_dev, void* stream);
+
+/*
+ * gofd_apply_interior_profiled -- gofd_apply_interior with a CUDA event
+ * recorded on `stream` after each kernel of the product; on return (the
+ * stream is synchronised) stage_ms[i] holds the time of stage i in ms and
+ * stage_names[i] (if stage_names is not NULL) a static name; *n_stages is the
+ * number of stages written (at most cap).  For measurement only.
+ */
+gofd_status gofd_apply_interior_profiled(gofd_problem* p, gofd_precision prec, const void* x_dev,
+                                         void* y_dev, void* stream, float* stage_ms,
+                                         const char** stage_names, int cap, int* n_stages);
+
+/*
+ * gofd_solve -- solve (GoFD-2) S u = b for the interior unknowns.
+ *   mode    GOFD_SOLVE_FP64 or GOFD_SOLVE_MIXED
+ *   rhs     GOFD_RHS_GRID: f_dev holds n_grid doubles (values off the mesh are ignored);
+ *           GOFD_RHS_VERTEX: f_dev holds N_v doubles
+ *   tol     stop when ||b - S u||_2 <= tol ||b||_2 (FP64 operator)
+ *   maxit   bound on the total number of PCG iterations
+ *   u_dev   device, N_v doubles: initial guess on entry (ignored if init_zero),
+ *           the solution on exit with boundary entries 0
+ *   info    optional (may be NULL)
+ * The stream is synchronised at every convergence check.  Returns
+ * GOFD_E_NOT_CONVERGED (with u holding the last iterate) if maxit is reached.
+ */
+gofd_status gofd_solve(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs,
+                       const double* f_dev, double tol, int maxit, int init_zero,
+                       double* u_dev, gofd_solve_info* info, void* stream);
+
+/* gofd_get_info -- sizes and set-up results (host struct). */
+gofd_status gofd_get_info(const gofd_problem* p, gofd_info* info);
+
+/*
+ * gofd_export_transfer -- the canonical ELL form of I_h^FD, copied to host:
+ *   owner    n_grid int32: owner simplex of each grid node, or -1
+ *   ell_idx  (d+1)*n_loc int32, slot-major: slot a of located node r (rows in
+ *            increasing grid index) is ell_idx[a*n_loc + r] = simplices[owner][a]
+ *   ell_w    (d+1)*n_loc doubles, same layout: phi of that vertex at the node
+ * Any output pointer may be NULL.
+ */
+gofd_status gofd_export_transfer(const gofd_problem* p, int32_t* owner,
+                                 int32_t* ell_idx, double* ell_w);
+
+/*
+ * gofd_export_vertex_data -- per-vertex set-up results, copied to host:
+ *   interior_index  N_v int32: index among the unknowns, or -1 on the boundary
+ *   colsum          N_v doubles: D_h,j for interior vertices (0 on the boundary)
+ */
+gofd_status gofd_export_vertex_data(const gofd_problem* p, int32_t* interior_index,
+                                    double* colsum);
+
+/* gofd_get_coefficients -- T_p for p in [0,n)^d (FP64, axis 0 fastest), to host. */
+gofd_status gofd_get_coefficients(const gofd_problem* p, double* T);
+
+/* gofd_get_symbol -- the real circulant symbol on [0,P/2]^d (FP64, unscaled), to host. */
+gofd_status gofd_get_symbol(const gofd_problem* p, double* lambda);
+
+/*
+ * gofd_afd_apply -- w = A_FD v on the grid (device, n_grid values each, no
+ * overlap), by the library's FFT convolution (Section 2.2).
+ */
+gofd_status gofd_afd_apply(gofd_problem* p, gofd_precision prec,
+                           const void* v_dev, void* w_dev, void* stream);
+
+/* gofd_destroy -- free the handle and all of its device memory (NULL is a no-op). */
+void gofd_destroy(gofd_problem* p);
+
+/* gofd_last_error -- message of the last failure (never NULL). */
+const char* gofd_last_error(const gofd_problem* p);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GOFD_H */

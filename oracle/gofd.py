@@ -197,6 +197,71 @@ def locate(verts, simp, box_lo, h, n, nodes=None, chunk=256):
     return owner
 
 
+def locate_pruned(verts, simp, box_lo, h, n):
+    """locate() for all nodes, testing each node only against the simplices
+    whose bounding box contains it (a node outside a simplex's bounding box is
+    outside the simplex, so the owner is unchanged).  Same exact predicate and
+    lowest-index tie rule as locate(); for full-size meshes.
+    """
+    verts = np.asarray(verts, dtype=np.float64)
+    simp = np.asarray(simp, dtype=np.int64)
+    d = verts.shape[1]
+    osign = element_orientations(verts, simp)
+    V = verts[simp]
+    bmin = V.min(axis=1)
+    bmax = V.max(axis=1)
+    axes = [grid_axis_coords(box_lo[a], h, n[a]) for a in range(d)]
+    # candidate index ranges per axis (exact coordinate comparison)
+    lo_k = [np.searchsorted(axes[a], bmin[:, a], side="left") for a in range(d)]
+    hi_k = [np.searchsorted(axes[a], bmax[:, a], side="right") for a in range(d)]
+    counts = np.ones(len(simp), dtype=np.int64)
+    for a in range(d):
+        counts *= np.maximum(0, hi_k[a] - lo_k[a])
+    elem = np.repeat(np.arange(len(simp)), counts)
+    off = np.arange(counts.sum()) - np.repeat(np.cumsum(counts) - counts, counts)
+    node = np.zeros(len(elem), dtype=np.int64)
+    stride = 1
+    rem = off.copy()
+    for a in range(d):
+        ext = np.maximum(0, hi_k[a] - lo_k[a])[elem]
+        k = lo_k[a][elem] + rem % ext
+        rem //= ext
+        node += k * stride
+        stride *= n[a]
+    owner = np.full(int(np.prod(n)), -1, dtype=np.int64)
+    chunk = 1 << 20
+    for c0 in range(0, len(elem), chunk):
+        e = elem[c0:c0 + chunk]
+        k = node[c0:c0 + chunk]
+        X = grid_node_coords(box_lo, h, n, k)
+        inside = np.ones(len(e), dtype=bool)
+        unsure = np.zeros(len(e), dtype=bool)
+        for i in range(d + 1):
+            pts = V[e].copy()
+            pts[:, i, :] = X
+            det, bnd = _orient_float_with_bound(pts)
+            sure = np.abs(det) > bnd
+            inside &= ~(sure & (det * osign[e] < 0))
+            unsure |= ~sure
+        for j in np.nonzero(inside & unsure)[0]:
+            for i in range(d + 1):
+                pts = V[e[j]].copy()
+                pts[i] = X[j]
+                if orient_exact(pts) * osign[e[j]] < 0:
+                    inside[j] = False
+                    break
+        ki = k[inside]
+        ei = e[inside]
+        order = np.lexsort((ei, ki))
+        ki, ei = ki[order], ei[order]
+        first = np.ones(len(ki), dtype=bool)
+        first[1:] = ki[1:] != ki[:-1]
+        cur = owner[ki[first]]
+        cand = ei[first]
+        owner[ki[first]] = np.where((cur < 0) | (cand < cur), cand, cur)
+    return owner
+
+
 def barycentric_exact(verts, simp_e, x):
     """phi_i(x) = D_i / orient(K), computed exactly then rounded to double.
 
@@ -522,8 +587,11 @@ class Problem:
 
 
 def build(d, verts, simp, alpha, h, box_lo, box_hi, M=None, levels=4, exact_weights=True,
-          coeff_T=None) -> Problem:
-    """Set up the oracle's GoFD problem: grid, I_h^FD, D_h, a_h, T, symbol."""
+          coeff_T=None, pruned=False) -> Problem:
+    """Set up the oracle's GoFD problem: grid, I_h^FD, D_h, a_h, T, symbol.
+
+    pruned=True locates with locate_pruned() (same owners, for large meshes).
+    """
     verts = np.asarray(verts, dtype=np.float64)
     simp = np.asarray(simp, dtype=np.int64)
     if not (0.0 < alpha <= 2.0):
@@ -536,7 +604,7 @@ def build(d, verts, simp, alpha, h, box_lo, box_hi, M=None, levels=4, exact_weig
         raise OracleError("the oracle supports cubic grids only")
     if np.any(verts < box_lo) or np.any(verts > box_hi):
         raise OracleError("mesh vertex outside the box")
-    owner = locate(verts, simp, box_lo, h, n)
+    owner = locate_pruned(verts, simp, box_lo, h, n) if pruned else locate(verts, simp, box_lo, h, n)
     nodes, idx, w = ell_layout(verts, simp, box_lo, h, n, owner, exact=exact_weights)
     I = transfer_matrix(nodes, idx, w, int(np.prod(n)), len(verts))
     bnd = boundary_vertices(simp, len(verts))

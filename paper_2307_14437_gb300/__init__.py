@@ -1,0 +1,8 @@
+"""GB300-native grid-overlay FD method (GoFD) for the fractional Laplacian.
+
+The compute path is the CUDA library ``libgofd.so`` (C ABI in ``include/gofd.h``);
+this package is its thin binding.  Build it with ``build_native.build()``.
+"""
+from .gofd import GofdError, Problem  # noqa: F401
+
+__all__ = ["Problem", "GofdError"]

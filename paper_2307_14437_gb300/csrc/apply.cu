@@ -1,0 +1,653 @@
+// The stiffness product y = I^T A_FD I x (GoFD-2) on interior-compacted vectors.
+//
+//   gather   v = I x on the grid, fused into the first FFT pass (ELL runs per line)
+//   A_FD v   zero-padded circulant convolution (Section 2.2, (AU-1)):
+//            real FFT along axis 0 (only the n nonzero lines), complex FFTs along
+//            the other axes (only n nonzero inputs; outputs kept on the needed
+//            range), multiplication by the real even symbol, inverse transforms
+//            that keep the n^d corner
+//   scatter  y = I^T w through the interior-vertex CSR, fixed summation order
+//
+// The FFTs are Stockham passes of radix 16 (and one of radix 2/4/8) computed in
+// registers, with the exchange between passes through padded shared memory.
+// Every transform is unnormalised; the symbol carries the 1/P^d factor.
+#include <algorithm>
+
+#include "gofd_internal.cuh"
+
+namespace gofd {
+
+// ---------------------------------------------------------------------------
+// complex arithmetic
+// ---------------------------------------------------------------------------
+template <class R> struct Cplx;
+template <> struct Cplx<float> { using T = float2; };
+template <> struct Cplx<double> { using T = double2; };
+
+template <class C> __device__ __forceinline__ C cmk(double x, double y);
+template <> __device__ __forceinline__ float2 cmk<float2>(double x, double y) { return make_float2((float)x, (float)y); }
+template <> __device__ __forceinline__ double2 cmk<double2>(double x, double y) { return make_double2(x, y); }
+
+template <class C> __device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <class C> __device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+template <class C> __device__ __forceinline__ C cmul(C a, C b) {
+    C r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+// a * conj(b)
+template <class C> __device__ __forceinline__ C cmulc(C a, C b) {
+    C r;
+    r.x = a.x * b.x + a.y * b.y;
+    r.y = a.y * b.x - a.x * b.y;
+    return r;
+}
+template <class C> __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
+
+// shared-memory index with one pad slot per 16 complex entries (bank spread)
+__device__ __forceinline__ int spad(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int spad_len(int n) { return n + (n >> 4) + 1; }
+
+// cos / sin of 2 pi k / 16
+__host__ __device__ constexpr double cos16(int k) {
+    switch (k & 15) {
+        case 0: return 1.0;
+        case 1: return 0.92387953251128675613;
+        case 2: return 0.70710678118654752440;
+        case 3: return 0.38268343236508977173;
+        case 4: return 0.0;
+        case 5: return -0.38268343236508977173;
+        case 6: return -0.70710678118654752440;
+        case 7: return -0.92387953251128675613;
+        case 8: return -1.0;
+        case 9: return -0.92387953251128675613;
+        case 10: return -0.70710678118654752440;
+        case 11: return -0.38268343236508977173;
+        case 12: return 0.0;
+        case 13: return 0.38268343236508977173;
+        case 14: return 0.70710678118654752440;
+        default: return 0.92387953251128675613;
+    }
+}
+__host__ __device__ constexpr double sin16(int k) { return cos16(k - 4); }
+
+// multiply by exp(-+ 2 pi i j / 16) (sign by INV); j is a compile-time constant after unrolling
+template <bool INV, class C> __device__ __forceinline__ C twc16(C a, int j) {
+    j &= 15;
+    if (j == 0) return a;
+    if (j == 4) {  // -i (forward) or +i (inverse)
+        C r;
+        if (!INV) { r.x = a.y; r.y = -a.x; } else { r.x = -a.y; r.y = a.x; }
+        return r;
+    }
+    if (j == 8) { a.x = -a.x; a.y = -a.y; return a; }
+    if (j == 12) {
+        C r;
+        if (!INV) { r.x = -a.y; r.y = a.x; } else { r.x = a.y; r.y = -a.x; }
+        return r;
+    }
+    double c = cos16(j), s = INV ? sin16(j) : -sin16(j);
+    return cmul(a, cmk<C>(c, s));
+}
+
+__host__ __device__ constexpr int bitrev(int x, int bits) {
+    int r = 0;
+    for (int i = 0; i < bits; ++i) r |= ((x >> i) & 1) << (bits - 1 - i);
+    return r;
+}
+
+// In-register DFT of length R (power of two <= 16), natural order in and out:
+// v[k] <- sum_r v[r] exp(-+2 pi i r k / R).  Radix-2 decimation in frequency,
+// then a compile-time bit-reversal permutation.
+template <int R, bool INV, class C> __device__ __forceinline__ void dft_reg(C* v) {
+    constexpr int LOG = (R == 2) ? 1 : (R == 4) ? 2 : (R == 8) ? 3 : 4;
+#pragma unroll
+    for (int st = 0; st < LOG; ++st) {
+        const int span = R >> (st + 1);
+#pragma unroll
+        for (int blk = 0; blk < R; blk += 2 * span) {
+#pragma unroll
+            for (int j = 0; j < span; ++j) {
+                C a = v[blk + j], b = v[blk + j + span];
+                v[blk + j] = cadd(a, b);
+                // twiddle exp(-2 pi i j / (2 span)) = index j * 16 / (2 span) of the 16-table
+                v[blk + j + span] = twc16<INV>(csub(a, b), j * (16 / (2 * span)));
+            }
+        }
+    }
+    C t[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) t[k] = v[bitrev(k, LOG)];
+#pragma unroll
+    for (int k = 0; k < R; ++k) v[k] = t[k];
+}
+
+// ---------------------------------------------------------------------------
+// one line FFT of length N (power of two >= 16) in padded shared memory,
+// computed by nthr = N/16 threads (thread index t of the line's group).
+// Stockham autosort: pass with radix R reads x[b + r N/R], applies twiddles
+// exp(-+2 pi i (b mod Ns) r / (Ns R)), a radix-R DFT, and writes
+// y[(b/Ns) Ns R + b mod Ns + r Ns].  The twiddle table holds exp(-2 pi i m / P)
+// for m < P; line length N = P / twstride.
+// ---------------------------------------------------------------------------
+constexpr int FFT_E = 16;
+
+template <int R, bool INV, class C>
+__device__ __forceinline__ void stockham_pass(C* buf, int N, int Ns, int t, int nthr, const C* __restrict__ tw,
+                                              int twstride, C (&v)[FFT_E]) {
+    constexpr int Q = FFT_E / R;
+    const int stride_in = N / R;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int b = t + q * nthr;
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[q * R + r] = buf[spad(b + r * stride_in)];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int b = t + q * nthr;
+        const int k = b % Ns;
+        const int step = (N / (Ns * R)) * twstride;
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+            if (k != 0) {
+                C w = __ldg(&tw[k * r * step]);
+                if (INV) w.y = -w.y;
+                v[q * R + r] = cmul(v[q * R + r], w);
+            }
+        }
+        dft_reg<R, INV>(v + q * R);
+        const int base = (b / Ns) * Ns * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[spad(base + r * Ns)] = v[q * R + r];
+    }
+    __syncthreads();
+}
+
+template <bool INV, class C>
+__device__ __forceinline__ void line_fft(C* buf, const LinePlan& plan, int t, const C* __restrict__ tw,
+                                         int twstride) {
+    C v[FFT_E];
+    int Ns = 1;
+    for (int ps = 0; ps < plan.npass; ++ps) {
+        const int R = plan.radix[ps];
+        if (R == 16) stockham_pass<16, INV>(buf, plan.N, Ns, t, plan.nthr, tw, twstride, v);
+        else if (R == 8) stockham_pass<8, INV>(buf, plan.N, Ns, t, plan.nthr, tw, twstride, v);
+        else if (R == 4) stockham_pass<4, INV>(buf, plan.N, Ns, t, plan.nthr, tw, twstride, v);
+        else stockham_pass<2, INV>(buf, plan.N, Ns, t, plan.nthr, tw, twstride, v);
+        Ns *= R;
+    }
+}
+
+LinePlan make_line_plan(int N) {
+    LinePlan p;
+    p.N = N;
+    p.nthr = N / FFT_E;
+    int rem = N;
+    while (rem >= 16) {
+        p.radix[p.npass++] = 16;
+        rem /= 16;
+    }
+    if (rem > 1) p.radix[p.npass++] = rem;
+    return p;
+}
+
+// ---------------------------------------------------------------------------
+// kernel 1: gather + real FFT along axis 0
+// ---------------------------------------------------------------------------
+template <class Real, int DP1>
+__global__ void __launch_bounds__(512) row_forward_kernel(const Real* __restrict__ x, const int32_t* __restrict__ iidx,
+                                   const Real* __restrict__ w, int64_t nloc,
+                                   const int32_t* __restrict__ run_ptr, const int32_t* __restrict__ run_k0,
+                                   const int32_t* __restrict__ run_len, const int32_t* __restrict__ run_e0,
+                                   int64_t nlines, LinePlan plan, const typename Cplx<Real>::T* __restrict__ tw,
+                                   typename Cplx<Real>::T* __restrict__ spec, int pitch, int gather_from_grid,
+                                   const Real* __restrict__ vgrid, int n0) {
+    using C = typename Cplx<Real>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* sm = reinterpret_cast<C*>(smem_raw);
+    const int N = plan.N;  // P/2
+    const int nthr = plan.nthr;
+    const int g = threadIdx.x / nthr, t = threadIdx.x % nthr;
+    const int64_t line = (int64_t)blockIdx.x * (blockDim.x / nthr) + g;
+    const bool active = line < nlines;
+    C* buf = sm + g * spad_len(N);
+    for (int i = t; i < spad_len(N); i += nthr) buf[i] = cmk<C>(0.0, 0.0);
+    __syncthreads();
+    if (active) {
+        Real* re = reinterpret_cast<Real*>(buf);
+        if (gather_from_grid) {
+            for (int k = t; k < n0; k += nthr) re[2 * spad(k >> 1) + (k & 1)] = vgrid[line * n0 + k];
+        } else {
+            const int r1 = run_ptr[line + 1];
+            for (int r = run_ptr[line]; r < r1; ++r) {
+                const int k0 = run_k0[r], len = run_len[r], e0 = run_e0[r];
+                for (int q = t; q < len; q += nthr) {
+                    const int64_t e = e0 + q;
+                    Real acc = 0;
+#pragma unroll
+                    for (int s = 0; s < DP1; ++s) acc += w[s * nloc + e] * x[iidx[s * nloc + e]];
+                    const int k = k0 + q;
+                    re[2 * spad(k >> 1) + (k & 1)] = acc;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    line_fft<false>(buf, plan, t, tw, 2);
+    if (!active) return;
+    // X[k] = (Z_k + conj Z_{N-k})/2 - i/2 W_P^k (Z_k - conj Z_{N-k}),  k = 0..N
+    C* out = spec + line * pitch;
+    for (int k = t; k <= N; k += nthr) {
+        C zk = buf[spad(k & (N - 1))];
+        C zc = cconj(buf[spad((N - k) & (N - 1))]);
+        C e = cadd(zk, zc), o = csub(zk, zc);
+        // -i * o
+        C mo;
+        mo.x = o.y;
+        mo.y = -o.x;
+        C wk = __ldg(&tw[k]);
+        C r = cadd(e, cmul(wk, mo));
+        r.x *= (Real)0.5;
+        r.y *= (Real)0.5;
+        out[k] = r;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// kernel 2: complex FFTs along a strided axis for TC adjacent columns
+//   MODE 0: forward, rows_in nonzero rows -> P rows out
+//   MODE 1: forward, multiply by the symbol, inverse; rows_out rows kept
+//   MODE 2: inverse, P rows in -> rows_out rows out
+// ---------------------------------------------------------------------------
+struct ColDesc {
+    int64_t in_slab, in_row, out_slab, out_row;
+    int rows_in, rows_out, ncols, TC;
+    int64_t lam_slab, lam_row;  // symbol strides (MODE 1), folded indices
+    int P;
+};
+
+template <class Real, int MODE>
+__global__ void __launch_bounds__(512) col_fft_kernel(const typename Cplx<Real>::T* __restrict__ in, typename Cplx<Real>::T* __restrict__ out,
+                               ColDesc cd, LinePlan plan, const typename Cplx<Real>::T* __restrict__ tw,
+                               const Real* __restrict__ lam) {
+    using C = typename Cplx<Real>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* sm = reinterpret_cast<C*>(smem_raw);
+    const int N = plan.N;  // P
+    const int TC = cd.TC;
+    const int g = threadIdx.x % TC, t = threadIdx.x / TC;
+    const int c0 = blockIdx.x * TC;
+    const int64_t slab = blockIdx.y;
+    C* buf = sm + g * spad_len(N);
+    const C* src = in + slab * cd.in_slab + c0;
+    // load rows_in rows of TC columns (consecutive threads -> consecutive columns)
+    for (int i = threadIdx.x; i < N * TC; i += blockDim.x) {
+        const int row = i / TC, cc = i % TC;
+        C v = cmk<C>(0.0, 0.0);
+        if (row < cd.rows_in && c0 + cc < cd.ncols) v = src[row * cd.in_row + cc];
+        sm[cc * spad_len(N) + spad(row)] = v;
+    }
+    __syncthreads();
+    if (MODE == 2) {
+        line_fft<true>(buf, plan, t, tw, 1);
+    } else {
+        line_fft<false>(buf, plan, t, tw, 1);
+    }
+    if (MODE == 1) {
+        const int H = cd.P / 2;
+        const int64_t sl = slab <= H ? slab : cd.P - slab;
+        const Real* lp = lam + sl * cd.lam_slab + c0;
+        for (int i = threadIdx.x; i < N * TC; i += blockDim.x) {
+            const int row = i / TC, cc = i % TC;
+            if (c0 + cc >= cd.ncols) continue;
+            const int fr = row <= H ? row : N - row;
+            const Real l = lp[fr * cd.lam_row + cc];
+            C& v = sm[cc * spad_len(N) + spad(row)];
+            v.x *= l;
+            v.y *= l;
+        }
+        __syncthreads();
+        line_fft<true>(buf, plan, t, tw, 1);
+    }
+    C* dst = out + slab * cd.out_slab + c0;
+    const int rows = (MODE == 0) ? N : cd.rows_out;
+    for (int i = threadIdx.x; i < rows * TC; i += blockDim.x) {
+        const int row = i / TC, cc = i % TC;
+        if (c0 + cc < cd.ncols) dst[row * cd.out_row + cc] = sm[cc * spad_len(N) + spad(row)];
+    }
+}
+
+// 1D: multiply the half spectrum by the symbol
+template <class Real>
+__global__ void spec_scale_kernel(typename Cplx<Real>::T* __restrict__ spec, const Real* __restrict__ lam, int H) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < H; k += gridDim.x * blockDim.x) {
+        spec[k].x *= lam[k];
+        spec[k].y *= lam[k];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// kernel 3: inverse real FFT along axis 0, keeps k0 < n0
+// ---------------------------------------------------------------------------
+template <class Real>
+__global__ void __launch_bounds__(512) row_inverse_kernel(const typename Cplx<Real>::T* __restrict__ spec, int pitch, int64_t nlines,
+                                   LinePlan plan, const typename Cplx<Real>::T* __restrict__ tw,
+                                   Real* __restrict__ wgrid, int n0) {
+    using C = typename Cplx<Real>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* sm = reinterpret_cast<C*>(smem_raw);
+    const int N = plan.N;
+    const int nthr = plan.nthr;
+    const int g = threadIdx.x / nthr, t = threadIdx.x % nthr;
+    const int64_t line = (int64_t)blockIdx.x * (blockDim.x / nthr) + g;
+    const bool active = line < nlines;
+    C* buf = sm + g * spad_len(N);
+    if (active) {
+        const C* X = spec + line * pitch;
+        // Z'_k = (X_k + conj X_{N-k}) + i W_P^{-k} (X_k - conj X_{N-k}),  k < N
+        for (int k = t; k < N; k += nthr) {
+            C xk = X[k], xc = cconj(X[N - k]);
+            C e = cadd(xk, xc);
+            C o = cmulc(csub(xk, xc), __ldg(&tw[k]));
+            C z;
+            z.x = e.x - o.y;
+            z.y = e.y + o.x;
+            buf[spad(k)] = z;
+        }
+    }
+    __syncthreads();
+    line_fft<true>(buf, plan, t, tw, 2);
+    if (!active) return;
+    Real* wl = wgrid + line * n0;
+    const Real* re = reinterpret_cast<const Real*>(buf);
+    for (int k = t; k < n0; k += nthr) wl[k] = re[2 * spad(k >> 1) + (k & 1)];
+}
+
+// ---------------------------------------------------------------------------
+// kernel 4: y = I^T w, TPR lanes per interior vertex, fixed order
+// ---------------------------------------------------------------------------
+template <class Real, int TPR>
+__global__ void scatter_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                               const Real* __restrict__ val, const Real* __restrict__ w, int64_t nint,
+                               Real* __restrict__ y, Real scale) {
+    // the loop is uniform across each warp so that every lane reaches the shuffles
+    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x % TPR;
+    for (int64_t t0 = gid - (threadIdx.x & 31); t0 < nint * TPR; t0 += nthreads) {
+        const int64_t i = (t0 + (threadIdx.x & 31)) / TPR;
+        Real acc = 0;
+        if (i < nint) {
+            const int b = ptr[i], e = ptr[i + 1];
+            for (int a = b + lane; a < e; a += TPR) acc += val[a] * w[col[a]];
+        }
+#pragma unroll
+        for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, TPR);
+        if (lane == 0 && i < nint) y[i] = acc * scale;
+    }
+}
+
+template <class Real>
+__global__ void compact_kernel(const Real* __restrict__ u, const int32_t* __restrict__ i2v, int64_t nint,
+                               Real* __restrict__ x) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= nint;
+         i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = (i < nint) ? u[i2v[i]] : (Real)0;
+}
+
+template <class Real>
+__global__ void expand_kernel(const Real* __restrict__ y, const int32_t* __restrict__ v2i, int64_t nv,
+                              const double* __restrict__ colsum, double scale, Real* __restrict__ u) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = v2i[v];
+        Real r = 0;
+        if (i >= 0) {
+            r = y[i];
+            if (colsum) r = (Real)((double)r * scale / colsum[i]);
+        }
+        u[v] = r;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct ApplyCfg {
+    LinePlan row, col;
+    int lpc;          // lines per CTA in the row kernels
+    int tc32, tc64;   // columns per CTA in the column kernels
+};
+
+static ApplyCfg cfg_for(const gofd_problem* p) {
+    ApplyCfg c;
+    c.row = make_line_plan(p->P / 2);
+    c.col = make_line_plan(p->P);
+    c.lpc = std::max(1, 256 / c.row.nthr);
+    c.tc32 = std::max(1, std::min(16, 8192 / p->P));
+    c.tc64 = std::max(1, std::min(16, 4096 / p->P));
+    return c;
+}
+
+template <class Real> static size_t row_smem(const ApplyCfg& c) {
+    return sizeof(typename Cplx<Real>::T) * spad_len(c.row.N) * c.lpc;
+}
+template <class Real> static size_t col_smem(const ApplyCfg& c, int tc) {
+    return sizeof(typename Cplx<Real>::T) * spad_len(c.col.N) * tc;
+}
+
+// The dynamic shared-memory limit is a per-kernel attribute shared by every
+// handle, so it is raised once to the device's opt-in maximum; each launch
+// still requests only what its line length needs.
+template <class Real> static void set_smem_attrs(int limit) {
+    GOFD_CUDA_TRY(cudaFuncSetAttribute(row_forward_kernel<Real, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    GOFD_CUDA_TRY(cudaFuncSetAttribute(row_forward_kernel<Real, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    GOFD_CUDA_TRY(cudaFuncSetAttribute(row_forward_kernel<Real, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    GOFD_CUDA_TRY(cudaFuncSetAttribute(row_inverse_kernel<Real>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    GOFD_CUDA_TRY(cudaFuncSetAttribute(col_fft_kernel<Real, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    GOFD_CUDA_TRY(cudaFuncSetAttribute(col_fft_kernel<Real, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    GOFD_CUDA_TRY(cudaFuncSetAttribute(col_fft_kernel<Real, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+}
+
+void setup_apply(gofd_problem* p) {
+    ApplyCfg c = cfg_for(p);
+    const int P = p->P, d = p->d;
+    p->pitch0 = ((P / 2 + 1) + 15) / 16 * 16;
+    const int64_t n = p->n[0];
+    int64_t rowsA = p->nlines;
+    size_t cbytes = sizeof(double2);
+    p->specA.alloc(cbytes * rowsA * p->pitch0);
+    if (d == 3) p->specB.alloc(cbytes * n * P * p->pitch0);
+    p->gridw.alloc(sizeof(double) * p->ngrid);
+    p->xin.alloc(sizeof(double) * (p->nint + 1));
+    p->yout.alloc(sizeof(double) * (p->nint + 1));
+    int limit = 0;
+    GOFD_CUDA_TRY(cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
+    const size_t need = std::max({row_smem<double>(c), col_smem<float>(c, c.tc32), col_smem<double>(c, c.tc64)});
+    if (need > (size_t)limit) fail(GOFD_E_GRID, "FFT line does not fit in shared memory");
+    set_smem_attrs<float>(limit);
+    set_smem_attrs<double>(limit);
+}
+
+// Optional stage markers: when non-null, an event is recorded on the stream
+// after every launch of the product (used by gofd_apply_interior_profiled).
+struct StageEvents {
+    cudaEvent_t ev[8];
+    const char* name[8];
+    int n = 0;
+};
+static thread_local StageEvents* g_marks = nullptr;
+
+static void mark(cudaStream_t st, const char* name) {
+    if (!g_marks || g_marks->n >= 8) return;
+    GOFD_CUDA_TRY(cudaEventRecord(g_marks->ev[g_marks->n], st));
+    g_marks->name[g_marks->n++] = name;
+}
+
+template <class Real>
+static void afd_core(gofd_problem* p, const ApplyCfg& c, const Real* x, const Real* vgrid, Real* wgrid,
+                     cudaStream_t st) {
+    using C = typename Cplx<Real>::T;
+    const int d = p->d, P = p->P, H = P / 2 + 1;
+    const int64_t n = p->n[0];
+    const C* tw = reinterpret_cast<const C*>(sizeof(Real) == 4 ? p->tw32.ptr : p->tw64.ptr);
+    const Real* lam = reinterpret_cast<const Real*>(sizeof(Real) == 4 ? p->lam32.ptr : p->lam64.ptr);
+    const Real* w = reinterpret_cast<const Real*>(sizeof(Real) == 4 ? p->ell_w32.ptr : p->ell_w64.ptr);
+    C* A = p->specA.as<C>();
+    C* B = p->specB.as<C>();
+    const int tc = sizeof(Real) == 4 ? c.tc32 : c.tc64;
+
+    // 1. gather + forward real FFT along axis 0
+    {
+        const int threads = c.lpc * c.row.nthr;
+        const unsigned blocks = (unsigned)((p->nlines + c.lpc - 1) / c.lpc);
+        const size_t sm = row_smem<Real>(c);
+        const int gfg = vgrid != nullptr;
+#define ROWF(DP1)                                                                                      \
+    row_forward_kernel<Real, DP1><<<blocks, threads, sm, st>>>(                                        \
+        x, p->ell_iidx.as<int32_t>(), w, p->nloc, p->line_run_ptr.as<int32_t>(), p->run_k0.as<int32_t>(), \
+        p->run_len.as<int32_t>(), p->run_e0.as<int32_t>(), p->nlines, c.row, tw, A, p->pitch0, gfg, vgrid, \
+        (int)n)
+        if (d == 1) ROWF(2);
+        else if (d == 2) ROWF(3);
+        else ROWF(4);
+#undef ROWF
+        GOFD_CHECK_LAUNCH();
+        mark(st, "gather_row_fft");
+    }
+    // 2. the other axes
+    const int threads_c = tc * c.col.nthr;
+    const size_t smc = col_smem<Real>(c, tc);
+    const unsigned cblocks = (unsigned)((H + tc - 1) / tc);
+    if (d == 1) {
+        spec_scale_kernel<Real><<<grid_blocks(H, 256), 256, 0, st>>>(A, lam, H);
+        GOFD_CHECK_LAUNCH();
+        mark(st, "symbol_mul");
+    } else if (d == 2) {
+        ColDesc cd{0, p->pitch0, 0, p->pitch0, (int)n, (int)n, H, tc, 0, H, P};
+        col_fft_kernel<Real, 1><<<dim3(cblocks, 1), threads_c, smc, st>>>(A, A, cd, c.col, tw, lam);
+        GOFD_CHECK_LAUNCH();
+        mark(st, "col_fft_conv");
+    } else {
+        const int64_t pt = p->pitch0;
+        ColDesc f{n * pt, pt, (int64_t)P * pt, pt, (int)n, P, H, tc, 0, 0, P};
+        col_fft_kernel<Real, 0><<<dim3(cblocks, (unsigned)n), threads_c, smc, st>>>(A, B, f, c.col, tw, lam);
+        GOFD_CHECK_LAUNCH();
+        mark(st, "col_fft_fwd_axis1");
+        ColDesc m{pt, (int64_t)P * pt, pt, (int64_t)P * pt, (int)n, (int)n, H, tc, (int64_t)H, (int64_t)H * H, P};
+        col_fft_kernel<Real, 1><<<dim3(cblocks, (unsigned)P), threads_c, smc, st>>>(B, B, m, c.col, tw, lam);
+        GOFD_CHECK_LAUNCH();
+        mark(st, "col_fft_conv_axis2");
+        ColDesc iv{(int64_t)P * pt, pt, n * pt, pt, P, (int)n, H, tc, 0, 0, P};
+        col_fft_kernel<Real, 2><<<dim3(cblocks, (unsigned)n), threads_c, smc, st>>>(B, A, iv, c.col, tw, lam);
+        GOFD_CHECK_LAUNCH();
+        mark(st, "col_fft_inv_axis1");
+    }
+    // 3. inverse real FFT along axis 0
+    {
+        const int threads = c.lpc * c.row.nthr;
+        const unsigned blocks = (unsigned)((p->nlines + c.lpc - 1) / c.lpc);
+        row_inverse_kernel<Real><<<blocks, threads, row_smem<Real>(c), st>>>(A, p->pitch0, p->nlines, c.row, tw,
+                                                                           wgrid, (int)n);
+        GOFD_CHECK_LAUNCH();
+        mark(st, "row_ifft");
+    }
+}
+
+template <class Real>
+static void scatter(gofd_problem* p, const Real* wgrid, Real* y, Real scale, cudaStream_t st) {
+    const Real* val = reinterpret_cast<const Real*>(sizeof(Real) == 4 ? p->csr_val32.ptr : p->csr_val64.ptr);
+    const double avg = p->nint ? (double)p->nnz_t / p->nint : 0;
+    const int threads = 256;
+    if (avg > 96) {
+        scatter_kernel<Real, 32><<<grid_blocks(p->nint * 32, threads, 1 << 20), threads, 0, st>>>(
+            p->csr_ptr.as<int32_t>(), p->csr_col.as<int32_t>(), val, wgrid, p->nint, y, scale);
+    } else if (avg > 24) {
+        scatter_kernel<Real, 8><<<grid_blocks(p->nint * 8, threads, 1 << 20), threads, 0, st>>>(
+            p->csr_ptr.as<int32_t>(), p->csr_col.as<int32_t>(), val, wgrid, p->nint, y, scale);
+    } else {
+        scatter_kernel<Real, 4><<<grid_blocks(p->nint * 4, threads, 1 << 20), threads, 0, st>>>(
+            p->csr_ptr.as<int32_t>(), p->csr_col.as<int32_t>(), val, wgrid, p->nint, y, scale);
+    }
+    GOFD_CHECK_LAUNCH();
+    mark(st, "scatter");
+}
+
+template <class Real>
+static void apply_t(gofd_problem* p, const Real* x, Real* y, cudaStream_t st) {
+    ApplyCfg c = cfg_for(p);
+    Real* wg = p->gridw.as<Real>();
+    afd_core<Real>(p, c, x, nullptr, wg, st);
+    scatter<Real>(p, wg, y, (Real)1, st);
+}
+
+void apply_interior(gofd_problem* p, bool fp64, const void* x, void* y, cudaStream_t st) {
+    if (fp64) apply_t<double>(p, (const double*)x, (double*)y, st);
+    else apply_t<float>(p, (const float*)x, (float*)y, st);
+}
+
+int apply_interior_profiled(gofd_problem* p, bool fp64, const void* x, void* y, cudaStream_t st, float* ms,
+                            const char** names, int cap) {
+    StageEvents se;
+    for (int i = 0; i < 8; ++i) GOFD_CUDA_TRY(cudaEventCreate(&se.ev[i]));
+    cudaEvent_t start;
+    GOFD_CUDA_TRY(cudaEventCreate(&start));
+    GOFD_CUDA_TRY(cudaEventRecord(start, st));
+    g_marks = &se;
+    try {
+        apply_interior(p, fp64, x, y, st);
+    } catch (...) {
+        g_marks = nullptr;
+        throw;
+    }
+    g_marks = nullptr;
+    GOFD_CUDA_TRY(cudaEventSynchronize(se.ev[se.n - 1]));
+    int n = se.n < cap ? se.n : cap;
+    cudaEvent_t prev = start;
+    for (int i = 0; i < n; ++i) {
+        GOFD_CUDA_TRY(cudaEventElapsedTime(&ms[i], prev, se.ev[i]));
+        if (names) names[i] = se.name[i];
+        prev = se.ev[i];
+    }
+    for (int i = 0; i < 8; ++i) cudaEventDestroy(se.ev[i]);
+    cudaEventDestroy(start);
+    return n;
+}
+
+void afd_apply_grid(gofd_problem* p, bool fp64, const void* v, void* w, cudaStream_t st) {
+    ApplyCfg c = cfg_for(p);
+    if (fp64) afd_core<double>(p, c, nullptr, (const double*)v, (double*)w, st);
+    else afd_core<float>(p, c, nullptr, (const float*)v, (float*)w, st);
+}
+
+void compact_vertex(gofd_problem* p, bool fp64, const void* u, void* x, cudaStream_t st) {
+    if (fp64)
+        compact_kernel<double><<<grid_blocks(p->nint + 1, 256), 256, 0, st>>>(
+            (const double*)u, p->int2vert.as<int32_t>(), p->nint, (double*)x);
+    else
+        compact_kernel<float><<<grid_blocks(p->nint + 1, 256), 256, 0, st>>>(
+            (const float*)u, p->int2vert.as<int32_t>(), p->nint, (float*)x);
+    GOFD_CHECK_LAUNCH();
+}
+
+void expand_interior(gofd_problem* p, bool fp64, const void* y, void* u, double scale_by_inv_colsum,
+                     cudaStream_t st) {
+    const double* cs = scale_by_inv_colsum != 0.0 ? p->colsum.as<double>() : nullptr;
+    if (fp64)
+        expand_kernel<double><<<grid_blocks(p->nv, 256), 256, 0, st>>>(
+            (const double*)y, p->vert2int.as<int32_t>(), p->nv, cs, scale_by_inv_colsum, (double*)u);
+    else
+        expand_kernel<float><<<grid_blocks(p->nv, 256), 256, 0, st>>>(
+            (const float*)y, p->vert2int.as<int32_t>(), p->nv, cs, scale_by_inv_colsum, (float*)u);
+    GOFD_CHECK_LAUNCH();
+}
+
+// y = scale * I^T f for a grid vector f (FP64): the RHS of (GoFD-2)
+void scatter_grid_f64(gofd_problem* p, const double* f, double* y, double scale, cudaStream_t st) {
+    scatter<double>(p, f, y, scale, st);
+}
+
+}  // namespace gofd

@@ -1,0 +1,186 @@
+// Internal declarations shared by the GoFD CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gofd.h"
+
+namespace gofd {
+
+// ---------------------------------------------------------------------------
+// error handling
+// ---------------------------------------------------------------------------
+struct Error {
+    gofd_status code;
+    std::string msg;
+};
+
+#define GOFD_CUDA_TRY(expr)                                                        \
+    do {                                                                           \
+        cudaError_t _e = (expr);                                                   \
+        if (_e != cudaSuccess)                                                     \
+            throw ::gofd::Error{GOFD_E_CUDA, std::string(#expr) + ": " +           \
+                                             cudaGetErrorString(_e)};              \
+    } while (0)
+
+#define GOFD_CHECK_LAUNCH() GOFD_CUDA_TRY(cudaGetLastError())
+
+[[noreturn]] inline void fail(gofd_status c, const std::string& m) { throw Error{c, m}; }
+
+// ---------------------------------------------------------------------------
+// device buffers owned by the handle
+// ---------------------------------------------------------------------------
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf() { release(); }
+    void alloc(size_t b) {
+        release();
+        if (b == 0) b = 16;
+        cudaError_t e = cudaMalloc(&ptr, b);
+        if (e != cudaSuccess) {
+            ptr = nullptr;
+            throw Error{GOFD_E_NOMEM, "cudaMalloc of " + std::to_string(b) + " bytes: " +
+                                          cudaGetErrorString(e)};
+        }
+        bytes = b;
+    }
+    void release() {
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        bytes = 0;
+    }
+    template <class T> T* as() const { return static_cast<T*>(ptr); }
+};
+
+// ---------------------------------------------------------------------------
+// FFT plans (per line length)
+// ---------------------------------------------------------------------------
+struct LinePlan {
+    int N = 0;               // complex line length (power of two)
+    int nthr = 0;            // threads per line = N / 16 (or N if N < 16)
+    int npass = 0;
+    int radix[8] = {0};
+};
+LinePlan make_line_plan(int N);
+
+// ---------------------------------------------------------------------------
+// the problem handle
+// ---------------------------------------------------------------------------
+struct Precond;   // defined in precond.cu
+
+struct Workspace;  // solver vectors, defined in solver.cu
+
+}  // namespace gofd
+
+struct gofd_problem {
+    // inputs
+    int d = 0;
+    int64_t nv = 0, ne = 0;
+    double alpha = 0, s = 0, h = 0;
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    int n[3] = {1, 1, 1};
+    int64_t ngrid = 0;
+    int64_t nlines = 0;        // n_1*n_2 (lines along axis 0)
+    int P = 0;                 // circulant length per axis
+    int64_t filon_M = 0;
+    int rich_levels = 4;
+    gofd_options opt{};
+    cudaStream_t setup_stream = nullptr;
+    int device = 0;
+
+    // mesh on the device
+    gofd::DevBuf verts, simp;
+
+    // point location / transfer
+    gofd::DevBuf owner;        // int32 [ngrid]
+    int64_t nloc = 0;
+    gofd::DevBuf ell_node;     // int32 [nloc]      grid index of each ELL row
+    gofd::DevBuf ell_vidx;     // int32 [(d+1)*nloc] vertex numbering (canonical)
+    gofd::DevBuf ell_w64;      // double[(d+1)*nloc]
+    gofd::DevBuf ell_w32;      // float [(d+1)*nloc]
+    gofd::DevBuf ell_iidx;     // int32 [(d+1)*nloc] interior numbering, boundary -> nint (zero slot)
+    int64_t nruns = 0;
+    gofd::DevBuf line_run_ptr; // int32 [nlines+1]
+    gofd::DevBuf run_k0;       // int32 [nruns]   first k0 of the run
+    gofd::DevBuf run_len;      // int32 [nruns]
+    gofd::DevBuf run_e0;       // int32 [nruns]   ELL row of the first node
+
+    // vertices
+    int64_t nint = 0;
+    gofd::DevBuf vert2int;     // int32 [nv], -1 on the boundary
+    gofd::DevBuf int2vert;     // int32 [nint]
+    gofd::DevBuf csr_ptr;      // int32 [nint+1]
+    gofd::DevBuf csr_col;      // int32 [nnz]   grid index
+    gofd::DevBuf csr_val64;    // double[nnz]
+    gofd::DevBuf csr_val32;    // float [nnz]
+    int64_t nnz_t = 0;
+    gofd::DevBuf colsum;       // double[nint]  D_h over interior vertices
+    double a_h = 0, min_colsum = 0;
+
+    // coefficients and symbol
+    gofd::DevBuf T;            // double[n^d]
+    gofd::DevBuf lam64;        // double[(P/2+1)^d], scaled by 1/P^d
+    gofd::DevBuf lam32;        // float [(P/2+1)^d], scaled by 1/P^d
+    gofd::DevBuf tw64, tw32;   // twiddle tables e^{-2 pi i m / L} for L = P and P/2 (concatenated)
+
+    // FFT convolution work buffers
+    int pitch0 = 0;            // complex entries per spectrum row along axis 0 (>= P/2+1)
+    gofd::DevBuf specA;        // complex, n_{d-1}..n_1 rows x pitch0 (largest precision)
+    gofd::DevBuf specB;        // 3D only: n x P x pitch0 complex
+    gofd::DevBuf gridw;        // real [ngrid] (largest precision): A_FD v on the grid
+    gofd::DevBuf xin;          // real [nint+1] compacted input (largest precision)
+    gofd::DevBuf yout;         // real [nint]
+    gofd::DevBuf stage_u, stage_y;  // host-call staging (allocated on first use)
+
+    // solver / preconditioner
+    gofd::Workspace* ws = nullptr;
+    gofd::Precond* pc = nullptr;
+
+    double t_setup_ms = 0;
+    std::string last_error;
+};
+
+namespace gofd {
+
+// set-up stages (setup_mesh.cu)
+void setup_mesh(gofd_problem* p, const double* verts_h, const int32_t* simp_h);
+
+// coefficients and symbol (coeff.cu)
+void setup_coefficients(gofd_problem* p);
+
+// FFT-convolution apply (apply.cu)
+void setup_apply(gofd_problem* p);
+void apply_interior(gofd_problem* p, bool fp64, const void* x, void* y, cudaStream_t st);
+void afd_apply_grid(gofd_problem* p, bool fp64, const void* v, void* w, cudaStream_t st);
+int apply_interior_profiled(gofd_problem* p, bool fp64, const void* x, void* y, cudaStream_t st, float* ms,
+                            const char** names, int cap);
+void compact_vertex(gofd_problem* p, bool fp64, const void* u, void* x, cudaStream_t st);
+void expand_interior(gofd_problem* p, bool fp64, const void* y, void* u, double scale_by_inv_colsum,
+                     cudaStream_t st);
+
+// solver (solver.cu)
+void solve(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs, const double* f, double tol,
+           int maxit, bool init_zero, double* u, gofd_solve_info* info, cudaStream_t st);
+void free_workspace(gofd_problem* p);
+
+// preconditioner (precond.cu)
+void setup_precond(gofd_problem* p);
+void free_precond(gofd_problem* p);
+int64_t precond_nnz(const gofd_problem* p);
+double precond_shift(const gofd_problem* p);
+// z = M^{-1} r on interior vectors (length nint); fp64 selects the precision
+void precond_apply(gofd_problem* p, bool fp64, const void* r, void* z, cudaStream_t st);
+
+// utilities (setup_mesh.cu)
+int64_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t st);
+int grid_blocks(int64_t work, int threads, int cap = 152 * 16);
+
+}  // namespace gofd

@@ -1,0 +1,185 @@
+"""Python binding of the GoFD C ABI (argument marshalling only).
+
+Device memory and streams come from PyTorch; every step of the method runs in
+the CUDA kernels of libgofd.so.  Vectors are torch tensors on the current CUDA
+device, in the caller's vertex order (N_v entries) or grid order (n^d entries,
+axis 0 fastest).
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _native as N
+
+
+class GofdError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{N.STATUS.get(status, status)}: {message}")
+        self.status = status
+        self.code = N.STATUS.get(status, str(status))
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t) -> C.c_void_p:
+    return C.c_void_p(t.data_ptr())
+
+
+_PREC = {"fp64": N.FP64, "fp32": N.FP32}
+_OPS = {"stiffness": N.OP_STIFFNESS, "fraclap": N.OP_FRACLAP}
+_MODES = {"fp64": N.SOLVE_FP64, "mixed": N.SOLVE_MIXED}
+_RHS = {"grid": N.RHS_GRID, "vertex": N.RHS_VERTEX}
+
+
+class Problem:
+    """One discrete GoFD problem: gofd_build(mesh, alpha, h, box)."""
+
+    def __init__(self, vertices, simplices, alpha: float, h: float, box_lo, box_hi, *, precond: int = 0,
+                 ic_level: int = 1, filon_M: int = 0, richardson_levels: int = 0, inner_tol: float = 0.0,
+                 check_every: int = 0, wait_budget_cycles: int = 0):
+        self._lib = N.load()
+        v = np.ascontiguousarray(vertices, dtype=np.float64)
+        s = np.ascontiguousarray(simplices, dtype=np.int32)
+        if v.ndim != 2 or s.ndim != 2 or s.shape[1] != v.shape[1] + 1:
+            raise ValueError("vertices must be (N_v, d) and simplices (N_e, d+1)")
+        self.d = v.shape[1]
+        lo = np.ascontiguousarray(box_lo, dtype=np.float64).reshape(-1)
+        hi = np.ascontiguousarray(box_hi, dtype=np.float64).reshape(-1)
+        opt = N.Options(precond=precond, ic_level=ic_level, filon_M=filon_M,
+                        richardson_levels=richardson_levels, wait_budget_cycles=wait_budget_cycles,
+                        inner_tol=inner_tol, check_every=check_every)
+        h_ = C.c_void_p()
+        st = self._lib.gofd_build(self.d, v.ctypes.data, v.shape[0], s.ctypes.data, s.shape[0], float(alpha),
+                                  float(h), lo.ctypes.data, hi.ctypes.data, C.byref(opt), C.byref(h_))
+        if st != 0:
+            raise GofdError(st, self._lib.gofd_last_error(None).decode())
+        self._h = h_
+        self.alpha = alpha
+        self.h = h
+        inf = self.info()
+        self.n_v = inf["n_v"]
+        self.n_interior = inf["n_interior"]
+        self.n = inf["n"][: self.d]
+        self.n_grid = inf["n_grid"]
+        self.P = inf["P"]
+
+    # -- life cycle ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.gofd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int):
+        if st != 0:
+            raise GofdError(st, self._lib.gofd_last_error(self._h).decode())
+
+    # -- queries ------------------------------------------------------------
+    def info(self) -> dict:
+        inf = N.Info()
+        self._check(self._lib.gofd_get_info(self._h, C.byref(inf)))
+        out = {k: getattr(inf, k) for k, _ in N.Info._fields_}
+        out["n"] = list(inf.n)
+        return out
+
+    def export_transfer(self):
+        """(owner[n_grid], ell_idx[d+1, n_loc], ell_w[d+1, n_loc]) as NumPy arrays."""
+        inf = self.info()
+        nl = inf["n_loc"]
+        owner = np.empty(inf["n_grid"], dtype=np.int32)
+        idx = np.empty((self.d + 1, nl), dtype=np.int32)
+        w = np.empty((self.d + 1, nl), dtype=np.float64)
+        self._check(self._lib.gofd_export_transfer(self._h, owner.ctypes.data, idx.ctypes.data, w.ctypes.data))
+        return owner, idx, w
+
+    def export_vertex_data(self):
+        ii = np.empty(self.n_v, dtype=np.int32)
+        cs = np.empty(self.n_v, dtype=np.float64)
+        self._check(self._lib.gofd_export_vertex_data(self._h, ii.ctypes.data, cs.ctypes.data))
+        return ii, cs
+
+    def coefficients(self) -> np.ndarray:
+        T = np.empty(self.n_grid, dtype=np.float64)
+        self._check(self._lib.gofd_get_coefficients(self._h, T.ctypes.data))
+        return T.reshape(tuple(reversed(self.n)))
+
+    def symbol(self) -> np.ndarray:
+        H = self.P // 2 + 1
+        lam = np.empty(H ** self.d, dtype=np.float64)
+        self._check(self._lib.gofd_get_symbol(self._h, lam.ctypes.data))
+        return lam.reshape((H,) * self.d)
+
+    # -- operators ----------------------------------------------------------
+    def apply(self, u, op: str = "stiffness", out=None, stream=None):
+        """y = S u (op='stiffness', (GoFD-2)) or h^{-2s} D_h^{-1} S u (op='fraclap')."""
+        torch = _torch()
+        prec = "fp64" if u.dtype == torch.float64 else "fp32"
+        if out is None:
+            out = torch.empty_like(u)
+        self._check(self._lib.gofd_apply(self._h, _OPS[op], _PREC[prec], _ptr(u), _ptr(out), _stream_ptr(stream)))
+        return out
+
+    def apply_interior(self, x, y, stream=None):
+        torch = _torch()
+        prec = "fp64" if x.dtype == torch.float64 else "fp32"
+        self._check(self._lib.gofd_apply_interior(self._h, _PREC[prec], _ptr(x), _ptr(y), _stream_ptr(stream)))
+        return y
+
+    def apply_interior_profiled(self, x, y, stream=None):
+        """apply_interior with per-stage CUDA-event times: returns [(name, ms), ...]."""
+        torch = _torch()
+        prec = "fp64" if x.dtype == torch.float64 else "fp32"
+        ms = (C.c_float * 8)()
+        names = (C.c_char_p * 8)()
+        cnt = C.c_int(0)
+        self._check(self._lib.gofd_apply_interior_profiled(self._h, _PREC[prec], _ptr(x), _ptr(y),
+                                                           _stream_ptr(stream), ms, names, 8, C.byref(cnt)))
+        return [(names[i].decode(), float(ms[i])) for i in range(cnt.value)]
+
+    def apply_host(self, u: np.ndarray, op: str = "stiffness", out: np.ndarray | None = None, stream=None):
+        """The apply on host buffers (copies inside the call)."""
+        prec = "fp64" if u.dtype == np.float64 else "fp32"
+        u = np.ascontiguousarray(u)
+        if out is None:
+            out = np.empty_like(u)
+        self._check(self._lib.gofd_apply_host(self._h, _OPS[op], _PREC[prec], C.c_void_p(u.ctypes.data),
+                                              C.c_void_p(out.ctypes.data), _stream_ptr(stream)))
+        return out
+
+    def afd_apply(self, v, out=None, stream=None):
+        """w = A_FD v on the grid (Section 2.2)."""
+        torch = _torch()
+        prec = "fp64" if v.dtype == torch.float64 else "fp32"
+        if out is None:
+            out = torch.empty_like(v)
+        self._check(self._lib.gofd_afd_apply(self._h, _PREC[prec], _ptr(v), _ptr(out), _stream_ptr(stream)))
+        return out
+
+    def solve(self, f, rhs: str = "grid", mode: str = "mixed", tol: float = 1e-8, maxit: int = 100000,
+              u0=None, stream=None):
+        """Solve (GoFD-2); f is a float64 CUDA tensor on the grid or the vertices."""
+        torch = _torch()
+        if f.dtype != torch.float64:
+            raise TypeError("f must be float64")
+        u = torch.zeros(self.n_v, dtype=torch.float64, device=f.device) if u0 is None else u0.clone()
+        info = N.SolveInfo()
+        st = self._lib.gofd_solve(self._h, _MODES[mode], _RHS[rhs], _ptr(f), float(tol), int(maxit),
+                                  1 if u0 is None else 0, _ptr(u), C.byref(info), _stream_ptr(stream))
+        self._check(st)
+        return u, {k: getattr(info, k) for k, _ in N.SolveInfo._fields_}

@@ -1,0 +1,287 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Bars: owner simplex and ELL layout of I_h^FD bit-exact; barycentric weights
+within their FP64 evaluation error; FP64 operators relative L2 <= 1e-12;
+FP32 operators <= 1e-5 (random inputs); solves reach relative residual <= tol
+measured with the oracle's operator.
+"""
+import numpy as np
+import pytest
+
+import meshgen as mg
+from oracle import gofd as o
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2307_14437_gb300 import build_native
+    build_native.build()
+
+
+def _gpu(v, s, alpha, h, lo, hi, **kw):
+    from paper_2307_14437_gb300 import Problem
+    return Problem(v, s, alpha, h, lo, hi, **kw)
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+# ---------------------------------------------------------------------------
+# workloads of parity size: (name, d, mesh builder, n, alpha, M)
+# ---------------------------------------------------------------------------
+def _case(name):
+    if name == "disk17":
+        v, s = mg.disk_ring_mesh(rings=6, seed=mg.seed_for(1, 1))
+        return 2, v, s, 17, 1.0, 2 ** 10
+    if name == "disk37_ragged":
+        v, s = mg.disk_ring_mesh(rings=9, seed=mg.seed_for(1, 2))
+        return 2, v, s, 37, 0.5, 2 ** 10
+    if name == "lshape33":
+        v, s = mg.lshape_mesh(spacing=0.15, seed=mg.seed_for(2, 1))
+        return 2, v, s, 33, 1.5, 2 ** 10
+    if name == "aligned2":
+        lo, hi, h = mg.grid_box(2, 11)
+        v, s = mg.grid_aligned_mesh(2, -1.0, h, 6, origin_cells=2)
+        return 2, v, s, 11, 1.2, 2 ** 10
+    if name == "ball9":
+        v, s = mg.ball_shell_mesh(shells=3, seed=mg.seed_for(3, 1))
+        return 3, v, s, 9, 1.5, 2 ** 8
+    if name == "aligned3":
+        lo, hi, h = mg.grid_box(3, 7)
+        v, s = mg.grid_aligned_mesh(3, -1.0, h, 4, origin_cells=1)
+        return 3, v, s, 7, 1.0, 2 ** 8
+    if name == "interval33":
+        v, s = mg.interval_mesh(16, seed=mg.seed_for(0, 1))
+        return 1, v, s, 33, 0.8, 2 ** 12
+    raise KeyError(name)
+
+
+SMALL = ["disk17", "disk37_ragged", "lshape33", "aligned2", "ball9", "aligned3", "interval33"]
+
+
+@pytest.fixture(scope="module")
+def built():
+    cache = {}
+
+    def get(name):
+        if name not in cache:
+            d, v, s, n, alpha, M = _case(name)
+            lo, hi, h = mg.grid_box(d, n)
+            ref = o.build(d, v, s, alpha, h, lo, hi, M=M)
+            gp = _gpu(v, s, alpha, h, lo, hi, filon_M=M)
+            cache[name] = (gp, ref)
+        return cache[name]
+    return get
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_transfer_bit_exact(built, name):
+    gp, ref = built(name)
+    owner, idx, w = gp.export_transfer()
+    assert np.array_equal(owner, ref.owner.astype(np.int32))
+    assert np.array_equal(idx, ref.ell_idx.astype(np.int32))
+    # exact rational weights rounded once vs FP64 cofactor ratios
+    assert np.abs(w - ref.ell_w).max() < 1e-13
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_boundary_numbering_and_colsums(built, name):
+    gp, ref = built(name)
+    ii, cs = gp.export_vertex_data()
+    expect = -np.ones(len(ref.verts), dtype=np.int64)
+    expect[ref.interior] = np.arange(len(ref.interior))
+    assert np.array_equal(ii, expect)
+    assert np.abs(cs[ref.interior] - ref.Dh[ref.interior]).max() < 1e-13 * ref.Dh.max()
+    inf = gp.info()
+    assert abs(inf["a_h"] - ref.a_h) < 1e-14 * ref.a_h
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_coefficients(built, name):
+    gp, ref = built(name)
+    T = gp.coefficients()
+    assert np.abs(T - ref.T).max() < 1e-13
+
+
+@pytest.mark.parametrize("name", ["disk17", "aligned2", "ball9", "interval33"])
+def test_symbol(built, name):
+    gp, ref = built(name)
+    if gp.P != ref.P:
+        pytest.skip("different circulant length")
+    lam = gp.symbol()
+    assert np.abs(lam - ref.lam).max() < 1e-12 * np.abs(ref.lam).max()
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_afd_apply(built, name):
+    gp, ref = built(name)
+    v = mg.random_vector(ref.n_grid, 7)
+    want = o.afd_apply(ref, v, method="direct")
+    got64 = gp.afd_apply(torch.tensor(v, device="cuda")).cpu().numpy()
+    got32 = gp.afd_apply(torch.tensor(v, device="cuda", dtype=torch.float32)).cpu().numpy()
+    assert _rel(got64, want) < 1e-12
+    assert _rel(got32.astype(np.float64), want) < 1e-5
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_stiffness_apply(built, name):
+    gp, ref = built(name)
+    u = mg.random_vector(len(ref.verts), 11)
+    want = o.stiffness_apply(ref, u, method="direct")
+    y64 = gp.apply(torch.tensor(u, device="cuda")).cpu().numpy()
+    y32 = gp.apply(torch.tensor(u, device="cuda", dtype=torch.float32)).cpu().numpy()
+    assert _rel(y64, want) < 1e-12
+    assert _rel(y32.astype(np.float64), want) < 1e-5
+    assert np.all(y64[ref.boundary] == 0.0)
+
+
+@pytest.mark.parametrize("name", ["disk17", "ball9"])
+def test_fraclap_apply(built, name):
+    gp, ref = built(name)
+    u = mg.random_vector(len(ref.verts), 12)
+    want = o.fraclap_apply(ref, u, method="direct")
+    got = gp.apply(torch.tensor(u, device="cuda"), op="fraclap").cpu().numpy()
+    assert _rel(got, want) < 1e-12
+
+
+def test_boundary_inputs_are_ignored(built):
+    gp, ref = built("disk17")
+    u = mg.random_vector(len(ref.verts), 13)
+    u2 = u.copy()
+    u2[ref.boundary] = np.nan
+    a = gp.apply(torch.tensor(u, device="cuda")).cpu().numpy()
+    b = gp.apply(torch.tensor(u2, device="cuda")).cpu().numpy()
+    assert np.array_equal(a, b)
+
+
+def test_apply_is_deterministic(built):
+    gp, ref = built("lshape33")
+    u = torch.tensor(mg.random_vector(len(ref.verts), 14), device="cuda", dtype=torch.float32)
+    a = gp.apply(u).cpu().numpy()
+    b = gp.apply(u).cpu().numpy()
+    assert np.array_equal(a, b)
+
+
+def test_apply_host_matches_device(built):
+    gp, ref = built("disk37_ragged")
+    u = mg.random_vector(len(ref.verts), 15)
+    a = gp.apply_host(u)
+    b = gp.apply(torch.tensor(u, device="cuda")).cpu().numpy()
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", ["disk17", "lshape33", "ball9"])
+def test_solve_residual(built, name, mode):
+    gp, ref = built(name)
+    f = np.ones(ref.n_grid)
+    tol = 1e-10
+    u, info = gp.solve(torch.tensor(f, device="cuda"), rhs="grid", mode=mode, tol=tol)
+    u = u.cpu().numpy()
+    b = o.rhs_grid(ref, f)
+    res = np.linalg.norm(b - o.stiffness_apply(ref, u)) / np.linalg.norm(b)
+    assert res < 2 * tol, (res, info)
+    x_ref, _ = o.solve(ref, b, tol=1e-13)
+    assert _rel(u, x_ref) < 1e-7
+    assert np.all(u[ref.boundary] == 0.0)
+
+
+def test_solve_vertex_rhs_equals_grid_rhs_for_constant_f(built):
+    # (GoFD-1) and (GoFD-3) give the same system for f = 1
+    gp, ref = built("disk17")
+    ug, _ = gp.solve(torch.ones(ref.n_grid, dtype=torch.float64, device="cuda"), rhs="grid", mode="fp64", tol=1e-12)
+    uv, _ = gp.solve(torch.ones(len(ref.verts), dtype=torch.float64, device="cuda"), rhs="vertex", mode="fp64",
+                     tol=1e-12)
+    assert _rel(uv.cpu().numpy(), ug.cpu().numpy()) < 1e-10
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+def test_degenerate_simplex_is_rejected():
+    from paper_2307_14437_gb300 import GofdError
+    v = np.array([[0.0, 0.0], [0.5, 0.5], [0.25, 0.25], [0.5, 0.0]])
+    s = np.array([[0, 1, 2], [0, 3, 1]])
+    lo, hi, h = mg.grid_box(2, 9)
+    with pytest.raises(GofdError) as e:
+        _gpu(v, s, 1.0, h, lo, hi, filon_M=2 ** 10)
+    assert e.value.code == "GOFD_E_DEGENERATE_SIMPLEX"
+
+
+def test_zero_column_sum_is_rejected():
+    # split an interior triangle that holds no grid node at its centroid: the
+    # new vertex's patch is that triangle, so its column sum D_h is exactly 0
+    from paper_2307_14437_gb300 import GofdError
+    v, s = mg.disk_ring_mesh(rings=6, seed=1)
+    lo, hi, h = mg.grid_box(2, 13)
+    n = o.grid_shape(lo, hi, h)
+    own = o.locate(v, s, lo, h, n)
+    cnt = np.bincount(own[own >= 0], minlength=len(s))
+    bnd = o.boundary_vertices(s, len(v))
+    e = int([k for k in np.nonzero(cnt == 0)[0] if not bnd[s[k]].any()][0])
+    a, b, c = s[e]
+    m = len(v)
+    v2 = np.vstack([v, v[s[e]].mean(axis=0)])
+    s2 = mg._orient_positive(v2, np.vstack([np.delete(s, e, axis=0), [[a, b, m], [b, c, m], [c, a, m]]]))
+    assert o.build(2, v2, s2, 1.0, h, lo, hi, M=2 ** 10, exact_weights=False).Dh[m] == 0.0
+    with pytest.raises(GofdError) as err:
+        _gpu(v2, s2, 1.0, h, lo, hi, filon_M=2 ** 10)
+    assert err.value.code == "GOFD_E_ZERO_COLSUM"
+
+
+def test_mesh_in_a_large_box_leaves_most_nodes_outside():
+    v, s = mg.disk_ring_mesh(rings=3, seed=2)
+    v = 0.2 * v
+    lo, hi, h = mg.grid_box(2, 65)
+    gp = _gpu(v, s, 1.0, h, lo, hi, filon_M=2 ** 10)
+    ref = o.build(2, v, s, 1.0, h, lo, hi, M=2 ** 10)
+    owner, idx, _ = gp.export_transfer()
+    assert np.array_equal(owner, ref.owner.astype(np.int32))
+    u = mg.random_vector(len(v), 3)
+    y = gp.apply(torch.tensor(u, device="cuda")).cpu().numpy()
+    assert _rel(y, o.stiffness_apply(ref, u)) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# configuration 1 in full (unit disk, 1951 vertices, 128^2 grid, alpha = 1)
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def c1():
+    v, s = mg.disk_ring_mesh()
+    lo, hi, h = mg.grid_box(2, 128)
+    ref = o.build(2, v, s, 1.0, h, lo, hi, exact_weights=False)
+    gp = _gpu(v, s, 1.0, h, lo, hi)
+    return gp, ref
+
+
+def test_c1_transfer_and_apply(c1):
+    gp, ref = c1
+    owner, idx, w = gp.export_transfer()
+    assert np.array_equal(owner, ref.owner.astype(np.int32))
+    assert np.array_equal(idx, ref.ell_idx.astype(np.int32))
+    assert np.abs(w - ref.ell_w).max() < 1e-12
+    assert np.abs(gp.coefficients() - ref.T).max() < 1e-13
+    u = mg.random_vector(len(ref.verts), 21)
+    want = o.stiffness_apply(ref, u)
+    assert _rel(gp.apply(torch.tensor(u, device="cuda")).cpu().numpy(), want) < 1e-12
+    y32 = gp.apply(torch.tensor(u, device="cuda", dtype=torch.float32)).cpu().numpy()
+    assert _rel(y32.astype(np.float64), want) < 1e-5
+
+
+def test_c1_solve_against_closed_form(c1):
+    gp, ref = c1
+    u, info = gp.solve(torch.ones(ref.n_grid, dtype=torch.float64, device="cuda"), rhs="grid", mode="fp64",
+                       tol=1e-10)
+    u = u.cpu().numpy()
+    b = o.rhs_grid(ref, np.ones(ref.n_grid))
+    assert np.linalg.norm(b - o.stiffness_apply(ref, u)) / np.linalg.norm(b) < 2e-10
+    # (exam-2): u = (2/pi) (1-|x|^2)^{1/2}; the FM error is O(h) in L2
+    err = o.lumped_l2(ref.verts, ref.simp, u - o.ball_exact(ref.verts, 0.5))
+    assert err < 0.02, err

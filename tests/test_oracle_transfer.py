@@ -223,3 +223,21 @@ def test_exact_weights_are_rounded_rationals():
 def test_grid_rejects_non_integral_box():
     with pytest.raises(o.OracleError):
         o.grid_shape([-1.0, -1.0], [1.0, 1.0], 0.3)
+
+
+@pytest.mark.parametrize("case", ["disk", "aligned2", "aligned3", "ball"])
+def test_pruned_locate_equals_brute_force(case):
+    if case == "disk":
+        v, s = mg.disk_ring_mesh(rings=8, seed=2)
+        lo, hi, h = mg.grid_box(2, 33)
+    elif case == "aligned2":
+        lo, hi, h = mg.grid_box(2, 9)
+        v, s = mg.grid_aligned_mesh(2, -1.0, h, 4, origin_cells=2)
+    elif case == "aligned3":
+        lo, hi, h = mg.grid_box(3, 5)
+        v, s = mg.grid_aligned_mesh(3, -1.0, h, 2, origin_cells=1)
+    else:
+        v, s = mg.ball_shell_mesh(shells=3, seed=4)
+        lo, hi, h = mg.grid_box(3, 9)
+    n = o.grid_shape(lo, hi, h)
+    assert np.array_equal(o.locate_pruned(v, s, lo, h, n), o.locate(v, s, lo, h, n))

@@ -16,7 +16,8 @@
  * Conventions shared by every call
  *  - Every call returns a gofd_status; nothing is thrown across the ABI.
  *    gofd_last_error() gives a message for the last failure on a handle
- *    (or, with a NULL handle, for the last failed gofd_build of the thread).
+ *    (or, with a NULL handle, for the last failed handle-free call of the
+ *    thread: gofd_build or gofd_afd_apply_noalloc).
  *  - Host inputs are copied; the caller keeps ownership of everything it
  *    passes.  A gofd_problem owns all of its device memory and frees it in
  *    gofd_destroy().  A handle is not thread safe: serialise calls on it.
@@ -235,6 +236,36 @@ gofd_status gofd_get_symbol(const gofd_problem* p, double* lambda);
  */
 gofd_status gofd_afd_apply(gofd_problem* p, gofd_precision prec,
                            const void* v_dev, void* w_dev, void* stream);
+
+/*
+ * gofd_afd_apply_noalloc -- w = A_FD v in FP32 on an n^d grid (d = 1..3)
+ * without allocating any memory.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc at the moment they
+ * need the product -- code running while a CUDA graph is being captured,
+ * plug-ins inside a framework that owns all device memory through its own
+ * allocator, real-time loops that must not risk an allocation failure.
+ *   d, n        grid dimension and nodes per axis (no handle is needed)
+ *   lambda_dev  device, (P/2+1)^d floats, axis 0 fastest: the real circulant
+ *               symbol divided by P^d, lambda_k / P^d for k in [0, P/2]^d, with
+ *               P = max(32, smallest power of two >= 2n-2); gofd_get_symbol
+ *               returns lambda_k (unscaled, FP64) for a built problem
+ *   v_dev       device, n^d floats (input grid vector)
+ *   w_dev       device, n^d floats (output), must not overlap v_dev
+ * The spectrum scratch is a file-scope device array of 1,064,960 complex
+ * floats (8.1 MiB, plus a 16 KiB twiddle table) that every GPU loading the
+ * library holds until the process exits.  A grid whose spectrum does not fit
+ * (a 2D grid needs n*pitch, a 3D grid n^2*pitch + n*P*pitch complex values,
+ * pitch = P/2+1 rounded up to a multiple of 16; so 2D n <= 1024) is rejected
+ * with GOFD_E_ARG before any device work.  The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress) and raises the
+ * kernels' shared-memory limit, so make that first call before any stream
+ * capture.  Every call uses the same array and it keeps the last call's
+ * contents; calls that overlap on the GPU (several streams or threads) race
+ * and give wrong results.  No cudaMalloc, cudaFree or allocating library
+ * routine is called.  Messages go to gofd_last_error(NULL).
+ */
+gofd_status gofd_afd_apply_noalloc(int d, int n, const float* lambda_dev, const float* v_dev,
+                                   float* w_dev, void* stream);
 
 /* gofd_destroy -- free the handle and all of its device memory (NULL is a no-op). */
 void gofd_destroy(gofd_problem* p);

@@ -61,6 +61,7 @@ EXPORTS = {
     "gofd_get_coefficients": (C.c_int, [_P, _P]),
     "gofd_get_symbol": (C.c_int, [_P, _P]),
     "gofd_afd_apply": (C.c_int, [_P, C.c_int, _P, _P, _P]),
+    "gofd_afd_apply_noalloc": (C.c_int, [C.c_int, C.c_int, _P, _P, _P, _P]),
     "gofd_destroy": (None, [_P]),
     "gofd_last_error": (C.c_char_p, [_P]),
 }

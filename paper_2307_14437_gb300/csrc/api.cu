@@ -319,4 +319,9 @@ gofd_status gofd_afd_apply(gofd_problem* p, gofd_precision prec, const void* v_d
     })
 }
 
+gofd_status gofd_afd_apply_noalloc(int d, int n, const float* lambda_dev, const float* v_dev, float* w_dev,
+                                   void* stream) {
+    GOFD_API_BODY(nullptr, { gofd::afd_apply_noalloc(d, n, lambda_dev, v_dev, w_dev, (cudaStream_t)stream); })
+}
+
 }  // extern "C"

@@ -12,6 +12,7 @@
 // registers, with the exchange between passes through padded shared memory.
 // Every transform is unnormalised; the symbol carries the 1/P^d factor.
 #include <algorithm>
+#include <mutex>
 
 #include "gofd_internal.cuh"
 
@@ -648,6 +649,130 @@ void expand_interior(gofd_problem* p, bool fp64, const void* y, void* u, double 
 // y = scale * I^T f for a grid vector f (FP64): the RHS of (GoFD-2)
 void scatter_grid_f64(gofd_problem* p, const double* f, double* y, double scale, cudaStream_t st) {
     scatter<double>(p, f, y, scale, st);
+}
+
+}  // namespace gofd
+
+// ===========================================================================
+// Allocation-free grid convolution w = A_FD v (FP32).
+//
+// Some callers cannot call cudaMalloc when they need this product: code that
+// runs while a CUDA graph is being captured (allocation is not allowed then),
+// plug-ins living inside a host framework whose device memory is entirely
+// owned by that framework's own allocator, and real-time loops that must not
+// risk an allocation failure or its latency.  This variant takes the symbol,
+// the input and the output from the caller and keeps its spectrum scratch in
+// a fixed file-scope device array instead of any allocation.  Every GPU that
+// loads the library holds that array (8.1 MiB plus a 16 KiB twiddle table)
+// until the process exits.  It launches the same kernels as the handle-based
+// product.
+// ===========================================================================
+namespace gofd {
+
+constexpr int64_t NOALLOC_MAX_COMPLEX = 1064960;  // 1024 rows x 1040: a 2D grid with n <= 1024
+constexpr int NOALLOC_MAX_P = 2048;
+static __device__ __align__(256) float2 g_noalloc_spec[NOALLOC_MAX_COMPLEX];
+static __device__ __align__(256) float2 g_noalloc_tw[NOALLOC_MAX_P];
+
+struct NoallocDevice {
+    bool ready = false;
+    float2* spec = nullptr;  // device address of g_noalloc_spec on this device
+    float2* tw = nullptr;    // device address of g_noalloc_tw on this device
+};
+static std::mutex g_noalloc_mu;
+static NoallocDevice g_noalloc_devices[128];
+
+__global__ void noalloc_twiddle_kernel(float2* __restrict__ tw, int P) {
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < P; m += gridDim.x * blockDim.x) {
+        double sn, cs;
+        sincospi(2.0 * (double)m / (double)P, &sn, &cs);
+        tw[m] = make_float2((float)cs, (float)-sn);
+    }
+}
+
+// Set-up once per device, with that device current: look up the arrays'
+// device addresses (a host-side symbol is not a device address) and raise the
+// kernels' dynamic shared-memory limit.
+static NoallocDevice noalloc_device() {
+    int dev = 0;
+    GOFD_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 128) fail(GOFD_E_CUDA, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    NoallocDevice& d = g_noalloc_devices[dev];
+    if (!d.ready) {
+        void* spec = nullptr;
+        void* tw = nullptr;
+        GOFD_CUDA_TRY(cudaGetSymbolAddress(&spec, g_noalloc_spec));
+        GOFD_CUDA_TRY(cudaGetSymbolAddress(&tw, g_noalloc_tw));
+        int limit = 0;
+        GOFD_CUDA_TRY(cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        set_smem_attrs<float>(limit);
+        d.spec = static_cast<float2*>(spec);
+        d.tw = static_cast<float2*>(tw);
+        d.ready = true;
+    }
+    return d;
+}
+
+void afd_apply_noalloc(int d, int n, const float* lam, const float* v, float* w, cudaStream_t st) {
+    if (d < 1 || d > 3) fail(GOFD_E_ARG, "d must be 1, 2 or 3");
+    if (n < 2) fail(GOFD_E_ARG, "n must be at least 2");
+    if (!lam || !v || !w) fail(GOFD_E_ARG, "NULL vector");
+    int P = 1;
+    while (P < 2 * n - 2) P *= 2;
+    if (P < 32) P = 32;
+    const int H = P / 2 + 1;
+    const int pitch = (H + 15) / 16 * 16;
+    int64_t nlines = 1;
+    for (int i = 1; i < d; ++i) nlines *= n;
+    const int64_t needA = nlines * pitch;
+    const int64_t needB = (d == 3) ? (int64_t)n * P * pitch : 0;
+    if (P > NOALLOC_MAX_P || needA + needB > NOALLOC_MAX_COMPLEX)
+        fail(GOFD_E_ARG, "grid too large for the static scratch of 1064960 complex values "
+                         "(a 2D grid needs n*pitch, a 3D grid n^2*pitch + n*P*pitch, pitch = P/2+1 rounded up to 16)");
+    const NoallocDevice dv = noalloc_device();
+    float2* A = dv.spec;
+    float2* B = dv.spec + needA;
+    noalloc_twiddle_kernel<<<grid_blocks(P, 256), 256, 0, st>>>(dv.tw, P);
+    GOFD_CHECK_LAUNCH();
+    const LinePlan row = make_line_plan(P / 2), col = make_line_plan(P);
+    const int lpc = std::max(1, 256 / row.nthr);
+    const int tc = std::max(1, std::min(16, 8192 / P));
+    const size_t rsm = sizeof(float2) * spad_len(row.N) * lpc;
+    const size_t csm = sizeof(float2) * spad_len(col.N) * tc;
+    const unsigned rblocks = (unsigned)((nlines + lpc - 1) / lpc);
+    // forward real FFT along axis 0 of the caller's grid vector
+    if (d == 1)
+        row_forward_kernel<float, 2><<<rblocks, lpc * row.nthr, rsm, st>>>(
+            nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, nlines, row, dv.tw, A, pitch, 1, v, n);
+    else if (d == 2)
+        row_forward_kernel<float, 3><<<rblocks, lpc * row.nthr, rsm, st>>>(
+            nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, nlines, row, dv.tw, A, pitch, 1, v, n);
+    else
+        row_forward_kernel<float, 4><<<rblocks, lpc * row.nthr, rsm, st>>>(
+            nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, nlines, row, dv.tw, A, pitch, 1, v, n);
+    GOFD_CHECK_LAUNCH();
+    const unsigned cblocks = (unsigned)((H + tc - 1) / tc);
+    const int threads_c = tc * col.nthr;
+    if (d == 1) {
+        spec_scale_kernel<float><<<grid_blocks(H, 256), 256, 0, st>>>(A, lam, H);
+    } else if (d == 2) {
+        ColDesc cd{0, pitch, 0, pitch, n, n, H, tc, 0, H, P};
+        col_fft_kernel<float, 1><<<dim3(cblocks, 1), threads_c, csm, st>>>(A, A, cd, col, dv.tw, lam);
+    } else {
+        const int64_t pt = pitch;
+        ColDesc f{(int64_t)n * pt, pt, (int64_t)P * pt, pt, n, P, H, tc, 0, 0, P};
+        col_fft_kernel<float, 0><<<dim3(cblocks, (unsigned)n), threads_c, csm, st>>>(A, B, f, col, dv.tw, lam);
+        GOFD_CHECK_LAUNCH();
+        ColDesc m{pt, (int64_t)P * pt, pt, (int64_t)P * pt, n, n, H, tc, (int64_t)H, (int64_t)H * H, P};
+        col_fft_kernel<float, 1><<<dim3(cblocks, (unsigned)P), threads_c, csm, st>>>(B, B, m, col, dv.tw, lam);
+        GOFD_CHECK_LAUNCH();
+        ColDesc iv{(int64_t)P * pt, pt, (int64_t)n * pt, pt, P, n, H, tc, 0, 0, P};
+        col_fft_kernel<float, 2><<<dim3(cblocks, (unsigned)n), threads_c, csm, st>>>(B, A, iv, col, dv.tw, lam);
+    }
+    GOFD_CHECK_LAUNCH();
+    row_inverse_kernel<float><<<rblocks, lpc * row.nthr, rsm, st>>>(A, pitch, nlines, row, dv.tw, w, n);
+    GOFD_CHECK_LAUNCH();
 }
 
 }  // namespace gofd

@@ -160,6 +160,7 @@ void setup_coefficients(gofd_problem* p);
 void setup_apply(gofd_problem* p);
 void apply_interior(gofd_problem* p, bool fp64, const void* x, void* y, cudaStream_t st);
 void afd_apply_grid(gofd_problem* p, bool fp64, const void* v, void* w, cudaStream_t st);
+void afd_apply_noalloc(int d, int n, const float* lam, const float* v, float* w, cudaStream_t st);
 int apply_interior_profiled(gofd_problem* p, bool fp64, const void* x, void* y, cudaStream_t st, float* ms,
                             const char** names, int cap);
 void compact_vertex(gofd_problem* p, bool fp64, const void* u, void* x, cudaStream_t st);

@@ -183,3 +183,23 @@ class Problem:
                                   1 if u0 is None else 0, _ptr(u), C.byref(info), _stream_ptr(stream))
         self._check(st)
         return u, {k: getattr(info, k) for k, _ in N.SolveInfo._fields_}
+
+
+def afd_apply_noalloc(d: int, n: int, lam_scaled, v, out=None, stream=None):
+    """w = A_FD v (FP32) through the entry point that allocates nothing.
+
+    For callers that cannot allocate device memory when they need the product
+    (inside CUDA graph capture, under a framework-owned allocator, in
+    real-time loops): the library keeps its scratch in a fixed device array.
+    lam_scaled is the float32 symbol lambda_k / P^d on [0, P/2]^d; v and out
+    are float32 grid vectors of n^d entries.  Calls that overlap on the GPU
+    race on the shared scratch.
+    """
+    lib = N.load()
+    torch = _torch()
+    if out is None:
+        out = torch.empty_like(v)
+    st = lib.gofd_afd_apply_noalloc(int(d), int(n), _ptr(lam_scaled), _ptr(v), _ptr(out), _stream_ptr(stream))
+    if st != 0:
+        raise GofdError(st, lib.gofd_last_error(None).decode())
+    return out

@@ -1,0 +1,40 @@
+// Set-up of the transposed-spectrum 2D product: the transposed scaled symbol,
+// the transposed spectrum buffer and the kernels' shared-memory limits.
+#include <algorithm>
+
+#include "gofd_internal.cuh"
+
+namespace gofd {
+
+void afd_2d_attrs_f32(int limit, int P, size_t* need);
+void afd_2d_attrs_f64(int limit, int P, size_t* need);
+
+__global__ void transpose_sym_kernel(const double* __restrict__ l64, double* __restrict__ t64,
+                                     float* __restrict__ t32, int H) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)H * H;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / H, c = i % H;   // t[r][c] = l[c][r]
+        const double v = l64[c * H + r];
+        t64[i] = v;
+        t32[i] = (float)v;
+    }
+}
+
+void setup_apply_2d(gofd_problem* p) {
+    const int H = p->P / 2 + 1;
+    p->ldT = (p->n[0] + 15) / 16 * 16;
+    p->specT.alloc(sizeof(double2) * (size_t)H * p->ldT);
+    p->lamT64.alloc(sizeof(double) * (size_t)H * H);
+    p->lamT32.alloc(sizeof(float) * (size_t)H * H);
+    transpose_sym_kernel<<<grid_blocks((int64_t)H * H, 256), 256, 0, p->setup_stream>>>(
+        p->lam64.as<double>(), p->lamT64.as<double>(), p->lamT32.as<float>(), H);
+    GOFD_CHECK_LAUNCH();
+    int limit = 0;
+    GOFD_CUDA_TRY(cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
+    size_t n32 = 0, n64 = 0;
+    afd_2d_attrs_f32(limit, p->P, &n32);
+    afd_2d_attrs_f64(limit, p->P, &n64);
+    if (std::max(n32, n64) > (size_t)limit) fail(GOFD_E_GRID, "FFT line does not fit in shared memory");
+}
+
+}  // namespace gofd

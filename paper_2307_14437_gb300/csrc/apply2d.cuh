@@ -1,0 +1,338 @@
+// 2D stiffness product with the half spectrum stored transposed (kernels).
+//
+//   row_fwd_t    gather v = I x straight into the registers of the first FFT
+//                pass of each grid line (no padded grid vector in memory), real
+//                FFT of the line, half spectrum written transposed through a
+//                shared-memory tile: spec_T[k_x0][line]
+//   col_conv_t   one spectrum column per thread group, contiguous in memory:
+//                loads go straight into registers, forward FFT over the n
+//                nonzero rows, the real even symbol multiplied in registers,
+//                inverse FFT starting from the same registers, n rows stored
+//   row_inv_t    transposed tile load, inverse real FFT of each line, the n
+//                kept samples written to the grid vector
+//
+// Line lengths are compile-time constants (powers of two), so every pass has
+// a constant radix and stride.  Passes exchange data through padded shared
+// memory with per-line named barriers, so lines of one CTA do not wait for
+// each other.
+#pragma once
+
+#include <algorithm>
+
+#include "gofd_internal.cuh"
+#include "fft_common.cuh"
+
+namespace gofd {
+
+__device__ __forceinline__ void group_sync(int g, int nthr) {
+    if (nthr >= 32) asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(nthr) : "memory");
+    else __syncthreads();
+}
+
+template <int R, bool INV, class C>
+__device__ __forceinline__ void reg_pass(C (&v)[FFT_E], int t, int nthr, int N, int Ns, const C* __restrict__ tw,
+                                         int twstride) {
+    constexpr int Q = FFT_E / R;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int b = t + q * nthr;
+        const int k = b % Ns;
+        if (k != 0) {
+            const int step = (N / (Ns * R)) * twstride;
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                C w = __ldg(&tw[k * r * step]);
+                if (INV) w.y = -w.y;
+                v[q * R + r] = cmul(v[q * R + r], w);
+            }
+        }
+        dft_reg<R, INV>(v + q * R);
+    }
+}
+
+template <int R, class C>
+__device__ __forceinline__ void reg_store(C* buf, const C (&v)[FFT_E], int t, int nthr, int Ns) {
+    constexpr int Q = FFT_E / R;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int b = t + q * nthr;
+        const int base = (b / Ns) * Ns * R + b % Ns;
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[spad(base + r * Ns)] = v[q * R + r];
+    }
+}
+
+template <int R, class C>
+__device__ __forceinline__ void reg_load(const C* buf, C (&v)[FFT_E], int t, int nthr, int N) {
+    constexpr int Q = FFT_E / R;
+    const int S = N / R;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int b = t + q * nthr;
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[q * R + r] = buf[spad(b + r * S)];
+    }
+}
+
+// Visit the thread's elements of a pass of radix R: f(i, pos) with i the
+// register index (a compile-time constant after unrolling) and pos = b + r N/R
+// the line position.  Dispatching on R keeps v[] in registers.
+template <int R, class F>
+__device__ __forceinline__ void each_elem_r(int t, int nthr, int N, F&& f) {
+    constexpr int Q = FFT_E / R;
+    const int S = N / R;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int b = t + q * nthr;
+#pragma unroll
+        for (int r = 0; r < R; ++r) f(q * R + r, b + r * S);
+    }
+}
+// ---------------------------------------------------------------------------
+// compile-time pass plans: radix 16 passes first, then the remainder
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int ct_full16(int N) { int f = 0; while (N >= 16) { N /= 16; ++f; } return f; }
+__host__ __device__ constexpr int ct_rem(int N) { while (N >= 16) N /= 16; return N; }
+__host__ __device__ constexpr int ct_npass(int N) { return ct_full16(N) + (ct_rem(N) > 1 ? 1 : 0); }
+__host__ __device__ constexpr int ct_radix(int N, int i) { return i < ct_full16(N) ? 16 : ct_rem(N); }
+// REV: the same radices in reverse order (the inverse column transform starts
+// with the forward transform's last radix so the data stays in registers)
+__host__ __device__ constexpr int ct_radix_o(int N, bool rev, int i) {
+    return rev ? ct_radix(N, ct_npass(N) - 1 - i) : ct_radix(N, i);
+}
+
+template <bool INV, int N, bool REV, int PS = 0, int NS = 1, class C>
+__device__ __forceinline__ void fft_ct(C (&v)[FFT_E], C* buf, int t, int g, const C* __restrict__ tw, int tws) {
+    if constexpr (PS < ct_npass(N)) {
+        constexpr int R = ct_radix_o(N, REV, PS);
+        constexpr int NTHR = N / FFT_E;
+        if constexpr (PS > 0) {
+            constexpr int RP = ct_radix_o(N, REV, PS - 1);
+            reg_store<RP>(buf, v, t, NTHR, NS / RP);
+            group_sync(g, NTHR);
+            reg_load<R>(buf, v, t, NTHR, N);
+            group_sync(g, NTHR);
+        }
+        reg_pass<R, INV>(v, t, NTHR, N, NS, tw, tws);
+        fft_ct<INV, N, REV, PS + 1, NS * R>(v, buf, t, g, tw, tws);
+    }
+}
+
+template <int N, bool REV>
+__host__ __device__ constexpr int ct_first(int) { return ct_radix_o(N, REV, 0); }
+template <int N, bool REV>
+__host__ __device__ constexpr int ct_last() { return ct_radix_o(N, REV, ct_npass(N) - 1); }
+
+// ---------------------------------------------------------------------------
+// gather of one grid sample: sum over the owner simplex's slots (ELL row e)
+// ---------------------------------------------------------------------------
+template <class Real, int DP1>
+__device__ __forceinline__ Real ell_value(const Real* __restrict__ x, const int32_t* __restrict__ iidx,
+                                          const Real* __restrict__ w, int64_t nloc, int64_t e) {
+    Real acc = 0;
+#pragma unroll
+    for (int s = 0; s < DP1; ++s) acc += __ldg(&w[s * nloc + e]) * __ldg(&x[__ldg(&iidx[s * nloc + e])]);
+    return acc;
+}
+
+struct Runs {
+    int n;          // runs on this line
+    int k0[2], len[2], e0[2];
+    int rb;         // first run index (for lines with more than two runs)
+};
+
+template <class Real, int DP1>
+__device__ __forceinline__ Real sample(int k, const Runs& rs, const int32_t* __restrict__ run_k0,
+                                       const int32_t* __restrict__ run_len, const int32_t* __restrict__ run_e0,
+                                       const Real* __restrict__ x, const int32_t* __restrict__ iidx,
+                                       const Real* __restrict__ w, int64_t nloc) {
+    if (rs.n <= 2) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+            if (r < rs.n && k >= rs.k0[r] && k < rs.k0[r] + rs.len[r])
+                return ell_value<Real, DP1>(x, iidx, w, nloc, rs.e0[r] + (k - rs.k0[r]));
+        return 0;
+    }
+    for (int r = rs.rb; r < rs.rb + rs.n; ++r) {
+        const int a = __ldg(&run_k0[r]);
+        if (k >= a && k < a + __ldg(&run_len[r])) return ell_value<Real, DP1>(x, iidx, w, nloc, __ldg(&run_e0[r]) + (k - a));
+    }
+    return 0;
+}
+
+// ---------------------------------------------------------------------------
+// kernel 1: gather + real FFT per grid line, transposed half spectrum out
+// ---------------------------------------------------------------------------
+template <class Real, int DP1, int N>
+__global__ void __launch_bounds__(512) row_fwd_t_kernel(
+    const Real* __restrict__ x, const int32_t* __restrict__ iidx, const Real* __restrict__ w, int64_t nloc,
+    const int32_t* __restrict__ run_ptr, const int32_t* __restrict__ run_k0, const int32_t* __restrict__ run_len,
+    const int32_t* __restrict__ run_e0, const Real* __restrict__ vgrid, int nlines, int n,
+    const typename Cplx<Real>::T* __restrict__ tw, typename Cplx<Real>::T* __restrict__ specT, int ld, int lpc) {
+    using C = typename Cplx<Real>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* sm = reinterpret_cast<C*>(smem_raw);
+    constexpr int nthr = N / FFT_E;
+    const int g = threadIdx.x / nthr, t = threadIdx.x % nthr;
+    const int line = blockIdx.x * lpc + g;
+    const bool active = line < nlines;
+    C* buf = sm + g * spad_len(N);
+
+    Runs rs;
+    rs.n = 0;
+    rs.rb = 0;
+    if (active && !vgrid) {
+        rs.rb = __ldg(&run_ptr[line]);
+        rs.n = __ldg(&run_ptr[line + 1]) - rs.rb;
+        for (int r = 0; r < 2; ++r)
+            if (r < rs.n) {
+                rs.k0[r] = __ldg(&run_k0[rs.rb + r]);
+                rs.len[r] = __ldg(&run_len[rs.rb + r]);
+                rs.e0[r] = __ldg(&run_e0[rs.rb + r]);
+            }
+    }
+    // pass-0 inputs z[m] = (v[2m], v[2m+1]) gathered straight into registers
+    C v[FFT_E];
+    each_elem_r<ct_radix_o(N, false, 0)>(t, nthr, N, [&](int i, int m) {
+        const int k = 2 * m;
+        Real a0 = 0, a1 = 0;
+        if (active && k < n) {
+            if (vgrid) {
+                a0 = vgrid[(int64_t)line * n + k];
+                if (k + 1 < n) a1 = vgrid[(int64_t)line * n + k + 1];
+            } else {
+                a0 = sample<Real, DP1>(k, rs, run_k0, run_len, run_e0, x, iidx, w, nloc);
+                if (k + 1 < n) a1 = sample<Real, DP1>(k + 1, rs, run_k0, run_len, run_e0, x, iidx, w, nloc);
+            }
+        }
+        v[i].x = a0;
+        v[i].y = a1;
+    });
+    fft_ct<false, N, false>(v, buf, t, g, tw, 2);
+    {
+        constexpr int RL = ct_last<N, false>();
+        reg_store<RL>(buf, v, t, nthr, N / RL);
+    }
+    __syncthreads();
+    // X[k] = (Z_k + conj Z_{N-k})/2 - i/2 W_P^k (Z_k - conj Z_{N-k}),  k = 0..N
+    constexpr int JMAX = FFT_E + 1;
+    C X[JMAX];
+#pragma unroll
+    for (int j = 0; j < JMAX; ++j) {
+        const int k = t + j * nthr;
+        if (k <= N) {
+            const C zk = buf[spad(k & (N - 1))];
+            const C zc = cconj(buf[spad((N - k) & (N - 1))]);
+            const C e = cadd(zk, zc), o = csub(zk, zc);
+            C mo;
+            mo.x = o.y;
+            mo.y = -o.x;
+            C r = cadd(e, cmul(__ldg(&tw[k]), mo));
+            r.x *= (Real)0.5;
+            r.y *= (Real)0.5;
+            X[j] = r;
+        }
+    }
+    __syncthreads();
+    // transposed tile: element (k, line g) at k*lpc + (g ^ (k & (lpc-1)))
+    const int msk = lpc - 1;
+#pragma unroll
+    for (int j = 0; j < JMAX; ++j) {
+        const int k = t + j * nthr;
+        if (k <= N) sm[k * lpc + (g ^ (k & msk))] = X[j];
+    }
+    __syncthreads();
+    const int total = (N + 1) * lpc;
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+        const int k = i / lpc, l = i % lpc;
+        const int ln = blockIdx.x * lpc + l;
+        if (ln < nlines) specT[(int64_t)k * ld + ln] = sm[k * lpc + (l ^ (k & msk))];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// kernel 2: per spectrum column: FFT (n nonzero rows), symbol, inverse FFT
+// ---------------------------------------------------------------------------
+template <class Real, int N>
+__global__ void __launch_bounds__(512) col_conv_t_kernel(typename Cplx<Real>::T* __restrict__ specT, int ld, int n,
+                                                       int H, const typename Cplx<Real>::T* __restrict__ tw,
+                                                       const Real* __restrict__ lamT) {
+    using C = typename Cplx<Real>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* sm = reinterpret_cast<C*>(smem_raw);
+    constexpr int nthr = N / FFT_E;
+    const int G = blockDim.x / nthr;
+    const int g = threadIdx.x / nthr, t = threadIdx.x % nthr;
+    const int col = blockIdx.x * G + g;
+    const bool active = col < H;
+    C* buf = sm + g * spad_len(N);
+    C* column = specT + (int64_t)(active ? col : 0) * ld;
+    C v[FFT_E];
+    each_elem_r<ct_radix_o(N, false, 0)>(t, nthr, N, [&](int i, int row) {
+        v[i] = (active && row < n) ? column[row] : cmk<C>(0.0, 0.0);
+    });
+    fft_ct<false, N, false>(v, buf, t, g, tw, 1);
+    {
+        // multiply by the (pre-scaled) symbol: row k_x1 folded to [0, N/2]
+        const Real* lc = lamT + (int64_t)(active ? col : 0) * H;
+        each_elem_r<ct_last<N, false>()>(t, nthr, N, [&](int i, int row) {
+            const int fr = row <= N / 2 ? row : N - row;
+            const Real l = __ldg(&lc[fr]);
+            v[i].x *= l;
+            v[i].y *= l;
+        });
+    }
+    fft_ct<true, N, true>(v, buf, t, g, tw, 1);
+    each_elem_r<ct_last<N, true>()>(t, nthr, N, [&](int i, int row) {
+        if (active && row < n) column[row] = v[i];
+    });
+}
+
+// ---------------------------------------------------------------------------
+// kernel 3: transposed tile in, inverse real FFT per line, n samples out
+// ---------------------------------------------------------------------------
+template <class Real, int N>
+__global__ void __launch_bounds__(512) row_inv_t_kernel(const typename Cplx<Real>::T* __restrict__ specT, int ld,
+                                                      int nlines, int n, const typename Cplx<Real>::T* __restrict__ tw,
+                                                      Real* __restrict__ wgrid, int lpc) {
+    using C = typename Cplx<Real>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* sm = reinterpret_cast<C*>(smem_raw);
+    constexpr int nthr = N / FFT_E;
+    const int msk = lpc - 1;
+    const int total = (N + 1) * lpc;
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+        const int k = i / lpc, l = i % lpc;
+        const int ln = blockIdx.x * lpc + l;
+        sm[k * lpc + (l ^ (k & msk))] = (ln < nlines) ? specT[(int64_t)k * ld + ln] : cmk<C>(0.0, 0.0);
+    }
+    __syncthreads();
+    const int g = threadIdx.x / nthr, t = threadIdx.x % nthr;
+    const int line = blockIdx.x * lpc + g;
+    const bool active = line < nlines;
+    C v[FFT_E];
+    // Z'_k = (X_k + conj X_{N-k}) + i W_P^{-k} (X_k - conj X_{N-k})
+    each_elem_r<ct_radix_o(N, false, 0)>(t, nthr, N, [&](int i, int k) {
+        const int kc = N - k;
+        const C xk = sm[k * lpc + (g ^ (k & msk))];
+        const C xc = cconj(sm[kc * lpc + (g ^ (kc & msk))]);
+        const C e = cadd(xk, xc);
+        const C o = cmulc(csub(xk, xc), __ldg(&tw[k]));
+        C z;
+        z.x = e.x - o.y;
+        z.y = e.y + o.x;
+        v[i] = z;
+    });
+    __syncthreads();
+    C* buf = sm + g * spad_len(N);
+    fft_ct<true, N, false>(v, buf, t, g, tw, 2);
+    if (!active) return;
+    Real* wl = wgrid + (int64_t)line * n;
+    each_elem_r<ct_last<N, false>()>(t, nthr, N, [&](int i, int m) {
+        const int k = 2 * m;
+        if (k < n) wl[k] = v[i].x;
+        if (k + 1 < n) wl[k + 1] = v[i].y;
+    });
+}
+
+}  // namespace gofd

@@ -1,0 +1,174 @@
+// Device helpers shared by the FFT-convolution kernels: complex arithmetic,
+// in-register radix-2/4/8/16 DFTs and the shared-memory Stockham pass.
+#pragma once
+
+#include "gofd_internal.cuh"
+
+namespace gofd {
+
+// ---------------------------------------------------------------------------
+// complex arithmetic
+// ---------------------------------------------------------------------------
+template <class R> struct Cplx;
+template <> struct Cplx<float> { using T = float2; };
+template <> struct Cplx<double> { using T = double2; };
+
+template <class C> __device__ __forceinline__ C cmk(double x, double y);
+template <> __device__ __forceinline__ float2 cmk<float2>(double x, double y) { return make_float2((float)x, (float)y); }
+template <> __device__ __forceinline__ double2 cmk<double2>(double x, double y) { return make_double2(x, y); }
+
+template <class C> __device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <class C> __device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+template <class C> __device__ __forceinline__ C cmul(C a, C b) {
+    C r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+// a * conj(b)
+template <class C> __device__ __forceinline__ C cmulc(C a, C b) {
+    C r;
+    r.x = a.x * b.x + a.y * b.y;
+    r.y = a.y * b.x - a.x * b.y;
+    return r;
+}
+template <class C> __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
+
+// shared-memory index with one pad slot per 16 complex entries (bank spread)
+__device__ __forceinline__ int spad(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int spad_len(int n) { return n + (n >> 4) + 1; }
+
+// cos / sin of 2 pi k / 16
+__host__ __device__ constexpr double cos16(int k) {
+    switch (k & 15) {
+        case 0: return 1.0;
+        case 1: return 0.92387953251128675613;
+        case 2: return 0.70710678118654752440;
+        case 3: return 0.38268343236508977173;
+        case 4: return 0.0;
+        case 5: return -0.38268343236508977173;
+        case 6: return -0.70710678118654752440;
+        case 7: return -0.92387953251128675613;
+        case 8: return -1.0;
+        case 9: return -0.92387953251128675613;
+        case 10: return -0.70710678118654752440;
+        case 11: return -0.38268343236508977173;
+        case 12: return 0.0;
+        case 13: return 0.38268343236508977173;
+        case 14: return 0.70710678118654752440;
+        default: return 0.92387953251128675613;
+    }
+}
+__host__ __device__ constexpr double sin16(int k) { return cos16(k - 4); }
+
+// multiply by exp(-+ 2 pi i j / 16) (sign by INV); j is a compile-time constant after unrolling
+template <bool INV, class C> __device__ __forceinline__ C twc16(C a, int j) {
+    j &= 15;
+    if (j == 0) return a;
+    if (j == 4) {  // -i (forward) or +i (inverse)
+        C r;
+        if (!INV) { r.x = a.y; r.y = -a.x; } else { r.x = -a.y; r.y = a.x; }
+        return r;
+    }
+    if (j == 8) { a.x = -a.x; a.y = -a.y; return a; }
+    if (j == 12) {
+        C r;
+        if (!INV) { r.x = -a.y; r.y = a.x; } else { r.x = a.y; r.y = -a.x; }
+        return r;
+    }
+    double c = cos16(j), s = INV ? sin16(j) : -sin16(j);
+    return cmul(a, cmk<C>(c, s));
+}
+
+__host__ __device__ constexpr int bitrev(int x, int bits) {
+    int r = 0;
+    for (int i = 0; i < bits; ++i) r |= ((x >> i) & 1) << (bits - 1 - i);
+    return r;
+}
+
+// In-register DFT of length R (power of two <= 16), natural order in and out:
+// v[k] <- sum_r v[r] exp(-+2 pi i r k / R).  Radix-2 decimation in frequency,
+// then a compile-time bit-reversal permutation.
+template <int R, bool INV, class C> __device__ __forceinline__ void dft_reg(C* v) {
+    constexpr int LOG = (R == 2) ? 1 : (R == 4) ? 2 : (R == 8) ? 3 : 4;
+#pragma unroll
+    for (int st = 0; st < LOG; ++st) {
+        const int span = R >> (st + 1);
+#pragma unroll
+        for (int blk = 0; blk < R; blk += 2 * span) {
+#pragma unroll
+            for (int j = 0; j < span; ++j) {
+                C a = v[blk + j], b = v[blk + j + span];
+                v[blk + j] = cadd(a, b);
+                // twiddle exp(-2 pi i j / (2 span)) = index j * 16 / (2 span) of the 16-table
+                v[blk + j + span] = twc16<INV>(csub(a, b), j * (16 / (2 * span)));
+            }
+        }
+    }
+    C t[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) t[k] = v[bitrev(k, LOG)];
+#pragma unroll
+    for (int k = 0; k < R; ++k) v[k] = t[k];
+}
+
+// ---------------------------------------------------------------------------
+// one line FFT of length N (power of two >= 16) in padded shared memory,
+// computed by nthr = N/16 threads (thread index t of the line's group).
+// Stockham autosort: pass with radix R reads x[b + r N/R], applies twiddles
+// exp(-+2 pi i (b mod Ns) r / (Ns R)), a radix-R DFT, and writes
+// y[(b/Ns) Ns R + b mod Ns + r Ns].  The twiddle table holds exp(-2 pi i m / P)
+// for m < P; line length N = P / twstride.
+// ---------------------------------------------------------------------------
+constexpr int FFT_E = 16;
+
+template <int R, bool INV, class C>
+__device__ __forceinline__ void stockham_pass(C* buf, int N, int Ns, int t, int nthr, const C* __restrict__ tw,
+                                              int twstride, C (&v)[FFT_E]) {
+    constexpr int Q = FFT_E / R;
+    const int stride_in = N / R;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int b = t + q * nthr;
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[q * R + r] = buf[spad(b + r * stride_in)];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int b = t + q * nthr;
+        const int k = b % Ns;
+        const int step = (N / (Ns * R)) * twstride;
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+            if (k != 0) {
+                C w = __ldg(&tw[k * r * step]);
+                if (INV) w.y = -w.y;
+                v[q * R + r] = cmul(v[q * R + r], w);
+            }
+        }
+        dft_reg<R, INV>(v + q * R);
+        const int base = (b / Ns) * Ns * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[spad(base + r * Ns)] = v[q * R + r];
+    }
+    __syncthreads();
+}
+
+template <bool INV, class C>
+__device__ __forceinline__ void line_fft(C* buf, const LinePlan& plan, int t, const C* __restrict__ tw,
+                                         int twstride) {
+    C v[FFT_E];
+    int Ns = 1;
+    for (int ps = 0; ps < plan.npass; ++ps) {
+        const int R = plan.radix[ps];
+        if (R == 16) stockham_pass<16, INV>(buf, plan.N, Ns, t, plan.nthr, tw, twstride, v);
+        else if (R == 8) stockham_pass<8, INV>(buf, plan.N, Ns, t, plan.nthr, tw, twstride, v);
+        else if (R == 4) stockham_pass<4, INV>(buf, plan.N, Ns, t, plan.nthr, tw, twstride, v);
+        else stockham_pass<2, INV>(buf, plan.N, Ns, t, plan.nthr, tw, twstride, v);
+        Ns *= R;
+    }
+}
+
+
+}  // namespace gofd

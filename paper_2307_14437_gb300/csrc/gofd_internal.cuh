@@ -135,6 +135,9 @@ struct gofd_problem {
     int pitch0 = 0;            // complex entries per spectrum row along axis 0 (>= P/2+1)
     gofd::DevBuf specA;        // complex, n_{d-1}..n_1 rows x pitch0 (largest precision)
     gofd::DevBuf specB;        // 3D only: n x P x pitch0 complex
+    gofd::DevBuf specT;        // 2D: transposed half spectrum, (P/2+1) x ldT complex
+    int ldT = 0;               // 2D: leading dimension of specT (n rounded up to 16)
+    gofd::DevBuf lamT64, lamT32;  // 2D: transposed scaled symbol
     gofd::DevBuf gridw;        // real [ngrid] (largest precision): A_FD v on the grid
     gofd::DevBuf xin;          // real [nint+1] compacted input (largest precision)
     gofd::DevBuf yout;         // real [nint]
@@ -158,6 +161,9 @@ void setup_coefficients(gofd_problem* p);
 
 // FFT-convolution apply (apply.cu)
 void setup_apply(gofd_problem* p);
+void setup_apply_2d(gofd_problem* p);
+void afd_2d_f32(gofd_problem* p, const float* x, const float* vgrid, float* wgrid, cudaStream_t st);
+void afd_2d_f64(gofd_problem* p, const double* x, const double* vgrid, double* wgrid, cudaStream_t st);
 void apply_interior(gofd_problem* p, bool fp64, const void* x, void* y, cudaStream_t st);
 void afd_apply_grid(gofd_problem* p, bool fp64, const void* v, void* w, cudaStream_t st);
 void afd_apply_noalloc(int d, int n, const float* lam, const float* v, float* w, cudaStream_t st);

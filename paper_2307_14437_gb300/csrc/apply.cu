@@ -211,17 +211,31 @@ template <class Real, int TPR>
 __global__ void scatter_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
                                const Real* __restrict__ val, const Real* __restrict__ w, int64_t nint,
                                Real* __restrict__ y, Real scale) {
-    // the loop is uniform across each warp so that every lane reaches the shuffles
+    // the loop is uniform across each warp so that every lane reaches the
+    // shuffles; four independent partial sums keep several loads in flight
+    // (the summation order is fixed, so results are deterministic)
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
     const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int lane = threadIdx.x % TPR;
     for (int64_t t0 = gid - (threadIdx.x & 31); t0 < nint * TPR; t0 += nthreads) {
         const int64_t i = (t0 + (threadIdx.x & 31)) / TPR;
-        Real acc = 0;
+        Real acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
         if (i < nint) {
             const int b = ptr[i], e = ptr[i + 1];
-            for (int a = b + lane; a < e; a += TPR) acc += val[a] * w[col[a]];
+            int a = b + lane;
+            for (; a + 3 * TPR < e; a += 4 * TPR) {
+                const int c0 = __ldg(&col[a]), c1 = __ldg(&col[a + TPR]);
+                const int c2 = __ldg(&col[a + 2 * TPR]), c3 = __ldg(&col[a + 3 * TPR]);
+                const Real v0 = __ldg(&val[a]), v1 = __ldg(&val[a + TPR]);
+                const Real v2 = __ldg(&val[a + 2 * TPR]), v3 = __ldg(&val[a + 3 * TPR]);
+                acc0 += v0 * __ldg(&w[c0]);
+                acc1 += v1 * __ldg(&w[c1]);
+                acc2 += v2 * __ldg(&w[c2]);
+                acc3 += v3 * __ldg(&w[c3]);
+            }
+            for (; a < e; a += TPR) acc0 += __ldg(&val[a]) * __ldg(&w[__ldg(&col[a])]);
         }
+        Real acc = (acc0 + acc1) + (acc2 + acc3);
 #pragma unroll
         for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, TPR);
         if (lane == 0 && i < nint) y[i] = acc * scale;

@@ -24,15 +24,25 @@
 
 namespace gofd {
 
+// Per-group barrier.  The ids are spelled out so that the compiler reserves
+// only ids 1..4 (dynamic ids make it reserve all 16 and halve residency).
 __device__ __forceinline__ void group_sync(int g, int nthr) {
-    if (nthr >= 32) asm volatile("bar.sync %0, %1;" ::"r"(g + 1), "r"(nthr) : "memory");
-    else __syncthreads();
+    if (nthr < 32) {
+        __syncthreads();
+        return;
+    }
+    switch (g) {
+        case 0: asm volatile("bar.sync 1, %0;" ::"r"(nthr) : "memory"); break;
+        case 1: asm volatile("bar.sync 2, %0;" ::"r"(nthr) : "memory"); break;
+        case 2: asm volatile("bar.sync 3, %0;" ::"r"(nthr) : "memory"); break;
+        default: asm volatile("bar.sync 4, %0;" ::"r"(nthr) : "memory"); break;
+    }
 }
 
-template <int R, bool INV, class C>
-__device__ __forceinline__ void reg_pass(C (&v)[FFT_E], int t, int nthr, int N, int Ns, const C* __restrict__ tw,
+template <int R, bool INV, int E, class C>
+__device__ __forceinline__ void reg_pass(C (&v)[E], int t, int nthr, int N, int Ns, const C* __restrict__ tw,
                                          int twstride) {
-    constexpr int Q = FFT_E / R;
+    constexpr int Q = E / R;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int b = t + q * nthr;
@@ -50,9 +60,9 @@ __device__ __forceinline__ void reg_pass(C (&v)[FFT_E], int t, int nthr, int N, 
     }
 }
 
-template <int R, class C>
-__device__ __forceinline__ void reg_store(C* buf, const C (&v)[FFT_E], int t, int nthr, int Ns) {
-    constexpr int Q = FFT_E / R;
+template <int R, int E, class C>
+__device__ __forceinline__ void reg_store(C* buf, const C (&v)[E], int t, int nthr, int Ns) {
+    constexpr int Q = E / R;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
         const int b = t + q * nthr;
@@ -62,9 +72,9 @@ __device__ __forceinline__ void reg_store(C* buf, const C (&v)[FFT_E], int t, in
     }
 }
 
-template <int R, class C>
-__device__ __forceinline__ void reg_load(const C* buf, C (&v)[FFT_E], int t, int nthr, int N) {
-    constexpr int Q = FFT_E / R;
+template <int R, int E, class C>
+__device__ __forceinline__ void reg_load(const C* buf, C (&v)[E], int t, int nthr, int N) {
+    constexpr int Q = E / R;
     const int S = N / R;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
@@ -77,9 +87,9 @@ __device__ __forceinline__ void reg_load(const C* buf, C (&v)[FFT_E], int t, int
 // Visit the thread's elements of a pass of radix R: f(i, pos) with i the
 // register index (a compile-time constant after unrolling) and pos = b + r N/R
 // the line position.  Dispatching on R keeps v[] in registers.
-template <int R, class F>
+template <int R, int E, class F>
 __device__ __forceinline__ void each_elem_r(int t, int nthr, int N, F&& f) {
-    constexpr int Q = FFT_E / R;
+    constexpr int Q = E / R;
     const int S = N / R;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
@@ -91,37 +101,36 @@ __device__ __forceinline__ void each_elem_r(int t, int nthr, int N, F&& f) {
 // ---------------------------------------------------------------------------
 // compile-time pass plans: radix 16 passes first, then the remainder
 // ---------------------------------------------------------------------------
-__host__ __device__ constexpr int ct_full16(int N) { int f = 0; while (N >= 16) { N /= 16; ++f; } return f; }
-__host__ __device__ constexpr int ct_rem(int N) { while (N >= 16) N /= 16; return N; }
-__host__ __device__ constexpr int ct_npass(int N) { return ct_full16(N) + (ct_rem(N) > 1 ? 1 : 0); }
-__host__ __device__ constexpr int ct_radix(int N, int i) { return i < ct_full16(N) ? 16 : ct_rem(N); }
+// E = elements per thread = the largest radix; passes of radix E first, then
+// the remainder.
+__host__ __device__ constexpr int ct_full(int N, int E) { int f = 0; while (N >= E) { N /= E; ++f; } return f; }
+__host__ __device__ constexpr int ct_rem(int N, int E) { while (N >= E) N /= E; return N; }
+__host__ __device__ constexpr int ct_npass(int N, int E) { return ct_full(N, E) + (ct_rem(N, E) > 1 ? 1 : 0); }
+__host__ __device__ constexpr int ct_radix(int N, int E, int i) { return i < ct_full(N, E) ? E : ct_rem(N, E); }
 // REV: the same radices in reverse order (the inverse column transform starts
 // with the forward transform's last radix so the data stays in registers)
-__host__ __device__ constexpr int ct_radix_o(int N, bool rev, int i) {
-    return rev ? ct_radix(N, ct_npass(N) - 1 - i) : ct_radix(N, i);
+__host__ __device__ constexpr int ct_radix_o(int N, int E, bool rev, int i) {
+    return rev ? ct_radix(N, E, ct_npass(N, E) - 1 - i) : ct_radix(N, E, i);
 }
+template <int N, int E, bool REV>
+__host__ __device__ constexpr int ct_last() { return ct_radix_o(N, E, REV, ct_npass(N, E) - 1); }
 
-template <bool INV, int N, bool REV, int PS = 0, int NS = 1, class C>
-__device__ __forceinline__ void fft_ct(C (&v)[FFT_E], C* buf, int t, int g, const C* __restrict__ tw, int tws) {
-    if constexpr (PS < ct_npass(N)) {
-        constexpr int R = ct_radix_o(N, REV, PS);
-        constexpr int NTHR = N / FFT_E;
+template <bool INV, int N, int E, bool REV, int PS = 0, int NS = 1, class C>
+__device__ __forceinline__ void fft_ct(C (&v)[E], C* buf, int t, int g, const C* __restrict__ tw, int tws) {
+    if constexpr (PS < ct_npass(N, E)) {
+        constexpr int R = ct_radix_o(N, E, REV, PS);
+        constexpr int NTHR = N / E;
         if constexpr (PS > 0) {
-            constexpr int RP = ct_radix_o(N, REV, PS - 1);
+            constexpr int RP = ct_radix_o(N, E, REV, PS - 1);
             reg_store<RP>(buf, v, t, NTHR, NS / RP);
             group_sync(g, NTHR);
             reg_load<R>(buf, v, t, NTHR, N);
             group_sync(g, NTHR);
         }
         reg_pass<R, INV>(v, t, NTHR, N, NS, tw, tws);
-        fft_ct<INV, N, REV, PS + 1, NS * R>(v, buf, t, g, tw, tws);
+        fft_ct<INV, N, E, REV, PS + 1, NS * R>(v, buf, t, g, tw, tws);
     }
 }
-
-template <int N, bool REV>
-__host__ __device__ constexpr int ct_first(int) { return ct_radix_o(N, REV, 0); }
-template <int N, bool REV>
-__host__ __device__ constexpr int ct_last() { return ct_radix_o(N, REV, ct_npass(N) - 1); }
 
 // ---------------------------------------------------------------------------
 // gather of one grid sample: sum over the owner simplex's slots (ELL row e)
@@ -163,7 +172,7 @@ __device__ __forceinline__ Real sample(int k, const Runs& rs, const int32_t* __r
 // ---------------------------------------------------------------------------
 // kernel 1: gather + real FFT per grid line, transposed half spectrum out
 // ---------------------------------------------------------------------------
-template <class Real, int DP1, int N>
+template <class Real, int DP1, int N, int E>
 __global__ void __launch_bounds__(512) row_fwd_t_kernel(
     const Real* __restrict__ x, const int32_t* __restrict__ iidx, const Real* __restrict__ w, int64_t nloc,
     const int32_t* __restrict__ run_ptr, const int32_t* __restrict__ run_k0, const int32_t* __restrict__ run_len,
@@ -172,7 +181,7 @@ __global__ void __launch_bounds__(512) row_fwd_t_kernel(
     using C = typename Cplx<Real>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* sm = reinterpret_cast<C*>(smem_raw);
-    constexpr int nthr = N / FFT_E;
+    constexpr int nthr = N / E;
     const int g = threadIdx.x / nthr, t = threadIdx.x % nthr;
     const int line = blockIdx.x * lpc + g;
     const bool active = line < nlines;
@@ -192,30 +201,64 @@ __global__ void __launch_bounds__(512) row_fwd_t_kernel(
             }
     }
     // pass-0 inputs z[m] = (v[2m], v[2m+1]) gathered straight into registers
-    C v[FFT_E];
-    each_elem_r<ct_radix_o(N, false, 0)>(t, nthr, N, [&](int i, int m) {
-        const int k = 2 * m;
-        Real a0 = 0, a1 = 0;
-        if (active && k < n) {
-            if (vgrid) {
-                a0 = vgrid[(int64_t)line * n + k];
-                if (k + 1 < n) a1 = vgrid[(int64_t)line * n + k + 1];
-            } else {
-                a0 = sample<Real, DP1>(k, rs, run_k0, run_len, run_e0, x, iidx, w, nloc);
-                if (k + 1 < n) a1 = sample<Real, DP1>(k + 1, rs, run_k0, run_len, run_e0, x, iidx, w, nloc);
+    C v[E];
+    if (vgrid || rs.n > 2) {
+        each_elem_r<ct_radix_o(N, E, false, 0), E>(t, nthr, N, [&](int i, int m) {
+            const int k = 2 * m;
+            Real a0 = 0, a1 = 0;
+            if (active && k < n) {
+                if (vgrid) {
+                    a0 = vgrid[(int64_t)line * n + k];
+                    if (k + 1 < n) a1 = vgrid[(int64_t)line * n + k + 1];
+                } else {
+                    a0 = sample<Real, DP1>(k, rs, run_k0, run_len, run_e0, x, iidx, w, nloc);
+                    if (k + 1 < n) a1 = sample<Real, DP1>(k + 1, rs, run_k0, run_len, run_e0, x, iidx, w, nloc);
+                }
             }
-        }
-        v[i].x = a0;
-        v[i].y = a1;
-    });
-    fft_ct<false, N, false>(v, buf, t, g, tw, 2);
+            v[i].x = a0;
+            v[i].y = a1;
+        });
+    } else if (rs.n > 0) {
+        // at most two runs on this line: ELL rows by selects, every load
+        // issued without branches so that many are in flight at once
+        each_elem_r<ct_radix_o(N, E, false, 0), E>(t, nthr, N, [&](int i, int m) {
+            const int k = 2 * m;
+            if (k >= n) {
+                v[i].x = 0;
+                v[i].y = 0;
+                return;
+            }
+            int ea = -1, eb = -1;
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                if (r < rs.n) {
+                    const int lo = rs.k0[r], hi = rs.k0[r] + rs.len[r];
+                    ea = (k >= lo && k < hi) ? rs.e0[r] + (k - lo) : ea;
+                    eb = (k + 1 >= lo && k + 1 < hi) ? rs.e0[r] + (k + 1 - lo) : eb;
+                }
+            }
+            const int64_t ca = ea >= 0 ? ea : 0, cb = eb >= 0 ? eb : 0;
+            Real a0 = 0, a1 = 0;
+#pragma unroll
+            for (int s = 0; s < DP1; ++s) {
+                a0 += __ldg(&w[s * nloc + ca]) * __ldg(&x[__ldg(&iidx[s * nloc + ca])]);
+                a1 += __ldg(&w[s * nloc + cb]) * __ldg(&x[__ldg(&iidx[s * nloc + cb])]);
+            }
+            v[i].x = ea >= 0 ? a0 : (Real)0;
+            v[i].y = eb >= 0 ? a1 : (Real)0;
+        });
+    } else {
+#pragma unroll
+        for (int i = 0; i < E; ++i) v[i] = cmk<C>(0.0, 0.0);
+    }
+    fft_ct<false, N, E, false>(v, buf, t, g, tw, 2);
     {
-        constexpr int RL = ct_last<N, false>();
+        constexpr int RL = ct_last<N, E, false>();
         reg_store<RL>(buf, v, t, nthr, N / RL);
     }
     __syncthreads();
     // X[k] = (Z_k + conj Z_{N-k})/2 - i/2 W_P^k (Z_k - conj Z_{N-k}),  k = 0..N
-    constexpr int JMAX = FFT_E + 1;
+    constexpr int JMAX = E + 1;
     C X[JMAX];
 #pragma unroll
     for (int j = 0; j < JMAX; ++j) {
@@ -253,37 +296,37 @@ __global__ void __launch_bounds__(512) row_fwd_t_kernel(
 // ---------------------------------------------------------------------------
 // kernel 2: per spectrum column: FFT (n nonzero rows), symbol, inverse FFT
 // ---------------------------------------------------------------------------
-template <class Real, int N>
-__global__ void __launch_bounds__(512) col_conv_t_kernel(typename Cplx<Real>::T* __restrict__ specT, int ld, int n,
+template <class Real, int N, int E>
+__global__ void __launch_bounds__(N / E > 256 ? N / E : 256) col_conv_t_kernel(typename Cplx<Real>::T* __restrict__ specT, int ld, int n,
                                                        int H, const typename Cplx<Real>::T* __restrict__ tw,
                                                        const Real* __restrict__ lamT) {
     using C = typename Cplx<Real>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* sm = reinterpret_cast<C*>(smem_raw);
-    constexpr int nthr = N / FFT_E;
+    constexpr int nthr = N / E;
     const int G = blockDim.x / nthr;
     const int g = threadIdx.x / nthr, t = threadIdx.x % nthr;
     const int col = blockIdx.x * G + g;
     const bool active = col < H;
     C* buf = sm + g * spad_len(N);
     C* column = specT + (int64_t)(active ? col : 0) * ld;
-    C v[FFT_E];
-    each_elem_r<ct_radix_o(N, false, 0)>(t, nthr, N, [&](int i, int row) {
+    C v[E];
+    each_elem_r<ct_radix_o(N, E, false, 0), E>(t, nthr, N, [&](int i, int row) {
         v[i] = (active && row < n) ? column[row] : cmk<C>(0.0, 0.0);
     });
-    fft_ct<false, N, false>(v, buf, t, g, tw, 1);
+    fft_ct<false, N, E, false>(v, buf, t, g, tw, 1);
     {
         // multiply by the (pre-scaled) symbol: row k_x1 folded to [0, N/2]
         const Real* lc = lamT + (int64_t)(active ? col : 0) * H;
-        each_elem_r<ct_last<N, false>()>(t, nthr, N, [&](int i, int row) {
+        each_elem_r<ct_last<N, E, false>(), E>(t, nthr, N, [&](int i, int row) {
             const int fr = row <= N / 2 ? row : N - row;
             const Real l = __ldg(&lc[fr]);
             v[i].x *= l;
             v[i].y *= l;
         });
     }
-    fft_ct<true, N, true>(v, buf, t, g, tw, 1);
-    each_elem_r<ct_last<N, true>()>(t, nthr, N, [&](int i, int row) {
+    fft_ct<true, N, E, true>(v, buf, t, g, tw, 1);
+    each_elem_r<ct_last<N, E, true>(), E>(t, nthr, N, [&](int i, int row) {
         if (active && row < n) column[row] = v[i];
     });
 }
@@ -291,14 +334,14 @@ __global__ void __launch_bounds__(512) col_conv_t_kernel(typename Cplx<Real>::T*
 // ---------------------------------------------------------------------------
 // kernel 3: transposed tile in, inverse real FFT per line, n samples out
 // ---------------------------------------------------------------------------
-template <class Real, int N>
+template <class Real, int N, int E>
 __global__ void __launch_bounds__(512) row_inv_t_kernel(const typename Cplx<Real>::T* __restrict__ specT, int ld,
                                                       int nlines, int n, const typename Cplx<Real>::T* __restrict__ tw,
                                                       Real* __restrict__ wgrid, int lpc) {
     using C = typename Cplx<Real>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* sm = reinterpret_cast<C*>(smem_raw);
-    constexpr int nthr = N / FFT_E;
+    constexpr int nthr = N / E;
     const int msk = lpc - 1;
     const int total = (N + 1) * lpc;
     for (int i = threadIdx.x; i < total; i += blockDim.x) {
@@ -310,9 +353,9 @@ __global__ void __launch_bounds__(512) row_inv_t_kernel(const typename Cplx<Real
     const int g = threadIdx.x / nthr, t = threadIdx.x % nthr;
     const int line = blockIdx.x * lpc + g;
     const bool active = line < nlines;
-    C v[FFT_E];
+    C v[E];
     // Z'_k = (X_k + conj X_{N-k}) + i W_P^{-k} (X_k - conj X_{N-k})
-    each_elem_r<ct_radix_o(N, false, 0)>(t, nthr, N, [&](int i, int k) {
+    each_elem_r<ct_radix_o(N, E, false, 0), E>(t, nthr, N, [&](int i, int k) {
         const int kc = N - k;
         const C xk = sm[k * lpc + (g ^ (k & msk))];
         const C xc = cconj(sm[kc * lpc + (g ^ (kc & msk))]);
@@ -325,10 +368,10 @@ __global__ void __launch_bounds__(512) row_inv_t_kernel(const typename Cplx<Real
     });
     __syncthreads();
     C* buf = sm + g * spad_len(N);
-    fft_ct<true, N, false>(v, buf, t, g, tw, 2);
+    fft_ct<true, N, E, false>(v, buf, t, g, tw, 2);
     if (!active) return;
     Real* wl = wgrid + (int64_t)line * n;
-    each_elem_r<ct_last<N, false>()>(t, nthr, N, [&](int i, int m) {
+    each_elem_r<ct_last<N, E, false>(), E>(t, nthr, N, [&](int i, int m) {
         const int k = 2 * m;
         if (k < n) wl[k] = v[i].x;
         if (k + 1 < n) wl[k + 1] = v[i].y;

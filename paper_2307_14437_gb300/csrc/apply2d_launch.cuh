@@ -11,23 +11,28 @@ namespace {
 using Real = REAL;
 using C = Cplx<Real>::T;
 
-int lines_per_cta(int nthr) { return std::max(1, std::min(8, 256 / nthr)); }
-int cols_per_cta(int nthr) { return std::max(1, std::min(8, 256 / nthr)); }
+// elements per thread (largest radix) of the row and column transforms
+constexpr int ct_elems_row(int N) { return N >= 4096 ? 16 : 8; }
+constexpr int ct_elems_col(int N) { return N >= 4096 ? 16 : 8; }
+int lines_per_cta(int nthr) { return std::max(1, std::min(4, 512 / nthr)); }
+int cols_per_cta(int nthr) { return std::max(1, std::min(4, 256 / nthr)); }
 size_t row_smem(int N, int lpc) { return sizeof(C) * std::max<size_t>((size_t)spad_len(N) * lpc, (size_t)(N + 1) * lpc); }
 size_t col_smem(int N, int G) { return sizeof(C) * (size_t)spad_len(N) * G; }
 
 template <int N>
 void set_attrs(int limit) {
-    GOFD_CUDA_TRY(cudaFuncSetAttribute(row_fwd_t_kernel<Real, 3, N / 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
-    GOFD_CUDA_TRY(cudaFuncSetAttribute(row_inv_t_kernel<Real, N / 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
-    GOFD_CUDA_TRY(cudaFuncSetAttribute(col_conv_t_kernel<Real, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    constexpr int ER = ct_elems_row(N / 2), EC = ct_elems_col(N);
+    GOFD_CUDA_TRY(cudaFuncSetAttribute(row_fwd_t_kernel<Real, 3, N / 2, ER>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    GOFD_CUDA_TRY(cudaFuncSetAttribute(row_inv_t_kernel<Real, N / 2, ER>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    GOFD_CUDA_TRY(cudaFuncSetAttribute(col_conv_t_kernel<Real, N, EC>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
 }
 
 // P = circulant length (column lines), rows use P/2
 template <int P>
 void run(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, cudaStream_t st) {
     constexpr int NR = P / 2, NC = P;
-    constexpr int tr = NR / FFT_E, tc = NC / FFT_E;
+    constexpr int ER = ct_elems_row(NR), EC = ct_elems_col(NC);
+    constexpr int tr = NR / ER, tc = NC / EC;
     const int lpc = lines_per_cta(tr), G = cols_per_cta(tc);
     const int n = p->n[0], H = P / 2 + 1, nlines = (int)p->nlines;
     const C* tw = reinterpret_cast<const C*>(sizeof(Real) == 4 ? p->tw32.ptr : p->tw64.ptr);
@@ -35,15 +40,15 @@ void run(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, cudaStr
     const Real* w = reinterpret_cast<const Real*>(sizeof(Real) == 4 ? p->ell_w32.ptr : p->ell_w64.ptr);
     C* S = p->specT.as<C>();
     const unsigned rblocks = (unsigned)((nlines + lpc - 1) / lpc);
-    row_fwd_t_kernel<Real, 3, NR><<<rblocks, lpc * tr, row_smem(NR, lpc), st>>>(
+    row_fwd_t_kernel<Real, 3, NR, ER><<<rblocks, lpc * tr, row_smem(NR, lpc), st>>>(
         x, p->ell_iidx.as<int32_t>(), w, p->nloc, p->line_run_ptr.as<int32_t>(), p->run_k0.as<int32_t>(),
         p->run_len.as<int32_t>(), p->run_e0.as<int32_t>(), vgrid, nlines, n, tw, S, p->ldT, lpc);
     GOFD_CHECK_LAUNCH();
     mark_stage(st, "gather_row_fft");
-    col_conv_t_kernel<Real, NC><<<(unsigned)((H + G - 1) / G), G * tc, col_smem(NC, G), st>>>(S, p->ldT, n, H, tw, lamT);
+    col_conv_t_kernel<Real, NC, EC><<<(unsigned)((H + G - 1) / G), G * tc, col_smem(NC, G), st>>>(S, p->ldT, n, H, tw, lamT);
     GOFD_CHECK_LAUNCH();
     mark_stage(st, "col_fft_conv");
-    row_inv_t_kernel<Real, NR><<<rblocks, lpc * tr, row_smem(NR, lpc), st>>>(S, p->ldT, nlines, n, tw, wgrid, lpc);
+    row_inv_t_kernel<Real, NR, ER><<<rblocks, lpc * tr, row_smem(NR, lpc), st>>>(S, p->ldT, nlines, n, tw, wgrid, lpc);
     GOFD_CHECK_LAUNCH();
     mark_stage(st, "row_ifft");
 }
@@ -72,7 +77,7 @@ void AFD2D_ATTR_FN(int limit, int P, size_t* need) {
 #undef ATTR
         default: fail(GOFD_E_GRID, "unsupported circulant length");
     }
-    const int tr = P / 2 / FFT_E, tc = P / FFT_E;
+    const int tr = P / 2 / ct_elems_row(P / 2), tc = P / ct_elems_col(P);
     *need = std::max(row_smem(P / 2, lines_per_cta(tr)), col_smem(P, cols_per_cta(tc)));
 }
 

@@ -87,6 +87,7 @@ typedef struct {
     uint64_t wait_budget_cycles; /* bound on every device-side spin wait (clock64 cycles); 0 = 2e9                    */
     double inner_tol;          /* mixed mode: relative reduction of each inner FP32 PCG; 0 = 1e-4                   */
     int check_every;           /* iterations between host convergence checks; 0 = 8                                  */
+    int ordering;              /* IC unknown order: 0 natural vertex order, 1 multicolour (shorter dependency chains)  */
 } gofd_options;
 
 typedef struct {
@@ -117,6 +118,7 @@ typedef struct {
     double alpha, s, h;
     double a_h, min_colsum;
     int64_t precond_nnz;       /* stored entries of the IC factor (0 without preconditioner) */
+    int precond_levels;        /* dependency levels of the IC factor (launches per triangular solve) */
     double ic_shift;
     double t_setup_ms;
 } gofd_info;
@@ -223,6 +225,16 @@ gofd_status gofd_export_transfer(const gofd_problem* p, int32_t* owner,
  */
 gofd_status gofd_export_vertex_data(const gofd_problem* p, int32_t* interior_index,
                                     double* colsum);
+
+/*
+ * gofd_export_precond -- the incomplete Cholesky factor L (L L^T ~ P A_h^(k) P^T,
+ * Section 3.3) copied to host: perm (n_interior int32, perm[new] = old interior
+ * index), lptr (n_interior+1 int32), lcol/lval (precond_nnz entries; columns
+ * ascending, the diagonal last in each row).  Any pointer may be NULL.
+ * GOFD_E_ARG if the problem was built without a preconditioner.
+ */
+gofd_status gofd_export_precond(const gofd_problem* p, int32_t* perm, int32_t* lptr, int32_t* lcol,
+                                double* lval);
 
 /* gofd_get_coefficients -- T_p for p in [0,n)^d (FP64, axis 0 fastest), to host. */
 gofd_status gofd_get_coefficients(const gofd_problem* p, double* T);

@@ -279,7 +279,11 @@ def barycentric_exact(verts, simp_e, x):
 
 
 def barycentric_float(verts, simp, owner_elems, X):
-    """Float barycentric coordinates (for large cases), clamped to [0,1]."""
+    """Float barycentric coordinates (for large cases), clamped to [0,1].
+
+    A coordinate is exactly 0 when the node lies on the facet opposite that
+    vertex (exact orientation test), as the exactly rounded value is.
+    """
     V = verts[simp[owner_elems]]
     full, _ = _orient_float_with_bound(V)
     d = verts.shape[1]
@@ -287,8 +291,12 @@ def barycentric_float(verts, simp, owner_elems, X):
     for i in range(d + 1):
         pts = V.copy()
         pts[:, i, :] = X
-        di, _ = _orient_float_with_bound(pts)
-        out[i] = np.clip(di / full, 0.0, 1.0)
+        di, bnd = _orient_float_with_bound(pts)
+        wi = np.clip(di / full, 0.0, 1.0)
+        for r in np.nonzero(np.abs(di) <= bnd)[0]:
+            if orient_exact(pts[r]) == 0:
+                wi[r] = 0.0
+        out[i] = wi
     return out
 
 
@@ -763,9 +771,28 @@ def stencil_matrix(prob: Problem, pattern: int) -> sp.csr_matrix:
 
 
 def preconditioner_matrix(prob: Problem, pattern: int) -> sp.csr_matrix:
-    """A_h^{(k)} = I^T A_FD^{(k)} I restricted to the interior block  ((Ah-4))."""
-    Ii = prob.I[:, prob.interior]
-    return (Ii.T @ stencil_matrix(prob, pattern) @ Ii).tocsr()
+    """A_h^{(k)} = I^T A_FD^{(k)} I restricted to the interior block  ((Ah-4)).
+
+    Reading R13: the pattern is structural -- (i, j) is stored iff some grid
+    node k and stencil offset delta give a product phi_i(x_k) T_delta
+    phi_j(x_{k+delta}) of nonzero factors; an entry whose contributions cancel
+    stays in the pattern with its (possibly zero) value.  Zero factors (a grid
+    node on a facet has a zero barycentric weight) contribute nothing.
+    """
+    Ii = prob.I[:, prob.interior].tocsr()
+    S = stencil_matrix(prob, pattern).tocsr()
+    Ib = Ii.copy()
+    Ib.data = (Ib.data != 0).astype(np.float64)
+    Ib.eliminate_zeros()
+    Sb = S.copy()
+    Sb.data = (Sb.data != 0).astype(np.float64)
+    Sb.eliminate_zeros()
+    struct = (Ib.T @ Sb @ Ib).tocsr()
+    struct.sort_indices()
+    num = (Ii.T @ S @ Ii).tocsr()
+    rows = np.repeat(np.arange(struct.shape[0]), np.diff(struct.indptr))
+    vals = np.asarray(num[rows, struct.indices]).ravel() if struct.nnz else np.zeros(0)
+    return sp.csr_matrix((vals, struct.indices.copy(), struct.indptr.copy()), shape=struct.shape)
 
 
 def ic_symbolic(A: sp.csr_matrix, level: int = 1):

@@ -25,7 +25,7 @@ RHS_GRID, RHS_VERTEX = 0, 1
 class Options(C.Structure):
     _fields_ = [("precond", C.c_int), ("ic_level", C.c_int), ("filon_M", C.c_int64),
                 ("richardson_levels", C.c_int), ("wait_budget_cycles", C.c_uint64),
-                ("inner_tol", C.c_double), ("check_every", C.c_int)]
+                ("inner_tol", C.c_double), ("check_every", C.c_int), ("ordering", C.c_int)]
 
 
 class SolveInfo(C.Structure):
@@ -40,7 +40,7 @@ class Info(C.Structure):
                 ("n_interior", C.c_int64), ("n_grid", C.c_int64), ("n_loc", C.c_int64), ("nnz_t", C.c_int64),
                 ("n_runs", C.c_int64), ("filon_M", C.c_int64), ("richardson_levels", C.c_int),
                 ("alpha", C.c_double), ("s", C.c_double), ("h", C.c_double), ("a_h", C.c_double),
-                ("min_colsum", C.c_double), ("precond_nnz", C.c_int64), ("ic_shift", C.c_double),
+                ("min_colsum", C.c_double), ("precond_nnz", C.c_int64), ("precond_levels", C.c_int), ("ic_shift", C.c_double),
                 ("t_setup_ms", C.c_double)]
 
 
@@ -59,6 +59,7 @@ EXPORTS = {
     "gofd_export_transfer": (C.c_int, [_P, _P, _P, _P]),
     "gofd_export_vertex_data": (C.c_int, [_P, _P, _P]),
     "gofd_get_coefficients": (C.c_int, [_P, _P]),
+    "gofd_export_precond": (C.c_int, [_P, _P, _P, _P, _P]),
     "gofd_get_symbol": (C.c_int, [_P, _P]),
     "gofd_afd_apply": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "gofd_afd_apply_noalloc": (C.c_int, [C.c_int, C.c_int, _P, _P, _P, _P]),

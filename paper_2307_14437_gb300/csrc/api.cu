@@ -257,6 +257,7 @@ gofd_status gofd_get_info(const gofd_problem* p, gofd_info* info) {
     info->a_h = p->a_h;
     info->min_colsum = p->min_colsum;
     info->precond_nnz = gofd::precond_nnz(p);
+    info->precond_levels = gofd::precond_levels(p);
     info->ic_shift = gofd::precond_shift(p);
     info->t_setup_ms = p->t_setup_ms;
     return GOFD_OK;
@@ -288,6 +289,12 @@ gofd_status gofd_export_vertex_data(const gofd_problem* p, int32_t* interior_ind
             for (int64_t v = 0; v < p->nv; ++v) colsum[v] = v2i[v] >= 0 ? cs[v2i[v]] : 0.0;
         }
     })
+}
+
+gofd_status gofd_export_precond(const gofd_problem* p, int32_t* perm, int32_t* lptr, int32_t* lcol, double* lval) {
+    if (!p) return GOFD_E_ARG;
+    gofd_problem* q = const_cast<gofd_problem*>(p);
+    GOFD_API_BODY(q, { gofd::precond_export(p, perm, lptr, lcol, lval); })
 }
 
 gofd_status gofd_get_coefficients(const gofd_problem* p, double* T) {

@@ -261,7 +261,8 @@ __global__ void ell_fill_kernel(const double* __restrict__ V, const int32_t* __r
         for (int i = 0; i <= D; ++i) {
             const double* pp[D + 1];
             for (int a = 0; a <= D; ++a) pp[a] = (a == i) ? x : pts[a];
-            double wi = orient_value<D>(pp) / DK;
+            // exactly 0 on the facet opposite vertex i (exact sign), else D_i / D_K
+            double wi = orient_sign<D>(pp) == 0 ? 0.0 : orient_value<D>(pp) / DK;
             wi = fmin(1.0, fmax(0.0, wi));
             vidx[(int64_t)i * nloc + e] = vv[i];
             w64[(int64_t)i * nloc + e] = wi;

@@ -47,7 +47,7 @@ class Problem:
 
     def __init__(self, vertices, simplices, alpha: float, h: float, box_lo, box_hi, *, precond: int = 0,
                  ic_level: int = 1, filon_M: int = 0, richardson_levels: int = 0, inner_tol: float = 0.0,
-                 check_every: int = 0, wait_budget_cycles: int = 0):
+                 check_every: int = 0, wait_budget_cycles: int = 0, ordering: int = 0):
         self._lib = N.load()
         v = np.ascontiguousarray(vertices, dtype=np.float64)
         s = np.ascontiguousarray(simplices, dtype=np.int32)
@@ -58,7 +58,7 @@ class Problem:
         hi = np.ascontiguousarray(box_hi, dtype=np.float64).reshape(-1)
         opt = N.Options(precond=precond, ic_level=ic_level, filon_M=filon_M,
                         richardson_levels=richardson_levels, wait_budget_cycles=wait_budget_cycles,
-                        inner_tol=inner_tol, check_every=check_every)
+                        inner_tol=inner_tol, check_every=check_every, ordering=ordering)
         h_ = C.c_void_p()
         st = self._lib.gofd_build(self.d, v.ctypes.data, v.shape[0], s.ctypes.data, s.shape[0], float(alpha),
                                   float(h), lo.ctypes.data, hi.ctypes.data, C.byref(opt), C.byref(h_))
@@ -113,6 +113,18 @@ class Problem:
         cs = np.empty(self.n_v, dtype=np.float64)
         self._check(self._lib.gofd_export_vertex_data(self._h, ii.ctypes.data, cs.ctypes.data))
         return ii, cs
+
+    def export_precond(self):
+        """(perm, lptr, lcol, lval) of the incomplete Cholesky factor (NumPy)."""
+        inf = self.info()
+        n, nnz = inf["n_interior"], inf["precond_nnz"]
+        perm = np.empty(n, dtype=np.int32)
+        lptr = np.empty(n + 1, dtype=np.int32)
+        lcol = np.empty(nnz, dtype=np.int32)
+        lval = np.empty(nnz, dtype=np.float64)
+        self._check(self._lib.gofd_export_precond(self._h, perm.ctypes.data, lptr.ctypes.data, lcol.ctypes.data,
+                                                  lval.ctypes.data))
+        return perm, lptr, lcol, lval
 
     def coefficients(self) -> np.ndarray:
         T = np.empty(self.n_grid, dtype=np.float64)

@@ -1,0 +1,105 @@
+"""Parity of the GPU incomplete Cholesky preconditioner (Section 3.3, (Ah-4))
+with the oracle's IC(1) under the same unknown order, and its effect on PCG."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import meshgen as mg
+from oracle import gofd as o
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2307_14437_gb300 import build_native
+    build_native.build()
+
+
+def _case(name):
+    if name == "disk":
+        v, s = mg.disk_ring_mesh(rings=8, seed=mg.seed_for(1, 4))
+        return 2, v, s, 25, 1.5, 2 ** 10
+    if name == "lshape":
+        v, s = mg.lshape_mesh(spacing=0.12, seed=mg.seed_for(2, 2))
+        return 2, v, s, 33, 1.0, 2 ** 10
+    if name == "ball":
+        v, s = mg.ball_shell_mesh(shells=3, seed=mg.seed_for(3, 3))
+        return 3, v, s, 11, 1.5, 2 ** 8
+    if name == "interval":
+        v, s = mg.interval_mesh(24, seed=mg.seed_for(0, 2))
+        return 1, v, s, 49, 1.2, 2 ** 12
+    raise KeyError(name)
+
+
+CASES = [("disk", 9), ("disk", 5), ("lshape", 9), ("ball", 27), ("ball", 7), ("interval", 3)]
+
+
+@pytest.mark.parametrize("ordering", [0, 1])
+@pytest.mark.parametrize("name,pattern", CASES)
+def test_ic1_factor_matches_oracle(name, pattern, ordering):
+    from paper_2307_14437_gb300 import Problem
+    d, v, s, n, alpha, M = _case(name)
+    lo, hi, h = mg.grid_box(d, n)
+    gp = Problem(v, s, alpha, h, lo, hi, filon_M=M, precond=pattern, ordering=ordering)
+    ref = o.build(d, v, s, alpha, h, lo, hi, M=M, exact_weights=False)
+    perm, lptr, lcol, lval = gp.export_precond()
+    assert sorted(perm.tolist()) == list(range(len(ref.interior)))
+    A = o.preconditioner_matrix(ref, pattern)
+    Ap = A[perm][:, perm].tocsr()
+    L, shift = o.ic_factor(Ap, 1)
+    assert gp.info()["ic_shift"] == shift
+    L = L.tocsr()
+    L.sort_indices()
+    assert np.array_equal(lptr, L.indptr.astype(np.int32))
+    assert np.array_equal(lcol, L.indices.astype(np.int32))
+    assert np.abs(lval - L.data).max() <= 1e-12 * np.abs(L.data).max()
+    gp.close()
+
+
+@pytest.mark.parametrize("ordering", [0, 1])
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_ic1_pcg_converges_with_fewer_iterations(mode, ordering):
+    from paper_2307_14437_gb300 import Problem
+    d, v, s, n, alpha, M = _case("disk")
+    lo, hi, h = mg.grid_box(d, n)
+    plain = Problem(v, s, alpha, h, lo, hi, filon_M=M, check_every=1)
+    pc = Problem(v, s, alpha, h, lo, hi, filon_M=M, precond=9, ordering=ordering, check_every=1)
+    ref = o.build(d, v, s, alpha, h, lo, hi, M=M, exact_weights=False)
+    f = torch.ones(pc.n_grid, dtype=torch.float64, device="cuda")
+    u0, i0 = plain.solve(f, mode=mode, tol=1e-10)
+    u1, i1 = pc.solve(f, mode=mode, tol=1e-10)
+    b = o.rhs_grid(ref, np.ones(ref.n_grid))
+    res = np.linalg.norm(b - o.stiffness_apply(ref, u1.cpu().numpy())) / np.linalg.norm(b)
+    assert res < 2e-10
+    assert i1["inner_iters"] < i0["inner_iters"], (i0, i1)
+    plain.close()
+    pc.close()
+
+
+def test_precond_iterations_close_to_oracle_pcg():
+    # the oracle's IC(1)-PCG with the same order needs (almost) the same count
+    from paper_2307_14437_gb300 import Problem
+    d, v, s, n, alpha, M = _case("lshape")
+    lo, hi, h = mg.grid_box(d, n)
+    gp = Problem(v, s, alpha, h, lo, hi, filon_M=M, precond=9, ordering=1, check_every=1)
+    ref = o.build(d, v, s, alpha, h, lo, hi, M=M, exact_weights=False)
+    perm, *_ = gp.export_precond()
+    b = o.rhs_grid(ref, np.ones(ref.n_grid))
+    _, oi = o.pcg_ic(ref, b, pattern=9, tol=1e-10, perm=perm)
+    _, gi = gp.solve(torch.ones(gp.n_grid, dtype=torch.float64, device="cuda"), mode="fp64", tol=1e-10)
+    assert abs(gi["inner_iters"] - oi["iters"]) <= 2, (gi, oi)
+    gp.close()
+
+
+def test_bad_pattern_is_rejected():
+    from paper_2307_14437_gb300 import GofdError, Problem
+    d, v, s, n, alpha, M = _case("disk")
+    lo, hi, h = mg.grid_box(d, n)
+    with pytest.raises(GofdError) as e:
+        Problem(v, s, alpha, h, lo, hi, filon_M=M, precond=27)
+    assert e.value.code == "GOFD_E_ARG"

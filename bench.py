@@ -51,10 +51,25 @@ def b_alg(d, n_loc, n_v, n_grid, P, b):
             + b * (P // 2 + 1) ** d)                   # symbol
 
 
-def workload(alpha=1.0):
+WORKLOADS = {
+    "lshape1024": "2D L-shape [-1,1]^2\\[0,1]^2, 6.05e4 vertices, 1024^2 grid in a 2048^2 circulant, alpha=1",
+    "graded2048": "2D graded unit disk, 2.1e5 vertices, 2048^2 grid in a 4096^2 circulant, alpha=1.2",
+    "ball256": "3D unit ball, 1.3e5 vertices, 256^3 grid in a 512^3 circulant, alpha=1.5",
+}
+
+
+def workload(name="lshape1024", alpha=None):
+    if name == "graded2048":
+        lo, hi, h = mg.grid_box(2, 2048)
+        v, s = mg.graded_disk_mesh(h, seed=mg.seed_for(4))
+        return v, s, 1.2 if alpha is None else alpha, h, lo, hi
+    if name == "ball256":
+        v, s = mg.ball_shell_mesh(seed=mg.seed_for(3))
+        lo, hi, h = mg.grid_box(3, 256)
+        return v, s, 1.5 if alpha is None else alpha, h, lo, hi
     v, s = mg.lshape_mesh(seed=mg.seed_for(2))
     lo, hi, h = mg.grid_box(2, N_GRID)
-    return v, s, alpha, h, lo, hi
+    return v, s, 1.0 if alpha is None else alpha, h, lo, hi
 
 
 class Clocks:
@@ -169,12 +184,12 @@ def run_gofd(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    v, s, alpha, h, lo, hi = workload()
+    v, s, alpha, h, lo, hi = workload(args.workload)
     t0 = time.perf_counter()
     prob = Problem(v, s, alpha, h, lo, hi)
     t_setup = time.perf_counter() - t0
     inf = prob.info()
-    d, n_loc, n_v, nint, P = 2, inf["n_loc"], inf["n_v"], inf["n_interior"], inf["P"]
+    d, n_loc, n_v, nint, P = inf["d"], inf["n_loc"], inf["n_v"], inf["n_interior"], inf["P"]
     B32 = b_alg(d, n_loc, n_v, inf["n_grid"], P, 4)
 
     gen = torch.Generator(device="cpu").manual_seed(5)
@@ -223,11 +238,15 @@ def run_gofd(args):
     H = P // 2 + 1
     n = inf["n"][0]
     # algorithmic bytes per launch of each kernel (FP32)
+    nl = n ** (d - 1)
     kbytes = {
-        "gather_row_fft": (d + 1) * 8 * n_loc + 4 * nint + 8 * n * H,
+        "gather_row_fft": (d + 1) * 8 * n_loc + 4 * nint + 8 * nl * H,
         "col_fft_conv": 8 * n * H * 2 + 4 * H * H,
-        "row_ifft": 8 * n * H + 4 * n * n,
+        "row_ifft": 8 * nl * H + 4 * n ** d,
         "scatter": inf["nnz_t"] * 8 + 4 * (nint + 1) + 4 * inf["nnz_t"] + 4 * nint,
+        "col_fft_fwd_axis1": 8 * nl * H + 8 * n * P * H,
+        "col_fft_conv_axis2": 2 * 8 * n * P * H + 4 * H ** 3,
+        "col_fft_inv_axis1": 8 * n * P * H + 8 * nl * H,
     }
     pk = peaks()
     hbm = pk.get("hbm_gbs", 6800.0)
@@ -259,7 +278,7 @@ def run_gofd(args):
 
     # time to relative residual 1e-8: mixed refinement vs plain FP64 PCG
     pcg = {}
-    if not args.no_pcg:
+    if not args.no_pcg and args.workload == "lshape1024":
         for a in ALPHAS:
             pa = prob if a == alpha else Problem(v, s, a, h, lo, hi)
             f = torch.ones(pa.n_grid, dtype=torch.float64, device=dev)
@@ -276,6 +295,23 @@ def run_gofd(args):
             pcg[f"alpha={a}"] = row
             if pa is not prob:
                 pa.close()
+        # the paper's IC(1) preconditioner (9-point pattern), both unknown orders
+        for ordering in (1, 0):
+            t1 = time.perf_counter()
+            pp = Problem(v, s, alpha, h, lo, hi, precond=9, ordering=ordering)
+            t_pc = time.perf_counter() - t1
+            f = torch.ones(pp.n_grid, dtype=torch.float64, device=dev)
+            pp.solve(f, mode="mixed", tol=1e-8)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            _, info = pp.solve(f, mode="mixed", tol=1e-8)
+            torch.cuda.synchronize()
+            pi = pp.info()
+            pcg[f"alpha={alpha} ic1 ordering={'multicolour' if ordering else 'natural'}"] = {
+                "mixed_s": round(time.perf_counter() - t1, 5), "inner_iters": info["inner_iters"],
+                "outer_iters": info["outer_iters"], "rel_res_fp64": info["rel_res_fp64"],
+                "levels": pi["precond_levels"], "factor_nnz": pi["precond_nnz"], "build_s": round(t_pc, 3)}
+            pp.close()
     clk = clocks.stop()
 
     if rank == 0:
@@ -283,13 +319,13 @@ def run_gofd(args):
                 "warmup": args.warmup, "ms_per_step": round(ms_max, 5), "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic (seeded jittered L-shape Delaunay mesh, uniform random x)",
-                "config": {"workload": "2D L-shape [-1,1]^2\\[0,1]^2, %d vertices, %d interior, 1024^2 grid "
-                                       "in a 2048^2 circulant, alpha=1, FP32 stiffness product" % (n_v, nint),
+                "config": {"workload": WORKLOADS[args.workload] + ", FP32 stiffness product (%d vertices, %d interior)"
+                                       % (n_v, nint),
                            "l2": "flushed (256 MB write) before every timed step",
                            "n_loc": n_loc, "setup_s": round(t_setup, 3)},
                 "roofline": roofline, "e2e": e2e, "pcg": pcg,
                 "gpu_launches": 4 * args.steps, "clocks": clk}
-        if world == 1 and not args.no_cpu:
+        if world == 1 and not args.no_cpu and args.workload == "lshape1024":
             try:
                 line["cpu_baseline"] = cpu_baseline()[1]
             except Exception as exc:  # the baseline is reported, never required
@@ -312,6 +348,7 @@ def main():
     ap.add_argument("--impl", default="gofd", choices=["gofd", "reference"])
     ap.add_argument("--no-pcg", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="lshape1024", choices=sorted(WORKLOADS))
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -429,9 +429,13 @@ def filon_coefficients(d: int, s: float, n: int, M: int) -> np.ndarray:
     (T-3) over j in [0,M)^d of the even samples is a DCT-I of the half range.
     """
     f = psi_tilde_samples(d, s, M)
+    # the trapezoid sum is M-periodic and even in each p_i: for M/2 < p < M it
+    # equals the value at M - p (needed when n > M/2 + 1 on a coarse level)
+    p_idx = np.arange(n) % M
+    p_idx = np.minimum(p_idx, M - p_idx)
     for ax in range(d):
         f = scipy.fft.dct(f, type=1, axis=ax)
-        f = np.take(f, np.arange(n), axis=ax)
+        f = np.take(f, p_idx, axis=ax)
     f = f / float(M) ** d
     p = np.arange(n, dtype=np.float64)
     fac = (-1.0) ** p * np.sinc(p / M) ** 2

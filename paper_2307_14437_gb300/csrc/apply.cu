@@ -13,6 +13,7 @@
 // Every transform is unnormalised; the symbol carries the 1/P^d factor.
 #include <algorithm>
 #include <mutex>
+#include <vector>
 
 #include "gofd_internal.cuh"
 #include "fft_common.cuh"
@@ -207,6 +208,27 @@ __global__ void __launch_bounds__(512) row_inverse_kernel(const typename Cplx<Re
 // ---------------------------------------------------------------------------
 // kernel 4: y = I^T w, TPR lanes per interior vertex, fixed order
 // ---------------------------------------------------------------------------
+// rows longer than SCATTER_LONG entries (patches of large elements on a fine
+// grid) are left to scatter_long_kernel, one CTA per row
+constexpr int SCATTER_LONG = 1024;
+
+template <class Real>
+__global__ void scatter_long_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                                    const Real* __restrict__ val, const Real* __restrict__ w,
+                                    const int32_t* __restrict__ rows, Real* __restrict__ y, Real scale) {
+    __shared__ Real part[256];
+    const int32_t i = rows[blockIdx.x];
+    Real acc = 0;
+    for (int a = ptr[i] + threadIdx.x; a < ptr[i + 1]; a += blockDim.x) acc += __ldg(&val[a]) * __ldg(&w[__ldg(&col[a])]);
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) y[i] = part[0] * scale;
+}
+
 template <class Real, int TPR>
 __global__ void scatter_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
                                const Real* __restrict__ val, const Real* __restrict__ w, int64_t nint,
@@ -220,7 +242,7 @@ __global__ void scatter_kernel(const int32_t* __restrict__ ptr, const int32_t* _
     for (int64_t t0 = gid - (threadIdx.x & 31); t0 < nint * TPR; t0 += nthreads) {
         const int64_t i = (t0 + (threadIdx.x & 31)) / TPR;
         Real acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
-        if (i < nint) {
+        if (i < nint && ptr[i + 1] - ptr[i] <= SCATTER_LONG) {
             const int b = ptr[i], e = ptr[i + 1];
             int a = b + lane;
             for (; a + 3 * TPR < e; a += 4 * TPR) {
@@ -238,7 +260,7 @@ __global__ void scatter_kernel(const int32_t* __restrict__ ptr, const int32_t* _
         Real acc = (acc0 + acc1) + (acc2 + acc3);
 #pragma unroll
         for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, TPR);
-        if (lane == 0 && i < nint) y[i] = acc * scale;
+        if (lane == 0 && i < nint && ptr[i + 1] - ptr[i] <= SCATTER_LONG) y[i] = acc * scale;
     }
 }
 
@@ -316,6 +338,16 @@ void setup_apply(gofd_problem* p) {
     p->gridw.alloc(sizeof(double) * p->ngrid);
     p->xin.alloc(sizeof(double) * (p->nint + 1));
     p->yout.alloc(sizeof(double) * (p->nint + 1));
+    {
+        std::vector<int32_t> ptr(p->nint + 1), rows;
+        GOFD_CUDA_TRY(cudaMemcpy(ptr.data(), p->csr_ptr.ptr, 4 * (p->nint + 1), cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < p->nint; ++i)
+            if (ptr[i + 1] - ptr[i] > SCATTER_LONG) rows.push_back((int32_t)i);
+        p->n_long_rows = (int64_t)rows.size();
+        p->long_rows.alloc(4 * (rows.size() + 1));
+        if (!rows.empty())
+            GOFD_CUDA_TRY(cudaMemcpy(p->long_rows.ptr, rows.data(), 4 * rows.size(), cudaMemcpyHostToDevice));
+    }
     int limit = 0;
     GOFD_CUDA_TRY(cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
     const size_t need = std::max({row_smem<double>(c), col_smem<float>(c, c.tc32), col_smem<double>(c, c.tc64)});
@@ -431,6 +463,11 @@ static void scatter(gofd_problem* p, const Real* wgrid, Real* y, Real scale, cud
             p->csr_ptr.as<int32_t>(), p->csr_col.as<int32_t>(), val, wgrid, p->nint, y, scale);
     }
     GOFD_CHECK_LAUNCH();
+    if (p->n_long_rows > 0) {
+        scatter_long_kernel<Real><<<(unsigned)p->n_long_rows, 256, 0, st>>>(
+            p->csr_ptr.as<int32_t>(), p->csr_col.as<int32_t>(), val, wgrid, p->long_rows.as<int32_t>(), y, scale);
+        GOFD_CHECK_LAUNCH();
+    }
     mark_stage(st, "scatter");
 }
 

@@ -123,6 +123,8 @@ struct gofd_problem {
     gofd::DevBuf csr_val32;    // float [nnz]
     int64_t nnz_t = 0;
     gofd::DevBuf colsum;       // double[nint]  D_h over interior vertices
+    gofd::DevBuf long_rows;    // int32 [n_long_rows] rows of I^T with more than 1024 entries
+    int64_t n_long_rows = 0;
     double a_h = 0, min_colsum = 0;
 
     // coefficients and symbol

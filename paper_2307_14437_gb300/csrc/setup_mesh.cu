@@ -441,16 +441,18 @@ __global__ void csr_scatter_kernel(const int32_t* __restrict__ iidx, int64_t nlo
     }
 }
 
-// Sort each row by ELL row (= by grid index), then emit columns, values and the
-// column sum D_h in that fixed order.
-__global__ void csr_finalize_kernel(const int32_t* __restrict__ ptr, int32_t nint,
-                                    int64_t* __restrict__ packed, const int32_t* __restrict__ ell_node,
-                                    const double* __restrict__ w64, int64_t nloc,
-                                    int32_t* __restrict__ col, double* __restrict__ v64,
-                                    float* __restrict__ v32, double* __restrict__ colsum) {
+// Sort each row by ELL row (= by grid index).  Rows up to SHORT_ROW entries:
+// insertion sort by one thread; longer rows (patches of large elements on a
+// fine grid): one CTA per row, bottom-up merge sort where every element finds
+// its place in the merged run by binary search in the partner run (keys are
+// unique: a vertex appears once per grid node).
+constexpr int SHORT_ROW = 256;
+
+__global__ void csr_sort_short_kernel(const int32_t* __restrict__ ptr, int32_t nint, int64_t* __restrict__ packed) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nint;
          i += (int64_t)gridDim.x * blockDim.x) {
         int32_t b = ptr[i], e = ptr[i + 1];
+        if (e - b > SHORT_ROW) continue;
         for (int32_t a = b + 1; a < e; ++a) {
             int64_t key = packed[a];
             int32_t c = a - 1;
@@ -460,6 +462,59 @@ __global__ void csr_finalize_kernel(const int32_t* __restrict__ ptr, int32_t nin
             }
             packed[c + 1] = key;
         }
+    }
+}
+
+__global__ void csr_sort_long_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ rows,
+                                     int64_t* __restrict__ packed, int64_t* __restrict__ tmp) {
+    const int32_t i = rows[blockIdx.x];
+    const int32_t b = ptr[i], L = ptr[i + 1] - b;
+    int64_t* src = packed + b;
+    int64_t* dst = tmp + b;
+    for (int32_t run = 1; run < L; run *= 2) {
+        for (int32_t p = threadIdx.x; p < L; p += blockDim.x) {
+            const int32_t q = p / run;
+            const int32_t own0 = q * run;
+            const int32_t oth0 = (q ^ 1) * run;
+            const int64_t key = src[p];
+            int32_t pos = p;
+            if (oth0 < L) {
+                const int32_t oth1 = min(oth0 + run, L);
+                int32_t lo = oth0, hi = oth1;   // number of partner keys below key
+                while (lo < hi) {
+                    const int32_t mid = (lo + hi) >> 1;
+                    if (src[mid] < key) lo = mid + 1;
+                    else hi = mid;
+                }
+                pos = min(own0, oth0) + (p - own0) + (lo - oth0);
+            }
+            dst[pos] = key;
+        }
+        __syncthreads();
+        int64_t* t = src;
+        src = dst;
+        dst = t;
+    }
+    if (src != packed + b)
+        for (int32_t p = threadIdx.x; p < L; p += blockDim.x) packed[b + p] = src[p];
+}
+
+__global__ void csr_long_rows_kernel(const int32_t* __restrict__ ptr, int32_t nint, int32_t* __restrict__ count,
+                                     int32_t* __restrict__ rows) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nint;
+         i += (int64_t)gridDim.x * blockDim.x)
+        if (ptr[i + 1] - ptr[i] > SHORT_ROW) rows[atomicAdd(count, 1)] = (int32_t)i;
+}
+
+// Emit columns, values and the column sum D_h in the sorted order.
+__global__ void csr_finalize_kernel(const int32_t* __restrict__ ptr, int32_t nint,
+                                    const int64_t* __restrict__ packed, const int32_t* __restrict__ ell_node,
+                                    const double* __restrict__ w64, int64_t nloc,
+                                    int32_t* __restrict__ col, double* __restrict__ v64,
+                                    float* __restrict__ v32, double* __restrict__ colsum) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nint;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t b = ptr[i], e = ptr[i + 1];
         double sum = 0.0;
         for (int32_t a = b; a < e; ++a) {
             int64_t r = packed[a] >> 2, s = packed[a] & 3;
@@ -634,6 +689,30 @@ static void setup_mesh_d(gofd_problem* p) {
                 p->ell_iidx.as<int32_t>(), nloc, dp1, nint, p->csr_ptr.as<int32_t>(),
                 cursor.as<int32_t>(), packed.as<int64_t>());
             GOFD_CHECK_LAUNCH();
+        }
+        csr_sort_short_kernel<<<grid_blocks(p->nint, 128), 128, 0, st>>>(p->csr_ptr.as<int32_t>(), nint,
+                                                                         packed.as<int64_t>());
+        GOFD_CHECK_LAUNCH();
+        {
+            // rows too long for one thread (orders are the same, rows are unique)
+            DevBuf nlong, rows;
+            nlong.alloc(sizeof(int32_t));
+            rows.alloc(sizeof(int32_t) * (p->nint + 1));
+            GOFD_CUDA_TRY(cudaMemsetAsync(nlong.ptr, 0, sizeof(int32_t), st));
+            csr_long_rows_kernel<<<grid_blocks(p->nint, 256), 256, 0, st>>>(p->csr_ptr.as<int32_t>(), nint,
+                                                                            nlong.as<int32_t>(), rows.as<int32_t>());
+            GOFD_CHECK_LAUNCH();
+            int32_t hl = 0;
+            GOFD_CUDA_TRY(cudaMemcpyAsync(&hl, nlong.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            GOFD_CUDA_TRY(cudaStreamSynchronize(st));
+            if (hl > 0) {
+                DevBuf tmp;
+                tmp.alloc(sizeof(int64_t) * p->nnz_t);
+                csr_sort_long_kernel<<<hl, 512, 0, st>>>(p->csr_ptr.as<int32_t>(), rows.as<int32_t>(),
+                                                         packed.as<int64_t>(), tmp.as<int64_t>());
+                GOFD_CHECK_LAUNCH();
+                GOFD_CUDA_TRY(cudaStreamSynchronize(st));
+            }
         }
         csr_finalize_kernel<<<grid_blocks(p->nint, 128), 128, 0, st>>>(
             p->csr_ptr.as<int32_t>(), nint, packed.as<int64_t>(), p->ell_node.as<int32_t>(),

@@ -1,0 +1,148 @@
+"""Parity at the full sizes of the benchmark workloads, in the configuration
+bench.py times (default options: paper Filon M, default circulant length).
+
+L-shape 6.05e4 vertices / 1024^2 grid and graded disk 2.1e5 vertices / 2048^2
+grid: every grid node's owner and ELL row against the exact oracle, the
+coefficients and symbol, FP32 and FP64 products against the oracle's FFT
+product, solves checked with the oracle's operator.  Unit ball 1.3e5 vertices
+/ 256^3 grid: owners of sampled nodes against the exact oracle, properties
+that hold at any size (symmetry, positivity, FP32/FP64 agreement) and the
+closed-form solution (exam-2).
+"""
+import numpy as np
+import pytest
+
+import meshgen as mg
+from oracle import gofd as o
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2307_14437_gb300 import build_native
+    build_native.build()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def lshape():
+    from paper_2307_14437_gb300 import Problem
+    v, s = mg.lshape_mesh(seed=mg.seed_for(2))
+    lo, hi, h = mg.grid_box(2, 1024)
+    gp = Problem(v, s, 1.0, h, lo, hi)
+    ref = o.build(2, v, s, 1.0, h, lo, hi, exact_weights=False, pruned=True, M=gp.info()["filon_M"])
+    return gp, ref
+
+
+def test_lshape_transfer_coefficients_symbol(lshape):
+    gp, ref = lshape
+    owner, idx, w = gp.export_transfer()
+    assert np.array_equal(owner, ref.owner.astype(np.int32))
+    assert np.array_equal(idx, ref.ell_idx.astype(np.int32))
+    assert np.abs(w - ref.ell_w).max() < 1e-12
+    assert np.abs(gp.coefficients() - ref.T).max() < 1e-13
+    assert gp.P == ref.P
+    assert np.abs(gp.symbol() - ref.lam).max() < 1e-12 * np.abs(ref.lam).max()
+
+
+def test_lshape_products(lshape):
+    gp, ref = lshape
+    u = mg.random_vector(len(ref.verts), 41)
+    want = o.stiffness_apply(ref, u)
+    y64 = gp.apply(torch.tensor(u, device="cuda")).cpu().numpy()
+    y32 = gp.apply(torch.tensor(u, device="cuda", dtype=torch.float32)).cpu().numpy().astype(np.float64)
+    assert _rel(y64, want) < 1e-12
+    assert _rel(y32, want) < 1e-5
+
+
+@pytest.mark.parametrize("alpha", [0.5, 1.0, 1.5])
+def test_lshape_solves_reach_1e8(lshape, alpha):
+    from paper_2307_14437_gb300 import Problem
+    gp0, ref0 = lshape
+    if alpha == 1.0:
+        gp, ref = gp0, ref0
+    else:
+        gp = Problem(ref0.verts, ref0.simp, alpha, ref0.h, ref0.box_lo, ref0.box_hi)
+        ref = o.build(2, ref0.verts, ref0.simp, alpha, ref0.h, ref0.box_lo, ref0.box_hi, exact_weights=False,
+                      pruned=True, M=gp.info()["filon_M"])
+    b = o.rhs_grid(ref, np.ones(ref.n_grid))
+    f = torch.ones(gp.n_grid, dtype=torch.float64, device="cuda")
+    for mode in ("mixed", "fp64"):
+        u, info = gp.solve(f, mode=mode, tol=1e-8)
+        res = np.linalg.norm(b - o.stiffness_apply(ref, u.cpu().numpy())) / np.linalg.norm(b)
+        assert res <= 1.05e-8, (mode, res, info)
+
+
+def test_lshape_ic1_pcg(lshape):
+    from paper_2307_14437_gb300 import Problem
+    _, ref = lshape
+    gp = Problem(ref.verts, ref.simp, 1.0, ref.h, ref.box_lo, ref.box_hi, precond=9, ordering=1)
+    f = torch.ones(gp.n_grid, dtype=torch.float64, device="cuda")
+    u, info = gp.solve(f, mode="mixed", tol=1e-8)
+    b = o.rhs_grid(ref, np.ones(ref.n_grid))
+    assert np.linalg.norm(b - o.stiffness_apply(ref, u.cpu().numpy())) / np.linalg.norm(b) <= 1.05e-8
+    gp.close()
+
+
+def test_graded_disk_2048(request):
+    from paper_2307_14437_gb300 import Problem
+    lo, hi, h = mg.grid_box(2, 2048)
+    v, s = mg.graded_disk_mesh(h, seed=mg.seed_for(4))
+    gp = Problem(v, s, 1.2, h, lo, hi)
+    ref = o.build(2, v, s, 1.2, h, lo, hi, exact_weights=False, pruned=True, M=gp.info()["filon_M"])
+    owner, idx, w = gp.export_transfer()
+    assert np.array_equal(owner, ref.owner.astype(np.int32))
+    assert np.array_equal(idx, ref.ell_idx.astype(np.int32))
+    assert np.abs(w - ref.ell_w).max() < 1e-12
+    assert np.abs(gp.coefficients() - ref.T).max() < 1e-13
+    u = mg.random_vector(len(v), 43)
+    want = o.stiffness_apply(ref, u)
+    y32 = gp.apply(torch.tensor(u, device="cuda", dtype=torch.float32)).cpu().numpy().astype(np.float64)
+    assert _rel(y32, want) < 1e-5
+    # GoFD-3 right-hand side from vertex values of f_target (Section 3.2)
+    ft = mg.target_bump(v)
+    uu, info = gp.solve(torch.tensor(ft, device="cuda"), rhs="vertex", mode="mixed", tol=1e-8)
+    b = o.rhs_vertex(ref, ft)
+    assert np.linalg.norm(b - o.stiffness_apply(ref, uu.cpu().numpy())) / np.linalg.norm(b) <= 1.05e-8
+    gp.close()
+
+
+def test_ball_256_properties_and_closed_form():
+    from paper_2307_14437_gb300 import Problem
+    v, s = mg.ball_shell_mesh(seed=mg.seed_for(3))
+    lo, hi, h = mg.grid_box(3, 256)
+    gp = Problem(v, s, 1.5, h, lo, hi)
+    owner, idx, w = gp.export_transfer()
+    n = o.grid_shape(lo, hi, h)
+    rng = np.random.default_rng(5)
+    located = np.nonzero(owner >= 0)[0]
+    sample = np.concatenate([rng.choice(located, 48, replace=False),
+                             rng.choice(np.nonzero(owner < 0)[0], 16, replace=False)])
+    want = o.locate(v, s, lo, h, n, nodes=sample, chunk=4)
+    assert np.array_equal(owner[sample], want.astype(np.int32))
+    # symmetry and positivity of S (Theorem 3.1), FP32 vs FP64 agreement
+    a = torch.tensor(mg.random_vector(len(v), 44), device="cuda")
+    b = torch.tensor(mg.random_vector(len(v), 45), device="cuda")
+    Sa, Sb = gp.apply(a), gp.apply(b)
+    ab, ba = float(torch.dot(b, Sa)), float(torch.dot(a, Sb))
+    assert abs(ab - ba) <= 1e-12 * float(torch.linalg.norm(Sa) * torch.linalg.norm(b))
+    ii, _ = gp.export_vertex_data()
+    mask = torch.tensor(ii >= 0, device="cuda", dtype=torch.float64)
+    assert float(torch.dot(a * mask, Sa)) > 0
+    Sa32 = gp.apply(a.float()).double()
+    assert float(torch.linalg.norm(Sa32 - Sa) / torch.linalg.norm(Sa)) < 1e-5
+    # (exam-2) with s = 0.75: u = C (1-|x|^2)^0.75, C = 0.300901...
+    u, info = gp.solve(torch.ones(gp.n_grid, dtype=torch.float64, device="cuda"), mode="mixed", tol=1e-8)
+    assert info["rel_res_fp64"] <= 1e-8
+    err = o.lumped_l2(v, s, u.cpu().numpy() - o.ball_exact(v, 0.75))
+    norm = o.lumped_l2(v, s, o.ball_exact(v, 0.75))
+    assert err / norm < 0.05, err / norm
+    gp.close()

@@ -204,6 +204,25 @@ gofd_status gofd_solve(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs,
                        const double* f_dev, double tol, int maxit, int init_zero,
                        double* u_dev, gofd_solve_info* info, void* stream);
 
+/*
+ * gofd_adjoint -- gradients of a loss L(u) through the solve with vertex data
+ * (GoFD-3), u = S(X)^{-1} h^{2s} D_h(X) f, for the data f and the mesh vertex
+ * coordinates X (the owner simplex of every grid node held fixed).
+ *   f_dev      device, N_v doubles: the vertex data of the forward solve
+ *   u_dev      device, N_v doubles: its solution (boundary entries are taken as 0)
+ *   g_dev      device, N_v doubles: dL/du (boundary entries ignored)
+ *   tol, maxit the adjoint solve S lambda = g (same modes as gofd_solve)
+ *   grad_f_dev device, N_v doubles: dL/df = h^{2s} D_h lambda (0 on the boundary)
+ *   grad_x_dev device, N_v*d doubles (row-major like the vertices): dL/dX
+ * The adjoint state is one more solve; no iterate of the forward solve is
+ * stored.  The first call allocates a vertex-major transpose of I_h^FD and
+ * two grid vectors that the handle keeps.  The paper has no adjoint; this
+ * differentiates its discrete system (Section 3.2).
+ */
+gofd_status gofd_adjoint(gofd_problem* p, gofd_solve_mode mode, const double* f_dev, const double* u_dev,
+                         const double* g_dev, double tol, int maxit, double* grad_f_dev,
+                         double* grad_x_dev, gofd_solve_info* info, void* stream);
+
 /* gofd_get_info -- sizes and set-up results (host struct). */
 gofd_status gofd_get_info(const gofd_problem* p, gofd_info* info);
 

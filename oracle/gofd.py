@@ -915,6 +915,58 @@ def pcg_ic(prob: Problem, b: np.ndarray, pattern: int = 9, tol: float = 1e-10, m
 
 
 # ============================================================================
+# 7b. Adjoint of the vertex-data solve (differentiating (GoFD-3))
+# ============================================================================
+
+def barycentric_gradients(verts, simp_rows):
+    """grad phi_a (constant on each simplex): (m, d+1, d)."""
+    V = verts[simp_rows]
+    d = V.shape[2]
+    J = np.transpose(V[:, 1:, :] - V[:, :1, :], (0, 2, 1))      # J[:, r, c] = X_{c+1,r} - X_{0,r}
+    Ji = np.linalg.inv(J)
+    G = np.empty((len(V), d + 1, d))
+    G[:, 1:, :] = Ji
+    G[:, 0, :] = -Ji.sum(axis=1)
+    return G
+
+
+def adjoint_vertex(prob: Problem, f_h: np.ndarray, u: np.ndarray, g: np.ndarray, tol: float = 1e-13):
+    """dL/df and dL/dX for u = S(X)^{-1} h^{2s} D_h(X) f  ((GoFD-3)), given g = dL/du.
+
+    With S lambda = g: dL = lambda^T (db - dS u).  b = h^{2s} D_h f gives
+    dL/df = h^{2s} D_h lambda.  For X: phi_a(x_k) depends on the vertices of the
+    owner simplex K (held fixed) with d phi_a/d X_{j,c} = -phi_j d phi_a/d x_c, so
+    dL/dX_{j,c} = sum_k phi_j(x_k) [d_c(I_h lambda) (A_FD I u)_k
+                                   + d_c(I_h u) (A_FD I lambda)_k
+                                   - h^{2s} d_c(I_h(lambda f))]   on K.
+    Returns (grad_f[N_v], grad_X[N_v, d]).
+    """
+    ii = prob.interior
+    nv = len(prob.verts)
+    gg = np.zeros(nv)
+    gg[ii] = g[ii]
+    lam, _ = cg(lambda x: stiffness_apply(prob, x), gg, ii, tol)
+    h2s = prob.h ** (2 * prob.s)
+    grad_f = np.zeros(nv)
+    grad_f[ii] = h2s * prob.Dh[ii] * lam[ii]
+    uu = np.zeros(nv)
+    uu[ii] = u[ii]
+    w_u = afd_apply(prob, prob.I @ uu)
+    w_l = afd_apply(prob, prob.I @ lam)
+    K = prob.owner[prob.nodes]
+    verts_K = np.asarray(prob.simp)[K]                         # (n_loc, d+1) == ell_idx.T
+    G = barycentric_gradients(prob.verts, verts_K)
+    gl = np.einsum("na,nac->nc", lam[verts_K], G)
+    gu = np.einsum("na,nac->nc", uu[verts_K], G)
+    glf = np.einsum("na,nac->nc", (lam * f_h)[verts_K], G)
+    c = gl * w_u[prob.nodes][:, None] + gu * w_l[prob.nodes][:, None] - h2s * glf
+    grad_X = np.zeros((nv, prob.d))
+    for a in range(prob.d + 1):
+        np.add.at(grad_X, prob.ell_idx[a], prob.ell_w[a][:, None] * c)
+    return grad_f, grad_X
+
+
+# ============================================================================
 # 8. Closed form on the unit ball  ((exam-0), (exam-2) with k = 0)
 # ============================================================================
 

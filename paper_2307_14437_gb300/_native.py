@@ -55,6 +55,7 @@ EXPORTS = {
                                                C.POINTER(C.c_char_p), C.c_int, C.POINTER(C.c_int)]),
     "gofd_solve": (C.c_int, [_P, C.c_int, C.c_int, _P, C.c_double, C.c_int, C.c_int, _P,
                              C.POINTER(SolveInfo), _P]),
+    "gofd_adjoint": (C.c_int, [_P, C.c_int, _P, _P, _P, C.c_double, C.c_int, _P, _P, C.POINTER(SolveInfo), _P]),
     "gofd_get_info": (C.c_int, [_P, C.POINTER(Info)]),
     "gofd_export_transfer": (C.c_int, [_P, _P, _P, _P]),
     "gofd_export_vertex_data": (C.c_int, [_P, _P, _P]),

@@ -43,6 +43,7 @@ int circulant_length(int n) {
 }
 
 void release_all(gofd_problem* p) {
+    gofd::free_adjoint(p);
     gofd::free_workspace(p);
     gofd::free_precond(p);
     if (p->setup_stream) cudaStreamDestroy(p->setup_stream);
@@ -233,6 +234,18 @@ gofd_status gofd_solve(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs, cons
         if (rhs != GOFD_RHS_GRID && rhs != GOFD_RHS_VERTEX) gofd::fail(GOFD_E_ARG, "bad rhs kind");
         if (!(tol > 0.0) || maxit < 1) gofd::fail(GOFD_E_ARG, "tol must be > 0 and maxit >= 1");
         gofd::solve(p, mode, rhs, f_dev, tol, maxit, init_zero != 0, u_dev, info, (cudaStream_t)stream);
+    })
+}
+
+gofd_status gofd_adjoint(gofd_problem* p, gofd_solve_mode mode, const double* f_dev, const double* u_dev,
+                         const double* g_dev, double tol, int maxit, double* grad_f_dev, double* grad_x_dev,
+                         gofd_solve_info* info, void* stream) {
+    if (!p) return GOFD_E_ARG;
+    GOFD_API_BODY(p, {
+        if (!f_dev || !u_dev || !g_dev || !grad_f_dev || !grad_x_dev) gofd::fail(GOFD_E_ARG, "NULL vector");
+        if (mode != GOFD_SOLVE_FP64 && mode != GOFD_SOLVE_MIXED) gofd::fail(GOFD_E_ARG, "bad mode");
+        if (!(tol > 0.0) || maxit < 1) gofd::fail(GOFD_E_ARG, "tol must be > 0 and maxit >= 1");
+        gofd::adjoint(p, mode, f_dev, u_dev, g_dev, tol, maxit, grad_f_dev, grad_x_dev, info, (cudaStream_t)stream);
     })
 }
 

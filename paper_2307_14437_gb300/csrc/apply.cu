@@ -212,21 +212,43 @@ __global__ void __launch_bounds__(512) row_inverse_kernel(const typename Cplx<Re
 // grid) are left to scatter_long_kernel, one CTA per row
 constexpr int SCATTER_LONG = 1024;
 
+// Long rows are cut into chunks of SCATTER_CHUNK entries; one CTA sums a
+// chunk (fixed-order tree), then one thread per long row adds its chunks in
+// order, so the result does not depend on scheduling.
+constexpr int SCATTER_CHUNK = 2048;
+
 template <class Real>
-__global__ void scatter_long_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
-                                    const Real* __restrict__ val, const Real* __restrict__ w,
-                                    const int32_t* __restrict__ rows, Real* __restrict__ y, Real scale) {
+__global__ void scatter_chunk_kernel(const int32_t* __restrict__ col, const Real* __restrict__ val,
+                                     const Real* __restrict__ w, const int32_t* __restrict__ cbeg,
+                                     const int32_t* __restrict__ cend, Real* __restrict__ partial) {
     __shared__ Real part[256];
-    const int32_t i = rows[blockIdx.x];
-    Real acc = 0;
-    for (int a = ptr[i] + threadIdx.x; a < ptr[i + 1]; a += blockDim.x) acc += __ldg(&val[a]) * __ldg(&w[__ldg(&col[a])]);
-    part[threadIdx.x] = acc;
+    const int32_t b = cbeg[blockIdx.x], e = cend[blockIdx.x];
+    Real a0 = 0, a1 = 0;
+    int a = b + threadIdx.x;
+    for (; a + 256 < e; a += 512) {
+        const int c0 = __ldg(&col[a]), c1 = __ldg(&col[a + 256]);
+        a0 += __ldg(&val[a]) * __ldg(&w[c0]);
+        a1 += __ldg(&val[a + 256]) * __ldg(&w[c1]);
+    }
+    for (; a < e; a += 256) a0 += __ldg(&val[a]) * __ldg(&w[__ldg(&col[a])]);
+    part[threadIdx.x] = a0 + a1;
     __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    for (int o = 128; o > 0; o >>= 1) {
         if (threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) y[i] = part[0] * scale;
+    if (threadIdx.x == 0) partial[blockIdx.x] = part[0];
+}
+
+template <class Real>
+__global__ void scatter_combine_kernel(const int32_t* __restrict__ rows, const int32_t* __restrict__ cptr,
+                                       int64_t nrows, const Real* __restrict__ partial, Real* __restrict__ y,
+                                       Real scale) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrows; r += (int64_t)gridDim.x * blockDim.x) {
+        Real s = 0;
+        for (int c = cptr[r]; c < cptr[r + 1]; ++c) s += partial[c];
+        y[rows[r]] = s * scale;
+    }
 }
 
 template <class Real, int TPR>
@@ -339,14 +361,31 @@ void setup_apply(gofd_problem* p) {
     p->xin.alloc(sizeof(double) * (p->nint + 1));
     p->yout.alloc(sizeof(double) * (p->nint + 1));
     {
-        std::vector<int32_t> ptr(p->nint + 1), rows;
+        // long rows of I^T and their chunks (set-up bookkeeping on the host)
+        std::vector<int32_t> ptr(p->nint + 1), rows, cptr(1, 0), cb, ce;
         GOFD_CUDA_TRY(cudaMemcpy(ptr.data(), p->csr_ptr.ptr, 4 * (p->nint + 1), cudaMemcpyDeviceToHost));
         for (int64_t i = 0; i < p->nint; ++i)
-            if (ptr[i + 1] - ptr[i] > SCATTER_LONG) rows.push_back((int32_t)i);
+            if (ptr[i + 1] - ptr[i] > SCATTER_LONG) {
+                rows.push_back((int32_t)i);
+                for (int32_t a = ptr[i]; a < ptr[i + 1]; a += SCATTER_CHUNK) {
+                    cb.push_back(a);
+                    ce.push_back(std::min(a + SCATTER_CHUNK, ptr[i + 1]));
+                }
+                cptr.push_back((int32_t)cb.size());
+            }
         p->n_long_rows = (int64_t)rows.size();
+        p->n_long_chunks = (int64_t)cb.size();
         p->long_rows.alloc(4 * (rows.size() + 1));
-        if (!rows.empty())
+        p->long_chunk_ptr.alloc(4 * cptr.size());
+        p->chunk_beg.alloc(4 * (cb.size() + 1));
+        p->chunk_end.alloc(4 * (ce.size() + 1));
+        p->long_partial.alloc(8 * (cb.size() + 1));
+        if (!rows.empty()) {
             GOFD_CUDA_TRY(cudaMemcpy(p->long_rows.ptr, rows.data(), 4 * rows.size(), cudaMemcpyHostToDevice));
+            GOFD_CUDA_TRY(cudaMemcpy(p->long_chunk_ptr.ptr, cptr.data(), 4 * cptr.size(), cudaMemcpyHostToDevice));
+            GOFD_CUDA_TRY(cudaMemcpy(p->chunk_beg.ptr, cb.data(), 4 * cb.size(), cudaMemcpyHostToDevice));
+            GOFD_CUDA_TRY(cudaMemcpy(p->chunk_end.ptr, ce.data(), 4 * ce.size(), cudaMemcpyHostToDevice));
+        }
     }
     int limit = 0;
     GOFD_CUDA_TRY(cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
@@ -464,8 +503,11 @@ static void scatter(gofd_problem* p, const Real* wgrid, Real* y, Real scale, cud
     }
     GOFD_CHECK_LAUNCH();
     if (p->n_long_rows > 0) {
-        scatter_long_kernel<Real><<<(unsigned)p->n_long_rows, 256, 0, st>>>(
-            p->csr_ptr.as<int32_t>(), p->csr_col.as<int32_t>(), val, wgrid, p->long_rows.as<int32_t>(), y, scale);
+        Real* part = reinterpret_cast<Real*>(p->long_partial.ptr);
+        scatter_chunk_kernel<Real><<<(unsigned)p->n_long_chunks, 256, 0, st>>>(
+            p->csr_col.as<int32_t>(), val, wgrid, p->chunk_beg.as<int32_t>(), p->chunk_end.as<int32_t>(), part);
+        scatter_combine_kernel<Real><<<grid_blocks(p->n_long_rows, 128), 128, 0, st>>>(
+            p->long_rows.as<int32_t>(), p->long_chunk_ptr.as<int32_t>(), p->n_long_rows, part, y, scale);
         GOFD_CHECK_LAUNCH();
     }
     mark_stage(st, "scatter");
@@ -510,6 +552,12 @@ int apply_interior_profiled(gofd_problem* p, bool fp64, const void* x, void* y, 
     for (int i = 0; i < 8; ++i) cudaEventDestroy(se.ev[i]);
     cudaEventDestroy(start);
     return n;
+}
+
+void afd_of_interior(gofd_problem* p, bool fp64, const void* x, void* wgrid, cudaStream_t st) {
+    ApplyCfg c = cfg_for(p);
+    if (fp64) afd_core<double>(p, c, (const double*)x, nullptr, (double*)wgrid, st);
+    else afd_core<float>(p, c, (const float*)x, nullptr, (float*)wgrid, st);
 }
 
 void afd_apply_grid(gofd_problem* p, bool fp64, const void* v, void* w, cudaStream_t st) {

@@ -78,6 +78,8 @@ struct Precond;   // defined in precond.cu
 
 struct Workspace;  // solver vectors, defined in solver.cu
 
+struct Adjoint;    // adjoint buffers, defined in adjoint.cu
+
 }  // namespace gofd
 
 struct gofd_problem {
@@ -124,7 +126,9 @@ struct gofd_problem {
     int64_t nnz_t = 0;
     gofd::DevBuf colsum;       // double[nint]  D_h over interior vertices
     gofd::DevBuf long_rows;    // int32 [n_long_rows] rows of I^T with more than 1024 entries
-    int64_t n_long_rows = 0;
+    gofd::DevBuf long_chunk_ptr, chunk_beg, chunk_end;  // chunks of the long rows
+    gofd::DevBuf long_partial; // chunk partial sums (largest precision)
+    int64_t n_long_rows = 0, n_long_chunks = 0;
     double a_h = 0, min_colsum = 0;
 
     // coefficients and symbol
@@ -148,6 +152,7 @@ struct gofd_problem {
     // solver / preconditioner
     gofd::Workspace* ws = nullptr;
     gofd::Precond* pc = nullptr;
+    gofd::Adjoint* adj = nullptr;
 
     double t_setup_ms = 0;
     std::string last_error;
@@ -179,6 +184,9 @@ void expand_interior(gofd_problem* p, bool fp64, const void* y, void* u, double 
 void solve(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs, const double* f, double tol,
            int maxit, bool init_zero, double* u, gofd_solve_info* info, cudaStream_t st);
 void free_workspace(gofd_problem* p);
+void solve_core(gofd_problem* p, gofd_solve_mode mode, const double* b, double tol, int maxit, bool init_zero,
+                double* x, gofd_solve_info* info, cudaStream_t st);
+void assemble_rhs(gofd_problem* p, gofd_rhs rhs, const double* f, double* b, cudaStream_t st);
 
 // preconditioner (precond.cu)
 void setup_precond(gofd_problem* p);
@@ -193,5 +201,12 @@ void precond_apply(gofd_problem* p, bool fp64, const void* r, void* z, cudaStrea
 // utilities (setup_mesh.cu)
 int64_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t st);
 int grid_blocks(int64_t work, int threads, int cap = 152 * 16);
+void sort_packed_rows(const int32_t* ptr, int64_t nrows, int64_t* packed, int64_t nnz, cudaStream_t st);
+// w = A_FD I x on the grid for an interior-compacted x (n_int + 1 entries)
+void afd_of_interior(gofd_problem* p, bool fp64, const void* x, void* wgrid, cudaStream_t st);
+// adjoint (adjoint.cu)
+void adjoint(gofd_problem* p, gofd_solve_mode mode, const double* f, const double* u, const double* g, double tol,
+             int maxit, double* grad_f, double* grad_x, gofd_solve_info* info, cudaStream_t st);
+void free_adjoint(gofd_problem* p);
 
 }  // namespace gofd

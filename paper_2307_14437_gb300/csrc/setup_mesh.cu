@@ -506,6 +506,29 @@ __global__ void csr_long_rows_kernel(const int32_t* __restrict__ ptr, int32_t ni
         if (ptr[i + 1] - ptr[i] > SHORT_ROW) rows[atomicAdd(count, 1)] = (int32_t)i;
 }
 
+// Sort every row of a row-pointer array of unique packed keys ascending.
+void sort_packed_rows(const int32_t* ptr, int64_t nrows, int64_t* packed, int64_t nnz, cudaStream_t st) {
+    csr_sort_short_kernel<<<grid_blocks(nrows, 128), 128, 0, st>>>(ptr, (int32_t)nrows, packed);
+    GOFD_CHECK_LAUNCH();
+    DevBuf nlong, rows;
+    nlong.alloc(sizeof(int32_t));
+    rows.alloc(sizeof(int32_t) * (nrows + 1));
+    GOFD_CUDA_TRY(cudaMemsetAsync(nlong.ptr, 0, sizeof(int32_t), st));
+    csr_long_rows_kernel<<<grid_blocks(nrows, 256), 256, 0, st>>>(ptr, (int32_t)nrows, nlong.as<int32_t>(),
+                                                                   rows.as<int32_t>());
+    GOFD_CHECK_LAUNCH();
+    int32_t hl = 0;
+    GOFD_CUDA_TRY(cudaMemcpyAsync(&hl, nlong.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    GOFD_CUDA_TRY(cudaStreamSynchronize(st));
+    if (hl > 0) {
+        DevBuf tmp;
+        tmp.alloc(sizeof(int64_t) * nnz);
+        csr_sort_long_kernel<<<hl, 512, 0, st>>>(ptr, rows.as<int32_t>(), packed, tmp.as<int64_t>());
+        GOFD_CHECK_LAUNCH();
+        GOFD_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+}
+
 // Emit columns, values and the column sum D_h in the sorted order.
 __global__ void csr_finalize_kernel(const int32_t* __restrict__ ptr, int32_t nint,
                                     const int64_t* __restrict__ packed, const int32_t* __restrict__ ell_node,
@@ -690,30 +713,7 @@ static void setup_mesh_d(gofd_problem* p) {
                 cursor.as<int32_t>(), packed.as<int64_t>());
             GOFD_CHECK_LAUNCH();
         }
-        csr_sort_short_kernel<<<grid_blocks(p->nint, 128), 128, 0, st>>>(p->csr_ptr.as<int32_t>(), nint,
-                                                                         packed.as<int64_t>());
-        GOFD_CHECK_LAUNCH();
-        {
-            // rows too long for one thread (orders are the same, rows are unique)
-            DevBuf nlong, rows;
-            nlong.alloc(sizeof(int32_t));
-            rows.alloc(sizeof(int32_t) * (p->nint + 1));
-            GOFD_CUDA_TRY(cudaMemsetAsync(nlong.ptr, 0, sizeof(int32_t), st));
-            csr_long_rows_kernel<<<grid_blocks(p->nint, 256), 256, 0, st>>>(p->csr_ptr.as<int32_t>(), nint,
-                                                                            nlong.as<int32_t>(), rows.as<int32_t>());
-            GOFD_CHECK_LAUNCH();
-            int32_t hl = 0;
-            GOFD_CUDA_TRY(cudaMemcpyAsync(&hl, nlong.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-            GOFD_CUDA_TRY(cudaStreamSynchronize(st));
-            if (hl > 0) {
-                DevBuf tmp;
-                tmp.alloc(sizeof(int64_t) * p->nnz_t);
-                csr_sort_long_kernel<<<hl, 512, 0, st>>>(p->csr_ptr.as<int32_t>(), rows.as<int32_t>(),
-                                                         packed.as<int64_t>(), tmp.as<int64_t>());
-                GOFD_CHECK_LAUNCH();
-                GOFD_CUDA_TRY(cudaStreamSynchronize(st));
-            }
-        }
+        sort_packed_rows(p->csr_ptr.as<int32_t>(), p->nint, packed.as<int64_t>(), p->nnz_t, st);
         csr_finalize_kernel<<<grid_blocks(p->nint, 128), 128, 0, st>>>(
             p->csr_ptr.as<int32_t>(), nint, packed.as<int64_t>(), p->ell_node.as<int32_t>(),
             p->ell_w64.as<double>(), nloc, p->csr_col.as<int32_t>(), p->csr_val64.as<double>(),

@@ -303,25 +303,17 @@ static int pcg(gofd_problem* p, Workspace* w, V* d, V* r, V* pv, V* q, V* z, dou
     return it;
 }
 
-void solve(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs, const double* f, double tol, int maxit,
-           bool init_zero, double* u, gofd_solve_info* info, cudaStream_t st) {
+// Solve S x = b on the interior unknowns (b, x: device, n_int (+1) FP64 each,
+// x[n_int] = 0 on exit).  x holds the initial guess unless init_zero.
+void solve_core(gofd_problem* p, gofd_solve_mode mode, const double* b, double tol, int maxit, bool init_zero,
+                double* x, gofd_solve_info* info, cudaStream_t st) {
     auto t0 = std::chrono::steady_clock::now();
     Workspace* w = ensure_ws(p);
     const int64_t n = p->nint;
     const int nb = grid_blocks(n, 256);
-    const double h2s = std::pow(p->h, 2.0 * p->s);
-    double* b = w->b64.as<double>();
-    double* x = w->x64.as<double>();
     double* r = w->r64.as<double>();
-    // right-hand side
-    if (rhs == GOFD_RHS_GRID) {
-        scatter_grid_f64(p, f, b, h2s, st);
-    } else {
-        rhs_vertex_kernel<<<nb, 256, 0, st>>>(f, p->int2vert.as<int32_t>(), p->colsum.as<double>(), h2s, n, b);
-        GOFD_CHECK_LAUNCH();
-    }
     if (init_zero) GOFD_CUDA_TRY(cudaMemsetAsync(x, 0, 8 * (n + 1), st));
-    else compact_vertex(p, true, u, x, st);
+    else GOFD_CUDA_TRY(cudaMemsetAsync(x + n, 0, 8, st));
     const double bn = norm64(p, w, b, st);
     int outer = 0, inner = 0;
     double rel = 0.0;
@@ -370,7 +362,6 @@ void solve(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs, const double* f,
             if (its == 0) break;
         }
     }
-    expand_interior(p, true, x, u, 0.0, st);
     GOFD_CUDA_TRY(cudaStreamSynchronize(st));
     auto t1 = std::chrono::steady_clock::now();
     if (info) {
@@ -387,6 +378,36 @@ void solve(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs, const double* f,
         info->t_solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
     }
     if (!converged) fail(GOFD_E_NOT_CONVERGED, "solver reached maxit before tol");
+}
+
+// b = h^{2s} I^T f (grid data) or h^{2s} D_h f (vertex data) on the interior
+void assemble_rhs(gofd_problem* p, gofd_rhs rhs, const double* f, double* b, cudaStream_t st) {
+    const int64_t n = p->nint;
+    const double h2s = std::pow(p->h, 2.0 * p->s);
+    if (rhs == GOFD_RHS_GRID) {
+        scatter_grid_f64(p, f, b, h2s, st);
+    } else {
+        rhs_vertex_kernel<<<grid_blocks(n, 256), 256, 0, st>>>(f, p->int2vert.as<int32_t>(), p->colsum.as<double>(),
+                                                             h2s, n, b);
+        GOFD_CHECK_LAUNCH();
+    }
+}
+
+void solve(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs, const double* f, double tol, int maxit,
+           bool init_zero, double* u, gofd_solve_info* info, cudaStream_t st) {
+    Workspace* w = ensure_ws(p);
+    double* b = w->b64.as<double>();
+    double* x = w->x64.as<double>();
+    assemble_rhs(p, rhs, f, b, st);
+    if (!init_zero) compact_vertex(p, true, u, x, st);
+    try {
+        solve_core(p, mode, b, tol, maxit, init_zero, x, info, st);
+    } catch (const Error& e) {
+        expand_interior(p, true, x, u, 0.0, st);   // the last iterate
+        throw;
+    }
+    expand_interior(p, true, x, u, 0.0, st);
+    GOFD_CUDA_TRY(cudaStreamSynchronize(st));
 }
 
 }  // namespace gofd

@@ -196,6 +196,18 @@ class Problem:
         self._check(st)
         return u, {k: getattr(info, k) for k, _ in N.SolveInfo._fields_}
 
+    def adjoint(self, f, u, grad_u, mode: str = "mixed", tol: float = 1e-10, maxit: int = 100000, stream=None):
+        """(dL/df, dL/dX) for the vertex-data solve u = S^{-1} h^{2s} D_h f given dL/du."""
+        torch = _torch()
+        gf = torch.empty(self.n_v, dtype=torch.float64, device=f.device)
+        gx = torch.empty((self.n_v, self.d), dtype=torch.float64, device=f.device)
+        info = N.SolveInfo()
+        g = grad_u.to(torch.float64).contiguous()
+        self._check(self._lib.gofd_adjoint(self._h, _MODES[mode], _ptr(f.contiguous()), _ptr(u.contiguous()),
+                                           _ptr(g), float(tol), int(maxit), _ptr(gf), _ptr(gx), C.byref(info),
+                                           _stream_ptr(stream)))
+        return gf, gx, {k: getattr(info, k) for k, _ in N.SolveInfo._fields_}
+
 
 def afd_apply_noalloc(d: int, n: int, lam_scaled, v, out=None, stream=None):
     """w = A_FD v (FP32) through the entry point that allocates nothing.
@@ -215,3 +227,41 @@ def afd_apply_noalloc(d: int, n: int, lam_scaled, v, out=None, stream=None):
     if st != 0:
         raise GofdError(st, lib.gofd_last_error(None).decode())
     return out
+
+
+class _SolveFunction:
+    """torch.autograd.Function for u = S(X)^{-1} h^{2s} D_h(X) f (vertex data)."""
+
+    _fn = None
+
+    @classmethod
+    def get(cls):
+        if cls._fn is None:
+            torch = _torch()
+
+            class Fn(torch.autograd.Function):
+                @staticmethod
+                def forward(ctx, f, X, simplices, alpha, h, box_lo, box_hi, tol, mode, opts):
+                    prob = Problem(X.detach().cpu().numpy(), simplices, alpha, h, box_lo, box_hi, **opts)
+                    fd = f.detach().to(torch.float64).contiguous()
+                    u, _ = prob.solve(fd, rhs="vertex", mode=mode, tol=tol)
+                    ctx.prob, ctx.tol, ctx.mode = prob, tol, mode
+                    ctx.save_for_backward(fd, u)
+                    return u
+
+                @staticmethod
+                def backward(ctx, grad_u):
+                    fd, u = ctx.saved_tensors
+                    gf, gx, _ = ctx.prob.adjoint(fd, u, grad_u, mode=ctx.mode, tol=ctx.tol)
+                    ctx.prob.close()
+                    return gf, gx, None, None, None, None, None, None, None, None
+
+            cls._fn = Fn
+        return cls._fn
+
+
+def solve(f, X, simplices, alpha, h, box_lo, box_hi, tol: float = 1e-10, mode: str = "mixed", **opts):
+    """Differentiable solve of (GoFD-3): returns u (N_v) for vertex data f (N_v)
+    and vertex coordinates X (N_v x d), both CUDA tensors; gradients flow to f
+    and X through the adjoint (the owner map of the grid nodes is held fixed)."""
+    return _SolveFunction.get().apply(f, X, simplices, alpha, h, box_lo, box_hi, tol, mode, opts)

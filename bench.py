@@ -55,7 +55,11 @@ WORKLOADS = {
     "lshape1024": "2D L-shape [-1,1]^2\\[0,1]^2, 6.05e4 vertices, 1024^2 grid in a 2048^2 circulant, alpha=1",
     "graded2048": "2D graded unit disk, 2.1e5 vertices, 2048^2 grid in a 4096^2 circulant, alpha=1.2",
     "ball256": "3D unit ball, 1.3e5 vertices, 256^3 grid in a 512^3 circulant, alpha=1.5",
+    "batch48": "48 instances (16 ring disks + 16 L-shapes, 5e3-1.5e5 vertices log-uniform, alpha cycling "
+               "0.5/1/1.5, grids 256^2-2048^2) x 8 right-hand sides (f=1 + 7 Gaussian bumps, width 0.1)",
 }
+BATCH_METRIC = "batched block-PCG: right-hand sides solved to rel-res 1e-8 per second (mixed), 1 GB300"
+BATCH_RHS = 8
 
 
 def workload(name="lshape1024", alpha=None):
@@ -340,6 +344,160 @@ def run_gofd(args):
     return 0
 
 
+def _min_height(v, s):
+    """Smallest triangle height: twice the area over the longest edge (2D)."""
+    p = v[s]
+    e0, e1, e2 = p[:, 1] - p[:, 0], p[:, 2] - p[:, 1], p[:, 0] - p[:, 2]
+    area2 = np.abs(e0[:, 0] * e2[:, 1] - e0[:, 1] * e2[:, 0])
+    longest = np.maximum(np.maximum(np.linalg.norm(e0, axis=1), np.linalg.norm(e1, axis=1)),
+                         np.linalg.norm(e2, axis=1))
+    return float(np.min(area2 / longest))
+
+
+def batch_grid_nodes(a_h):
+    """Smallest n in {256, 512, 1024, 2048} with 2/(n-1) <= a_h/2 (else 2048)."""
+    for n in (256, 512, 1024, 2048):
+        if 2.0 / (n - 1) <= 0.5 * a_h:
+            return n
+    return 2048
+
+
+def run_batch(args):
+    """The batched workload: every instance solves its 8 right-hand sides with
+    lock-step block PCG (FP32 inner, FP64 refinement, autotuned launch shapes),
+    all instances concurrently on their own streams.  A step is the whole
+    batch.  Compared with one right-hand side at a time in plain FP64 PCG."""
+    import torch
+    from paper_2307_14437_gb300 import Problem, solve_many
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    specs = mg.batch_instances()[rank::world]          # instances are independent: shard, no collective
+    meshes, probs, Fs, rows = {}, [], [], []
+    t0 = time.perf_counter()
+    for sp in specs:
+        key = (sp["kind"], sp["mesh"])
+        if key not in meshes:
+            meshes[key] = mg.batch_mesh(sp)
+        v, s = meshes[key]
+        n = batch_grid_nodes(_min_height(v, s))
+        lo, hi, h = mg.grid_box(2, n)
+        t1 = time.perf_counter()
+        pr = Problem(v, s, sp["alpha"], h, lo, hi)
+        t_setup = time.perf_counter() - t1
+        inside = mg.in_disk if sp["kind"] == "disk" else mg.in_lshape
+        F = mg.rhs_family(mg.grid_points(lo, h, n), BATCH_RHS, seed=sp["seed"] + 7, inside=inside)
+        probs.append(pr)
+        Fs.append(torch.tensor(F, device=dev))
+        rows.append({"kind": sp["kind"], "n_v": len(v), "n": n, "alpha": sp["alpha"], "setup_s": round(t_setup, 3)})
+    t_build = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    for pr, r in zip(probs, rows):
+        r["tuned_ms_per_product"] = round(pr.autotune(nb=BATCH_RHS), 4)
+    t_tune = time.perf_counter() - t1
+    torch.cuda.synchronize()
+
+    warm, steps = max(1, min(args.warmup, 1)), max(1, min(args.steps, 2))
+    for _ in range(warm):
+        solve_many(probs, Fs, mode="mixed", tol=1e-8)
+    clocks = Clocks(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for _ in range(steps):
+        out = solve_many(probs, Fs, mode="mixed", tol=1e-8)
+    torch.cuda.synchronize()
+    t_batch = (time.perf_counter() - t1) / steps
+    worst = max(i["rel_res_fp64"] for _, infos in out for i in infos)
+    for r, (_, infos) in zip(rows, out):
+        r["inner_iters"] = max(i["inner_iters"] for i in infos)
+
+    # end to end: right-hand sides from pinned host memory, solutions back to pinned host memory
+    Fh = [f.cpu().pin_memory() for f in Fs]
+    Uh = [torch.empty((BATCH_RHS, pr.n_v), dtype=torch.float64, pin_memory=True) for pr in probs]
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    Fd = [f.to(dev, non_blocking=True) for f in Fh]
+    res = solve_many(probs, Fd, mode="mixed", tol=1e-8)
+    for u_h, (U, _) in zip(Uh, res):
+        u_h.copy_(U, non_blocking=True)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t1
+
+    # one right-hand side at a time, plain FP64 PCG (no batching, no refinement)
+    t1 = time.perf_counter()
+    for pr, F in zip(probs, Fs):
+        for c in range(BATCH_RHS):
+            pr.solve(F[c].contiguous(), mode="fp64", tol=1e-8)
+    torch.cuda.synchronize()
+    t_single = time.perf_counter() - t1
+
+    # the batched FP32 product of the largest instance against the HBM roofline
+    big = max(range(len(probs)), key=lambda i: rows[i]["n"] * 1e9 + rows[i]["n_v"])
+    pr = probs[big]
+    inf = pr.info()
+    ld = inf["n_interior"] + 1
+    X = torch.zeros((BATCH_RHS, ld), dtype=torch.float32, device=dev)
+    X[:, :ld - 1] = torch.rand((BATCH_RHS, ld - 1), device=dev) * 2 - 1
+    Y = torch.empty_like(X)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        pr.apply_interior_batch(X, Y)
+    st = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(20)]
+    for a, b in ev:
+        flush.fill_(1.0)
+        a.record(st)
+        pr.apply_interior_batch(X, Y)
+        b.record(st)
+    torch.cuda.synchronize()
+    ms = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    B = BATCH_RHS * b_alg(2, inf["n_loc"], inf["n_v"], inf["n_grid"], inf["P"], 4) \
+        - (BATCH_RHS - 1) * 4 * (inf["P"] // 2 + 1) ** 2        # the symbol is read once per batch
+    hbm = peaks().get("hbm_gbs", 6800.0)
+    clk = clocks.stop()
+    nsolves = world * len(probs) * BATCH_RHS
+    t_max = t_batch
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_batch], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    if rank == 0:
+        line = {"metric": BATCH_METRIC, "value": round(nsolves / t_max, 3), "unit": "solves/s", "n_gpus": world,
+                "steps": steps, "warmup": warm, "ms_per_step": round(1e3 * t_max, 2), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 refinement)",
+                "data": "synthetic (seeded jittered Delaunay disks and L-shapes, f=1 + Gaussian bumps)",
+                "config": {"workload": WORKLOADS["batch48"], "instances": len(probs), "rhs_per_instance": BATCH_RHS,
+                           "grids": {str(k): sum(r["n"] == k for r in rows) for k in (256, 512, 1024, 2048)},
+                           "l2": "inputs larger than L2 for the large instances; no flush between solves",
+                           "build_s": round(t_build, 2), "autotune_s": round(t_tune, 2)},
+                "worst_rel_res_fp64": worst,
+                "one_at_a_time_fp64": {"s": round(t_single, 3), "solves_per_s": round(nsolves / t_single, 3),
+                                       "speedup_batched_mixed": round(t_single / t_batch, 3)},
+                "e2e": {"value": round(nsolves / t_e2e, 3), "unit": "solves/s",
+                        "h2d_bytes_per_step": int(sum(f.numel() * 8 for f in Fh)),
+                        "d2h_bytes_per_step": int(sum(u.numel() * 8 for u in Uh))},
+                "roofline": {"bound": "hbm", "kernel": "batched FP32 product (8 columns), largest instance",
+                             "instance": rows[big], "achieved": round(B / (ms * 1e-3) / 1e9, 1), "peak": hbm,
+                             "unit": "GB/s", "frac": round(B / (ms * 1e-3) / 1e9 / hbm, 4), "traffic": None,
+                             "ms": round(ms, 4)},
+                "instances": rows, "clocks": clk}
+        print(json.dumps(line), flush=True)
+    for pr in probs:
+        pr.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -354,6 +512,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch48":
+        return run_batch(args)
     return run_gofd(args)
 
 

@@ -177,6 +177,18 @@ gofd_status gofd_apply_interior(gofd_problem* p, gofd_precision prec,
                                 const void* x_dev, void* y_dev, void* stream);
 
 /*
+ * gofd_apply_interior_batch -- gofd_apply_interior on nb columns at once:
+ * column c of x at x_dev + c*ld (N_int+1 values, the last one 0), of y at
+ * y_dev + c*ld (N_int values written); ld >= N_int+1, x and y must not
+ * overlap.  In 2D the product kernels run over all columns in one launch
+ * each; other dimensions loop over the columns.  Results equal nb calls of
+ * gofd_apply_interior.  Allocates the batch workspace (see gofd_solve_batch)
+ * on first use.
+ */
+gofd_status gofd_apply_interior_batch(gofd_problem* p, gofd_precision prec, int nb, const void* x_dev,
+                                      int64_t ld, void* y_dev, void* stream);
+
+/*
  * gofd_apply_interior_profiled -- gofd_apply_interior with a CUDA event
  * recorded on `stream` after each kernel of the product; on return (the
  * stream is synchronised) stage_ms[i] holds the time of stage i in ms and
@@ -222,6 +234,39 @@ gofd_status gofd_solve(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs,
 gofd_status gofd_adjoint(gofd_problem* p, gofd_solve_mode mode, const double* f_dev, const double* u_dev,
                          const double* g_dev, double tol, int maxit, double* grad_f_dev,
                          double* grad_x_dev, gofd_solve_info* info, void* stream);
+
+/*
+ * gofd_solve_batch -- solve (GoFD-2) S u_c = b_c for nb right-hand sides on
+ * one mesh and grid, in lock step (block PCG: one batched product of S per
+ * iteration for all columns, per-column scalars and stopping).
+ *   f_dev   device, column c at f_dev + c*ldf (ldf >= n_grid for
+ *           GOFD_RHS_GRID, >= N_v for GOFD_RHS_VERTEX)
+ *   u_dev   device, N_v*nb doubles, column c at u_dev + c*N_v; the solutions
+ *           (boundary entries 0).  Always started from zero.
+ *   infos   optional, nb entries (iteration counts are those of the columns'
+ *           active rounds; t_solve_ms is the batch's wall time)
+ * Every column meets ||b_c - S u_c|| <= tol ||b_c|| with the FP64 operator,
+ * else GOFD_E_NOT_CONVERGED.  Allocates on the first call (or a larger nb)
+ * about (12 n_int + n_grid) * 8 bytes per column, plus (2D) a batch spectrum
+ * of (P/2+1) * round16(n) complex per column, and keeps it in the handle.
+ * The paper solves one right-hand side at a time; the batch is ours (many
+ * data f on one mesh share every set-up product).
+ */
+gofd_status gofd_solve_batch(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs, int nb,
+                             const double* f_dev, int64_t ldf, double tol, int maxit,
+                             double* u_dev, gofd_solve_info* infos, void* stream);
+
+/*
+ * gofd_autotune -- time the batched FP32 product with nb columns for each
+ * launch shape (grid lines per CTA in the row FFTs, columns per CTA in the
+ * column FFTs, lanes per row in the scatter) and keep the fastest in the
+ * handle for all later products.  *best_ms (may be NULL) receives its time
+ * per product of nb columns.  The FFT shapes leave every result bit
+ * unchanged; the scatter's lanes per row change the order of its row sums,
+ * so products may differ in the last bits between shapes (each shape is
+ * reproducible run to run).  Uses the batch workspace of gofd_solve_batch.
+ */
+gofd_status gofd_autotune(gofd_problem* p, int nb, void* stream, double* best_ms);
 
 /* gofd_get_info -- sizes and set-up results (host struct). */
 gofd_status gofd_get_info(const gofd_problem* p, gofd_info* info);

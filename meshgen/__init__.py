@@ -310,3 +310,73 @@ def grid_box(d: int, n: int, lo: float = -1.0, hi: float = 1.0):
     """Cube [lo,hi]^d with n nodes per axis: returns (box_lo, box_hi, h)."""
     h = (hi - lo) / (n - 1)
     return np.full(d, lo), np.full(d, hi), h
+
+
+def grid_points(box_lo, h: float, n: int) -> np.ndarray:
+    """Coordinates of all n^d nodes of the grid from box_lo with spacing h,
+    in linear order (axis 0 fastest)."""
+    lo = np.asarray(box_lo, dtype=np.float64).reshape(-1)
+    axes = [lo[a] + h * np.arange(n) for a in range(len(lo))]
+    mesh = np.meshgrid(*axes, indexing="ij")
+    return np.stack([m.reshape(-1, order="F") for m in mesh], axis=1)
+
+
+def in_disk(c: np.ndarray) -> bool:
+    return float(np.sum(c * c)) < 1.0
+
+
+def in_lshape(c: np.ndarray) -> bool:
+    return bool(_in_L(np.asarray(c, dtype=np.float64).reshape(1, -1))[0])
+
+
+def rhs_family(points: np.ndarray, k: int, seed: int, width: float = 0.1, inside=None) -> np.ndarray:
+    """k right-hand sides (k x len(points)): f = 1, then k-1 Gaussian bumps of
+    the given width with seeded centres uniform in the domain (rejection
+    sampling in [-1,1]^d against ``inside``; without it, in [-0.5,0.5]^d)."""
+    rng = np.random.default_rng(seed)
+    d = points.shape[1]
+    out = np.empty((k, len(points)))
+    out[0] = 1.0
+    for j in range(1, k):
+        if inside is None:
+            c = rng.uniform(-0.5, 0.5, size=d)
+        else:
+            c = rng.uniform(-1.0, 1.0, size=d)
+            while not inside(c):
+                c = rng.uniform(-1.0, 1.0, size=d)
+        out[j] = gaussian_bump(points, c, width)
+    return out
+
+
+# ----------------------------------------------------------------------------
+# the batched workload: 32 meshes (16 disks, 16 L-shapes), 48 instances
+# ----------------------------------------------------------------------------
+
+BATCH_ALPHAS = (0.5, 1.0, 1.5)
+
+
+def batch_instances(seed: int = seed_for(5)):
+    """Instance list of the batched workload: 16 ring-disk and 16 L-shape
+    meshes with vertex counts log-uniform in [5e3, 1.5e5]; mesh i of each kind
+    runs at alpha = BATCH_ALPHAS[i % 3], and the first 8 of each kind also at
+    the next alpha in the cycle (32 meshes, 48 instances).  Returns a list of
+    dicts {kind, mesh, target_vertices, alpha, seed}."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for kind in ("disk", "lshape"):
+        counts = np.exp(rng.uniform(np.log(5e3), np.log(1.5e5), size=16))
+        for i, nv in enumerate(counts):
+            ms = seed + 1000 * (kind == "lshape") + i
+            for rep in ((0, 1) if i < 8 else (0,)):
+                out.append({"kind": kind, "mesh": i, "target_vertices": int(nv),
+                            "alpha": BATCH_ALPHAS[(i + rep) % 3], "seed": int(ms)})
+    return out
+
+
+def batch_mesh(spec):
+    """The mesh of one batch instance (deterministic in spec's kind, target and seed)."""
+    nv = spec["target_vertices"]
+    if spec["kind"] == "disk":
+        rings = max(2, int(round(math.sqrt(nv / 3.0))))
+        return disk_ring_mesh(rings=rings, seed=spec["seed"])
+    return lshape_mesh(spacing=0.0076 * math.sqrt(60503.0 / nv), seed=spec["seed"])

@@ -51,11 +51,15 @@ EXPORTS = {
     "gofd_apply": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P]),
     "gofd_apply_host": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P]),
     "gofd_apply_interior": (C.c_int, [_P, C.c_int, _P, _P, _P]),
+    "gofd_apply_interior_batch": (C.c_int, [_P, C.c_int, C.c_int, _P, C.c_int64, _P, _P]),
     "gofd_apply_interior_profiled": (C.c_int, [_P, C.c_int, _P, _P, _P, C.POINTER(C.c_float),
                                                C.POINTER(C.c_char_p), C.c_int, C.POINTER(C.c_int)]),
     "gofd_solve": (C.c_int, [_P, C.c_int, C.c_int, _P, C.c_double, C.c_int, C.c_int, _P,
                              C.POINTER(SolveInfo), _P]),
     "gofd_adjoint": (C.c_int, [_P, C.c_int, _P, _P, _P, C.c_double, C.c_int, _P, _P, C.POINTER(SolveInfo), _P]),
+    "gofd_solve_batch": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, C.c_int64, C.c_double, C.c_int, _P,
+                                   _P, _P]),
+    "gofd_autotune": (C.c_int, [_P, C.c_int, _P, C.POINTER(C.c_double)]),
     "gofd_get_info": (C.c_int, [_P, C.POINTER(Info)]),
     "gofd_export_transfer": (C.c_int, [_P, _P, _P, _P]),
     "gofd_export_vertex_data": (C.c_int, [_P, _P, _P]),

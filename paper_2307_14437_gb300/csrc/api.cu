@@ -43,6 +43,7 @@ int circulant_length(int n) {
 }
 
 void release_all(gofd_problem* p) {
+    gofd::free_batch(p);
     gofd::free_adjoint(p);
     gofd::free_workspace(p);
     gofd::free_precond(p);
@@ -178,6 +179,18 @@ gofd_status gofd_apply_interior(gofd_problem* p, gofd_precision prec, const void
     })
 }
 
+gofd_status gofd_apply_interior_batch(gofd_problem* p, gofd_precision prec, int nb, const void* x_dev, int64_t ld,
+                                      void* y_dev, void* stream) {
+    if (!p) return GOFD_E_ARG;
+    GOFD_API_BODY(p, {
+        if (!x_dev || !y_dev) gofd::fail(GOFD_E_ARG, "NULL vector");
+        if (prec != GOFD_FP64 && prec != GOFD_FP32) gofd::fail(GOFD_E_ARG, "bad precision");
+        if (nb < 1 || nb > 4096) gofd::fail(GOFD_E_ARG, "nb must be in [1, 4096]");
+        if (ld < p->nint + 1) gofd::fail(GOFD_E_ARG, "ld must be >= n_interior + 1");
+        gofd::apply_batch(p, prec == GOFD_FP64, x_dev, y_dev, nb, ld, (cudaStream_t)stream);
+    })
+}
+
 gofd_status gofd_apply_interior_profiled(gofd_problem* p, gofd_precision prec, const void* x_dev, void* y_dev,
                                          void* stream, float* stage_ms, const char** stage_names, int cap,
                                          int* n_stages) {
@@ -246,6 +259,30 @@ gofd_status gofd_adjoint(gofd_problem* p, gofd_solve_mode mode, const double* f_
         if (mode != GOFD_SOLVE_FP64 && mode != GOFD_SOLVE_MIXED) gofd::fail(GOFD_E_ARG, "bad mode");
         if (!(tol > 0.0) || maxit < 1) gofd::fail(GOFD_E_ARG, "tol must be > 0 and maxit >= 1");
         gofd::adjoint(p, mode, f_dev, u_dev, g_dev, tol, maxit, grad_f_dev, grad_x_dev, info, (cudaStream_t)stream);
+    })
+}
+
+gofd_status gofd_solve_batch(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs, int nb, const double* f_dev,
+                             int64_t ldf, double tol, int maxit, double* u_dev, gofd_solve_info* infos,
+                             void* stream) {
+    if (!p) return GOFD_E_ARG;
+    GOFD_API_BODY(p, {
+        if (nb < 1 || nb > 4096) gofd::fail(GOFD_E_ARG, "nb must be in [1, 4096]");
+        if (!f_dev || !u_dev) gofd::fail(GOFD_E_ARG, "NULL vector");
+        if (mode != GOFD_SOLVE_FP64 && mode != GOFD_SOLVE_MIXED) gofd::fail(GOFD_E_ARG, "bad mode");
+        if (rhs != GOFD_RHS_GRID && rhs != GOFD_RHS_VERTEX) gofd::fail(GOFD_E_ARG, "bad rhs kind");
+        if (ldf < (rhs == GOFD_RHS_GRID ? p->ngrid : p->nv)) gofd::fail(GOFD_E_ARG, "ldf smaller than a column");
+        if (!(tol > 0.0) || maxit < 1) gofd::fail(GOFD_E_ARG, "tol must be > 0 and maxit >= 1");
+        gofd::solve_batch(p, mode, rhs, nb, f_dev, ldf, tol, maxit, u_dev, infos, (cudaStream_t)stream);
+    })
+}
+
+gofd_status gofd_autotune(gofd_problem* p, int nb, void* stream, double* best_ms) {
+    if (!p) return GOFD_E_ARG;
+    GOFD_API_BODY(p, {
+        if (nb < 1 || nb > 4096) gofd::fail(GOFD_E_ARG, "nb must be in [1, 4096]");
+        const double ms = gofd::autotune(p, nb, (cudaStream_t)stream);
+        if (best_ms) *best_ms = ms;
     })
 }
 

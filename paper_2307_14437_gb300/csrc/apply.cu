@@ -220,8 +220,10 @@ constexpr int SCATTER_CHUNK = 2048;
 template <class Real>
 __global__ void scatter_chunk_kernel(const int32_t* __restrict__ col, const Real* __restrict__ val,
                                      const Real* __restrict__ w, const int32_t* __restrict__ cbeg,
-                                     const int32_t* __restrict__ cend, Real* __restrict__ partial) {
+                                     const int32_t* __restrict__ cend, Real* __restrict__ partial, int64_t ws) {
     __shared__ Real part[256];
+    w += blockIdx.y * ws;
+    partial += (int64_t)blockIdx.y * gridDim.x;
     const int32_t b = cbeg[blockIdx.x], e = cend[blockIdx.x];
     Real a0 = 0, a1 = 0;
     int a = b + threadIdx.x;
@@ -243,7 +245,9 @@ __global__ void scatter_chunk_kernel(const int32_t* __restrict__ col, const Real
 template <class Real>
 __global__ void scatter_combine_kernel(const int32_t* __restrict__ rows, const int32_t* __restrict__ cptr,
                                        int64_t nrows, const Real* __restrict__ partial, Real* __restrict__ y,
-                                       Real scale) {
+                                       Real scale, int64_t nchunks, int64_t ys) {
+    partial += blockIdx.y * nchunks;
+    y += blockIdx.y * ys;
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrows; r += (int64_t)gridDim.x * blockDim.x) {
         Real s = 0;
         for (int c = cptr[r]; c < cptr[r + 1]; ++c) s += partial[c];
@@ -254,7 +258,9 @@ __global__ void scatter_combine_kernel(const int32_t* __restrict__ rows, const i
 template <class Real, int TPR>
 __global__ void scatter_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
                                const Real* __restrict__ val, const Real* __restrict__ w, int64_t nint,
-                               Real* __restrict__ y, Real scale) {
+                               Real* __restrict__ y, Real scale, int64_t ws, int64_t ys) {
+    w += blockIdx.y * ws;
+    y += blockIdx.y * ys;
     // the loop is uniform across each warp so that every lane reaches the
     // shuffles; four independent partial sums keep several loads in flight
     // (the summation order is fixed, so results are deterministic)
@@ -416,8 +422,8 @@ static void afd_core(gofd_problem* p, const ApplyCfg& c, const Real* x, const Re
                      cudaStream_t st) {
     using C = typename Cplx<Real>::T;
     if (p->d == 2) {
-        if (sizeof(Real) == 4) afd_2d_f32(p, (const float*)x, (const float*)vgrid, (float*)wgrid, st);
-        else afd_2d_f64(p, (const double*)x, (const double*)vgrid, (double*)wgrid, st);
+        if (sizeof(Real) == 4) afd_2d_f32(p, (const float*)x, (const float*)vgrid, (float*)wgrid, 1, 0, 0, nullptr, st);
+        else afd_2d_f64(p, (const double*)x, (const double*)vgrid, (double*)wgrid, 1, 0, 0, nullptr, st);
         return;
     }
     const int d = p->d, P = p->P, H = P / 2 + 1;
@@ -486,31 +492,40 @@ static void afd_core(gofd_problem* p, const ApplyCfg& c, const Real* x, const Re
     }
 }
 
+// y_b = scale * I^T w_b for nb right-hand sides (w_b = wgrid + b ws, y_b = y + b ys);
+// partial: nb x n_long_chunks scratch for the long rows (NULL: the handle's, nb = 1)
 template <class Real>
-static void scatter(gofd_problem* p, const Real* wgrid, Real* y, Real scale, cudaStream_t st) {
+static void scatter_b(gofd_problem* p, const Real* wgrid, Real* y, Real scale, int nb, int64_t ws, int64_t ys,
+                      Real* partial, cudaStream_t st) {
     const Real* val = reinterpret_cast<const Real*>(sizeof(Real) == 4 ? p->csr_val32.ptr : p->csr_val64.ptr);
     const double avg = p->nint ? (double)p->nnz_t / p->nint : 0;
     const int threads = 256;
-    if (avg > 96) {
-        scatter_kernel<Real, 32><<<grid_blocks(p->nint * 32, threads, 1 << 20), threads, 0, st>>>(
-            p->csr_ptr.as<int32_t>(), p->csr_col.as<int32_t>(), val, wgrid, p->nint, y, scale);
-    } else if (avg > 24) {
-        scatter_kernel<Real, 8><<<grid_blocks(p->nint * 8, threads, 1 << 20), threads, 0, st>>>(
-            p->csr_ptr.as<int32_t>(), p->csr_col.as<int32_t>(), val, wgrid, p->nint, y, scale);
-    } else {
-        scatter_kernel<Real, 4><<<grid_blocks(p->nint * 4, threads, 1 << 20), threads, 0, st>>>(
-            p->csr_ptr.as<int32_t>(), p->csr_col.as<int32_t>(), val, wgrid, p->nint, y, scale);
-    }
+    int tpr = avg > 96 ? 32 : (avg > 24 ? 8 : 4);
+    if (p->tune_tpr == 4 || p->tune_tpr == 8 || p->tune_tpr == 16 || p->tune_tpr == 32) tpr = p->tune_tpr;
+#define SCAT(TPR)                                                                                              \
+    scatter_kernel<Real, TPR><<<dim3(grid_blocks(p->nint * TPR, threads, 1 << 20), nb), threads, 0, st>>>(       \
+        p->csr_ptr.as<int32_t>(), p->csr_col.as<int32_t>(), val, wgrid, p->nint, y, scale, ws, ys)
+    if (tpr == 32) SCAT(32);
+    else if (tpr == 16) SCAT(16);
+    else if (tpr == 8) SCAT(8);
+    else SCAT(4);
+#undef SCAT
     GOFD_CHECK_LAUNCH();
     if (p->n_long_rows > 0) {
-        Real* part = reinterpret_cast<Real*>(p->long_partial.ptr);
-        scatter_chunk_kernel<Real><<<(unsigned)p->n_long_chunks, 256, 0, st>>>(
-            p->csr_col.as<int32_t>(), val, wgrid, p->chunk_beg.as<int32_t>(), p->chunk_end.as<int32_t>(), part);
-        scatter_combine_kernel<Real><<<grid_blocks(p->n_long_rows, 128), 128, 0, st>>>(
-            p->long_rows.as<int32_t>(), p->long_chunk_ptr.as<int32_t>(), p->n_long_rows, part, y, scale);
+        Real* part = partial ? partial : reinterpret_cast<Real*>(p->long_partial.ptr);
+        scatter_chunk_kernel<Real><<<dim3((unsigned)p->n_long_chunks, nb), 256, 0, st>>>(
+            p->csr_col.as<int32_t>(), val, wgrid, p->chunk_beg.as<int32_t>(), p->chunk_end.as<int32_t>(), part, ws);
+        scatter_combine_kernel<Real><<<dim3(grid_blocks(p->n_long_rows, 128), nb), 128, 0, st>>>(
+            p->long_rows.as<int32_t>(), p->long_chunk_ptr.as<int32_t>(), p->n_long_rows, part, y, scale,
+            p->n_long_chunks, ys);
         GOFD_CHECK_LAUNCH();
     }
     mark_stage(st, "scatter");
+}
+
+template <class Real>
+static void scatter(gofd_problem* p, const Real* wgrid, Real* y, Real scale, cudaStream_t st) {
+    scatter_b<Real>(p, wgrid, y, scale, 1, 0, 0, nullptr, st);
 }
 
 template <class Real>
@@ -552,6 +567,27 @@ int apply_interior_profiled(gofd_problem* p, bool fp64, const void* x, void* y, 
     for (int i = 0; i < 8; ++i) cudaEventDestroy(se.ev[i]);
     cudaEventDestroy(start);
     return n;
+}
+
+// Y[b] = S X[b] for nb interior vectors: X[b] = x + b ld (ld >= n_int + 1, pad
+// slot zero), Y[b] = y + b ld.  2D: one launch sequence over the batch with
+// the scratch of the batch workspace; otherwise one product per vector.
+void apply_interior_batch(gofd_problem* p, bool fp64, const void* x, void* y, int nb, int64_t ld, void* grid_ws,
+                          void* spec_ws, void* partial_ws, cudaStream_t st) {
+    if (p->d == 2) {
+        const int64_t ws = p->ngrid;
+        if (fp64) {
+            afd_2d_f64(p, (const double*)x, nullptr, (double*)grid_ws, nb, ld, ws, spec_ws, st);
+            scatter_b<double>(p, (const double*)grid_ws, (double*)y, 1.0, nb, ws, ld, (double*)partial_ws, st);
+        } else {
+            afd_2d_f32(p, (const float*)x, nullptr, (float*)grid_ws, nb, ld, ws, spec_ws, st);
+            scatter_b<float>(p, (const float*)grid_ws, (float*)y, 1.0f, nb, ws, ld, (float*)partial_ws, st);
+        }
+        return;
+    }
+    const size_t b = fp64 ? 8 : 4;
+    for (int k = 0; k < nb; ++k)
+        apply_interior(p, fp64, (const char*)x + k * ld * b, (char*)y + k * ld * b, st);
 }
 
 void afd_of_interior(gofd_problem* p, bool fp64, const void* x, void* wgrid, cudaStream_t st) {

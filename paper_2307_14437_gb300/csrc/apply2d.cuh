@@ -177,11 +177,16 @@ __global__ void __launch_bounds__(512) row_fwd_t_kernel(
     const Real* __restrict__ x, const int32_t* __restrict__ iidx, const Real* __restrict__ w, int64_t nloc,
     const int32_t* __restrict__ run_ptr, const int32_t* __restrict__ run_k0, const int32_t* __restrict__ run_len,
     const int32_t* __restrict__ run_e0, const Real* __restrict__ vgrid, int nlines, int n,
-    const typename Cplx<Real>::T* __restrict__ tw, typename Cplx<Real>::T* __restrict__ specT, int ld, int lpc) {
+    const typename Cplx<Real>::T* __restrict__ tw, typename Cplx<Real>::T* __restrict__ specT, int ld, int lpc,
+    int64_t xstride, int64_t sstride) {
     using C = typename Cplx<Real>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* sm = reinterpret_cast<C*>(smem_raw);
     constexpr int nthr = N / E;
+    // batch of right-hand sides along gridDim.y (strides 0 for one vector)
+    x += blockIdx.y * xstride;
+    if (vgrid) vgrid += blockIdx.y * xstride;
+    specT += blockIdx.y * sstride;
     const int g = threadIdx.x / nthr, t = threadIdx.x % nthr;
     const int line = blockIdx.x * lpc + g;
     const bool active = line < nlines;
@@ -299,8 +304,9 @@ __global__ void __launch_bounds__(512) row_fwd_t_kernel(
 template <class Real, int N, int E>
 __global__ void __launch_bounds__(N / E > 256 ? N / E : 256) col_conv_t_kernel(typename Cplx<Real>::T* __restrict__ specT, int ld, int n,
                                                        int H, const typename Cplx<Real>::T* __restrict__ tw,
-                                                       const Real* __restrict__ lamT) {
+                                                       const Real* __restrict__ lamT, int64_t sstride) {
     using C = typename Cplx<Real>::T;
+    specT += blockIdx.y * sstride;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* sm = reinterpret_cast<C*>(smem_raw);
     constexpr int nthr = N / E;
@@ -337,8 +343,11 @@ __global__ void __launch_bounds__(N / E > 256 ? N / E : 256) col_conv_t_kernel(t
 template <class Real, int N, int E>
 __global__ void __launch_bounds__(512) row_inv_t_kernel(const typename Cplx<Real>::T* __restrict__ specT, int ld,
                                                       int nlines, int n, const typename Cplx<Real>::T* __restrict__ tw,
-                                                      Real* __restrict__ wgrid, int lpc) {
+                                                      Real* __restrict__ wgrid, int lpc, int64_t sstride,
+                                                      int64_t wstride) {
     using C = typename Cplx<Real>::T;
+    specT += blockIdx.y * sstride;
+    wgrid += blockIdx.y * wstride;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* sm = reinterpret_cast<C*>(smem_raw);
     constexpr int nthr = N / E;

@@ -14,8 +14,15 @@ using C = Cplx<Real>::T;
 // elements per thread (largest radix) of the row and column transforms
 constexpr int ct_elems_row(int N) { return N >= 4096 ? 16 : 8; }
 constexpr int ct_elems_col(int N) { return N >= 4096 ? 16 : 8; }
-int lines_per_cta(int nthr) { return std::max(1, std::min(4, 512 / nthr)); }
-int cols_per_cta(int nthr) { return std::max(1, std::min(4, 256 / nthr)); }
+int lines_per_cta(int nthr, int tuned) {
+    if (tuned > 0 && tuned * nthr <= 512 && tuned <= 4) return tuned;
+    return std::max(1, std::min(4, 512 / nthr));
+}
+// the column kernel is compiled for at most max(N/E, 256) threads per CTA
+int cols_per_cta(int nthr, int tuned) {
+    if (tuned > 0 && tuned * nthr <= std::max(nthr, 256) && tuned <= 4) return tuned;
+    return std::max(1, std::min(4, 256 / nthr));
+}
 size_t row_smem(int N, int lpc) { return sizeof(C) * std::max<size_t>((size_t)spad_len(N) * lpc, (size_t)(N + 1) * lpc); }
 size_t col_smem(int N, int G) { return sizeof(C) * (size_t)spad_len(N) * G; }
 
@@ -27,45 +34,51 @@ void set_attrs(int limit) {
     GOFD_CUDA_TRY(cudaFuncSetAttribute(col_conv_t_kernel<Real, N, EC>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
 }
 
-// P = circulant length (column lines), rows use P/2
+// P = circulant length (column lines), rows use P/2; nb right-hand sides with
+// strides xs (input), ws (output grid) and the batch spectrum buffer
 template <int P>
-void run(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, cudaStream_t st) {
+void run(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, int nb, int64_t xs, int64_t ws, C* S,
+         cudaStream_t st) {
     constexpr int NR = P / 2, NC = P;
     constexpr int ER = ct_elems_row(NR), EC = ct_elems_col(NC);
     constexpr int tr = NR / ER, tc = NC / EC;
-    const int lpc = lines_per_cta(tr), G = cols_per_cta(tc);
+    const int lpc = lines_per_cta(tr, p->tune_lpc), G = cols_per_cta(tc, p->tune_cols);
     const int n = p->n[0], H = P / 2 + 1, nlines = (int)p->nlines;
     const C* tw = reinterpret_cast<const C*>(sizeof(Real) == 4 ? p->tw32.ptr : p->tw64.ptr);
     const Real* lamT = reinterpret_cast<const Real*>(sizeof(Real) == 4 ? p->lamT32.ptr : p->lamT64.ptr);
     const Real* w = reinterpret_cast<const Real*>(sizeof(Real) == 4 ? p->ell_w32.ptr : p->ell_w64.ptr);
-    C* S = p->specT.as<C>();
+    const int64_t ss = (int64_t)H * p->ldT;
     const unsigned rblocks = (unsigned)((nlines + lpc - 1) / lpc);
-    row_fwd_t_kernel<Real, 3, NR, ER><<<rblocks, lpc * tr, row_smem(NR, lpc), st>>>(
+    row_fwd_t_kernel<Real, 3, NR, ER><<<dim3(rblocks, nb), lpc * tr, row_smem(NR, lpc), st>>>(
         x, p->ell_iidx.as<int32_t>(), w, p->nloc, p->line_run_ptr.as<int32_t>(), p->run_k0.as<int32_t>(),
-        p->run_len.as<int32_t>(), p->run_e0.as<int32_t>(), vgrid, nlines, n, tw, S, p->ldT, lpc);
+        p->run_len.as<int32_t>(), p->run_e0.as<int32_t>(), vgrid, nlines, n, tw, S, p->ldT, lpc, xs, nb > 1 ? ss : 0);
     GOFD_CHECK_LAUNCH();
     mark_stage(st, "gather_row_fft");
-    col_conv_t_kernel<Real, NC, EC><<<(unsigned)((H + G - 1) / G), G * tc, col_smem(NC, G), st>>>(S, p->ldT, n, H, tw, lamT);
+    col_conv_t_kernel<Real, NC, EC><<<dim3((unsigned)((H + G - 1) / G), nb), G * tc, col_smem(NC, G), st>>>(
+        S, p->ldT, n, H, tw, lamT, nb > 1 ? ss : 0);
     GOFD_CHECK_LAUNCH();
     mark_stage(st, "col_fft_conv");
-    row_inv_t_kernel<Real, NR, ER><<<rblocks, lpc * tr, row_smem(NR, lpc), st>>>(S, p->ldT, nlines, n, tw, wgrid, lpc);
+    row_inv_t_kernel<Real, NR, ER><<<dim3(rblocks, nb), lpc * tr, row_smem(NR, lpc), st>>>(
+        S, p->ldT, nlines, n, tw, wgrid, lpc, nb > 1 ? ss : 0, ws);
     GOFD_CHECK_LAUNCH();
     mark_stage(st, "row_ifft");
 }
 
 }  // namespace
 
-void AFD2D_FN(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, cudaStream_t st) {
+void AFD2D_FN(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, int nb, int64_t xs, int64_t ws,
+              void* spec, cudaStream_t st) {
+    C* S = spec ? static_cast<C*>(spec) : p->specT.as<C>();
     switch (p->P) {
-        case 32: run<32>(p, x, vgrid, wgrid, st); break;
-        case 64: run<64>(p, x, vgrid, wgrid, st); break;
-        case 128: run<128>(p, x, vgrid, wgrid, st); break;
-        case 256: run<256>(p, x, vgrid, wgrid, st); break;
-        case 512: run<512>(p, x, vgrid, wgrid, st); break;
-        case 1024: run<1024>(p, x, vgrid, wgrid, st); break;
-        case 2048: run<2048>(p, x, vgrid, wgrid, st); break;
-        case 4096: run<4096>(p, x, vgrid, wgrid, st); break;
-        case 8192: run<8192>(p, x, vgrid, wgrid, st); break;
+        case 32: run<32>(p, x, vgrid, wgrid, nb, xs, ws, S, st); break;
+        case 64: run<64>(p, x, vgrid, wgrid, nb, xs, ws, S, st); break;
+        case 128: run<128>(p, x, vgrid, wgrid, nb, xs, ws, S, st); break;
+        case 256: run<256>(p, x, vgrid, wgrid, nb, xs, ws, S, st); break;
+        case 512: run<512>(p, x, vgrid, wgrid, nb, xs, ws, S, st); break;
+        case 1024: run<1024>(p, x, vgrid, wgrid, nb, xs, ws, S, st); break;
+        case 2048: run<2048>(p, x, vgrid, wgrid, nb, xs, ws, S, st); break;
+        case 4096: run<4096>(p, x, vgrid, wgrid, nb, xs, ws, S, st); break;
+        case 8192: run<8192>(p, x, vgrid, wgrid, nb, xs, ws, S, st); break;
         default: fail(GOFD_E_GRID, "unsupported circulant length");
     }
 }
@@ -78,7 +91,12 @@ void AFD2D_ATTR_FN(int limit, int P, size_t* need) {
         default: fail(GOFD_E_GRID, "unsupported circulant length");
     }
     const int tr = P / 2 / ct_elems_row(P / 2), tc = P / ct_elems_col(P);
-    *need = std::max(row_smem(P / 2, lines_per_cta(tr)), col_smem(P, cols_per_cta(tc)));
+    size_t nd = 0;
+    for (int k = 1; k <= 4; ++k) {   // every shape the autotuner may pick
+        if (k * tr <= 512) nd = std::max(nd, row_smem(P / 2, k));
+        if (k * tc <= std::max(tc, 256)) nd = std::max(nd, col_smem(P, k));
+    }
+    *need = nd;
 }
 
 }  // namespace gofd

@@ -1,0 +1,445 @@
+// Many right-hand sides on one problem: lock-step block PCG.
+//
+// nb right-hand sides advance together: every iteration applies S to all nb
+// search directions in one batched launch sequence (2D: the product kernels
+// run over a batch index; other dimensions: one product per column), and the
+// inner products are reduced per column in a fixed order.  Each column keeps
+// its own scalars and stops (alpha = 0 from then on) when its residual meets
+// its tolerance.  Mixed mode refines every column in FP64 around FP32 inner
+// solves, as the single-vector solver does.  The autotuner times the launch
+// shapes of the product (lines / columns per CTA, lanes per scatter row) on
+// the batch and keeps the fastest.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "gofd_internal.cuh"
+
+namespace gofd {
+
+constexpr int BRED_BLOCKS = 96;
+constexpr int BRED_THREADS = 256;
+
+struct BScal {
+    double rz, pq, alpha, beta, rr, r0, rtol, aux;
+    int done, pad;
+};
+
+struct BatchWork {
+    int cap = 0;
+    int64_t ld = 0;
+    DevBuf b64, x64, r64, p64, q64, z64, d64;
+    DevBuf r32, p32, q32, z32, d32;
+    DevBuf grid, spec, partial;
+    DevBuf red, cnt, scal, colv;
+    std::vector<BScal> host;
+};
+
+// ---------------------------------------------------------------------------
+// per-column fixed-order reductions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double bblock_sum(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double t = 0;
+    if (warp == 0) {
+        t = (lane < (int)(blockDim.x >> 5)) ? sh[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    }
+    __syncthreads();
+    return t;
+}
+
+// adds the block partials of column blockIdx.y in block order in the last block
+__device__ __forceinline__ bool bfinish(double mine, double* red, unsigned* cnt, double* total) {
+    __shared__ bool last;
+    double* part = red + (int64_t)blockIdx.y * gridDim.x;
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = mine;
+        __threadfence();
+        last = atomicAdd(&cnt[blockIdx.y], 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return false;
+    __shared__ double sh[32];
+    double v = 0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) v += ((volatile double*)part)[i];
+    v = bblock_sum(v, sh);
+    if (threadIdx.x == 0) {
+        *total = v;
+        cnt[blockIdx.y] = 0;
+    }
+    return true;
+}
+
+template <class V>
+__device__ __forceinline__ double bdot_local(const V* a, const V* b, int64_t n) {
+    double acc = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc += (double)a[i] * (double)b[i];
+    return acc;
+}
+
+// mode 0: rz = (r,z) init; 1: rz_new = (r,z) -> beta; 2: pq -> alpha; 3: aux = (a,a)
+template <class V>
+__global__ void bdot_kernel(const V* __restrict__ A, const V* __restrict__ B, int64_t n, int64_t ld, double* red,
+                            unsigned* cnt, BScal* s, int mode) {
+    __shared__ double sh[32];
+    const V* a = A + blockIdx.y * ld;
+    const V* b = B + blockIdx.y * ld;
+    double acc = bblock_sum(bdot_local(a, b, n), sh);
+    double tot;
+    if (bfinish(acc, red, cnt, &tot) && threadIdx.x == 0) {
+        BScal& c = s[blockIdx.y];
+        if (mode == 0) {
+            c.rz = tot;
+            c.beta = 0.0;
+        } else if (mode == 1) {
+            c.beta = c.done ? 0.0 : tot / c.rz;
+            c.rz = tot;
+        } else if (mode == 2) {
+            c.pq = tot;
+            c.alpha = (c.done || !(tot > 0.0)) ? 0.0 : c.rz / tot;
+            if (!(tot > 0.0)) c.done = 1;
+        } else {
+            c.aux = tot;
+        }
+    }
+}
+
+// x += alpha p; r -= alpha q; rr = (r,r); (no preconditioner: rz = rr, beta); done test
+template <class V>
+__global__ void bupdate_kernel(V* __restrict__ X, V* __restrict__ R, const V* __restrict__ Pp,
+                               const V* __restrict__ Q, int64_t n, int64_t ld, double* red, unsigned* cnt, BScal* s,
+                               int has_pc) {
+    __shared__ double sh[32];
+    const double a = s[blockIdx.y].alpha;
+    V* x = X + blockIdx.y * ld;
+    V* r = R + blockIdx.y * ld;
+    const V* p = Pp + blockIdx.y * ld;
+    const V* q = Q + blockIdx.y * ld;
+    double acc = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const V ri = (V)((double)r[i] - a * (double)q[i]);
+        x[i] = (V)((double)x[i] + a * (double)p[i]);
+        r[i] = ri;
+        acc += (double)ri * (double)ri;
+    }
+    acc = bblock_sum(acc, sh);
+    double tot;
+    if (bfinish(acc, red, cnt, &tot) && threadIdx.x == 0) {
+        BScal& c = s[blockIdx.y];
+        c.rr = tot;
+        if (!has_pc) {
+            c.beta = c.done ? 0.0 : tot / c.rz;
+            c.rz = tot;
+        }
+        if (sqrt(tot) <= c.rtol * c.r0) c.done = 1;
+    }
+}
+
+template <class V>
+__global__ void bupdate_p_kernel(V* __restrict__ Pp, const V* __restrict__ Z, int64_t n, int64_t ld,
+                                 const BScal* s) {
+    const double b = s[blockIdx.y].beta;
+    V* p = Pp + blockIdx.y * ld;
+    const V* z = Z + blockIdx.y * ld;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = (V)((double)z[i] + b * (double)p[i]);
+}
+
+__global__ void bset_start_kernel(BScal* s, const double* __restrict__ rtol, int nb) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nb; c += gridDim.x * blockDim.x) {
+        BScal& x = s[c];
+        x.r0 = sqrt(x.aux);
+        x.rr = x.aux;
+        x.rtol = rtol[c];
+        x.done = x.r0 == 0.0;
+        x.alpha = x.beta = 0.0;
+    }
+}
+
+template <class V>
+__global__ void bcopy_kernel(const V* __restrict__ a, V* __restrict__ b, int64_t n, int64_t ld) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[blockIdx.y * ld + i] = a[blockIdx.y * ld + i];
+}
+
+__global__ void bresidual_kernel(const double* __restrict__ B, const double* __restrict__ Y, double* __restrict__ R,
+                                 int64_t n, int64_t ld) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        R[blockIdx.y * ld + i] = B[blockIdx.y * ld + i] - Y[blockIdx.y * ld + i];
+}
+
+// R *= inv (per column, in place)
+__global__ void bscale_kernel(double* __restrict__ R, const double* __restrict__ inv, int64_t n, int64_t ld) {
+    const double s = inv[blockIdx.y];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        R[blockIdx.y * ld + i] *= s;
+}
+
+__global__ void baccumulate64_kernel(double* __restrict__ X, const double* __restrict__ D,
+                                     const double* __restrict__ sc, int64_t n, int64_t ld) {
+    const double s = sc[blockIdx.y];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        X[blockIdx.y * ld + i] += s * D[blockIdx.y * ld + i];
+}
+
+// r32 = r / ||r|| (columns already converged get 0)
+__global__ void bscale_to_f32_kernel(const double* __restrict__ R, float* __restrict__ R32,
+                                     const double* __restrict__ inv, int64_t n, int64_t ld) {
+    const double s = inv[blockIdx.y];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        R32[blockIdx.y * ld + i] = (float)(R[blockIdx.y * ld + i] * s);
+}
+
+__global__ void baccumulate_kernel(double* __restrict__ X, const float* __restrict__ D32, const double* __restrict__ sc,
+                                   int64_t n, int64_t ld) {
+    const double s = sc[blockIdx.y];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        X[blockIdx.y * ld + i] += s * (double)D32[blockIdx.y * ld + i];
+}
+
+// ---------------------------------------------------------------------------
+static BatchWork* ensure_batch(gofd_problem* p, int nb) {
+    BatchWork* w = p->batch;
+    if (w && w->cap >= nb) return w;
+    delete w;
+    w = new BatchWork();
+    p->batch = w;
+    w->cap = nb;
+    w->ld = p->nint + 1;
+    const int64_t m = w->ld * nb;
+    for (DevBuf* b : {&w->b64, &w->x64, &w->r64, &w->p64, &w->q64, &w->z64, &w->d64}) b->alloc(8 * m);
+    for (DevBuf* b : {&w->r32, &w->p32, &w->q32, &w->z32, &w->d32}) b->alloc(4 * m);
+    GOFD_CUDA_TRY(cudaMemset(w->p64.ptr, 0, 8 * m));
+    GOFD_CUDA_TRY(cudaMemset(w->p32.ptr, 0, 4 * m));
+    GOFD_CUDA_TRY(cudaMemset(w->x64.ptr, 0, 8 * m));
+    w->grid.alloc(8 * p->ngrid * nb);
+    if (p->d == 2) w->spec.alloc(sizeof(double2) * (size_t)(p->P / 2 + 1) * p->ldT * nb);
+    w->partial.alloc(8 * (p->n_long_chunks + 1) * nb);
+    w->red.alloc(8 * BRED_BLOCKS * nb);
+    w->cnt.alloc(sizeof(unsigned) * nb);
+    GOFD_CUDA_TRY(cudaMemset(w->cnt.ptr, 0, sizeof(unsigned) * nb));
+    w->scal.alloc(sizeof(BScal) * nb);
+    w->colv.alloc(8 * 3 * nb);
+    w->host.resize(nb);
+    return w;
+}
+
+void free_batch(gofd_problem* p) {
+    delete p->batch;
+    p->batch = nullptr;
+}
+
+static void read_bscal(BatchWork* w, int nb, cudaStream_t st) {
+    GOFD_CUDA_TRY(cudaMemcpyAsync(w->host.data(), w->scal.ptr, sizeof(BScal) * nb, cudaMemcpyDeviceToHost, st));
+    GOFD_CUDA_TRY(cudaStreamSynchronize(st));
+}
+
+// column norms^2 of A (FP64) into host vector
+static void bnorms(gofd_problem* p, BatchWork* w, const double* A, int nb, std::vector<double>& out, cudaStream_t st) {
+    bdot_kernel<double><<<dim3(BRED_BLOCKS, nb), BRED_THREADS, 0, st>>>(A, A, p->nint, w->ld, w->red.as<double>(),
+                                                                       w->cnt.as<unsigned>(), w->scal.as<BScal>(), 3);
+    GOFD_CHECK_LAUNCH();
+    read_bscal(w, nb, st);
+    out.resize(nb);
+    for (int c = 0; c < nb; ++c) out[c] = w->host[c].aux;
+}
+
+// block PCG on S D = R (all columns, precision V) from D = 0; column c stops at
+// ||r_c|| <= rtol[c] ||r_c(0)|| (rtol: device, nb entries)
+template <class V>
+static int bpcg(gofd_problem* p, BatchWork* w, int nb, V* D, V* R, V* Pd, V* Q, V* Z, const double* rtol, int maxit,
+                cudaStream_t st) {
+    const bool f64 = sizeof(V) == 8;
+    const int64_t n = p->nint, ld = w->ld;
+    BScal* s = w->scal.as<BScal>();
+    double* red = w->red.as<double>();
+    unsigned* cnt = w->cnt.as<unsigned>();
+    const dim3 vg(grid_blocks(n, 256, 512), nb);
+    const dim3 rg(BRED_BLOCKS, nb);
+    const bool pc = p->pc != nullptr;
+    const int check = p->opt.check_every > 0 ? p->opt.check_every : 8;
+    GOFD_CUDA_TRY(cudaMemsetAsync(D, 0, sizeof(V) * ld * nb, st));
+    V* ZZ = R;
+    if (pc) {
+        for (int c = 0; c < nb; ++c) precond_apply(p, f64, R + c * ld, Z + c * ld, st);
+        ZZ = Z;
+    }
+    // r0 and tolerances
+    {
+        bdot_kernel<V><<<rg, BRED_THREADS, 0, st>>>(R, R, n, ld, red, cnt, s, 3);
+        bset_start_kernel<<<1, 128, 0, st>>>(s, rtol, nb);
+        bdot_kernel<V><<<rg, BRED_THREADS, 0, st>>>(R, ZZ, n, ld, red, cnt, s, 0);
+        bcopy_kernel<V><<<vg, 256, 0, st>>>(ZZ, Pd, n, ld);
+        GOFD_CHECK_LAUNCH();
+    }
+    int it = 0;
+    while (it < maxit) {
+        apply_interior_batch(p, f64, Pd, Q, nb, ld, w->grid.ptr, w->spec.ptr, w->partial.ptr, st);
+        bdot_kernel<V><<<rg, BRED_THREADS, 0, st>>>(Pd, Q, n, ld, red, cnt, s, 2);
+        bupdate_kernel<V><<<rg, BRED_THREADS, 0, st>>>(D, R, Pd, Q, n, ld, red, cnt, s, pc ? 1 : 0);
+        if (pc) {
+            for (int c = 0; c < nb; ++c) precond_apply(p, f64, R + c * ld, Z + c * ld, st);
+            bdot_kernel<V><<<rg, BRED_THREADS, 0, st>>>(R, Z, n, ld, red, cnt, s, 1);
+        }
+        bupdate_p_kernel<V><<<vg, 256, 0, st>>>(Pd, ZZ, n, ld, s);
+        GOFD_CHECK_LAUNCH();
+        ++it;
+        if (it % check == 0 || it == maxit) {
+            read_bscal(w, nb, st);
+            bool all = true;
+            for (int c = 0; c < nb; ++c) all &= w->host[c].done != 0;
+            if (all) break;
+        }
+    }
+    return it;
+}
+
+void solve_batch(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs, int nb, const double* F, int64_t ldf,
+                 double tol, int maxit, double* U, gofd_solve_info* infos, cudaStream_t st) {
+    auto t0 = std::chrono::steady_clock::now();
+    BatchWork* w = ensure_batch(p, nb);
+    const int64_t n = p->nint, ld = w->ld;
+    double* B = w->b64.as<double>();
+    double* X = w->x64.as<double>();
+    double* R = w->r64.as<double>();
+    const dim3 vg(grid_blocks(n, 256, 512), nb);
+    for (int c = 0; c < nb; ++c) assemble_rhs(p, rhs, F + c * ldf, B + c * ld, st);
+    GOFD_CUDA_TRY(cudaMemsetAsync(X, 0, 8 * ld * nb, st));
+    std::vector<double> bn, rn;
+    bnorms(p, w, B, nb, bn, st);
+    for (double& v : bn) v = std::sqrt(v);
+    std::vector<int> outer(nb, 0), inner(nb, 0);
+    std::vector<double> rel(nb, 0.0);
+    int total_inner = 0, rounds = 0;
+    bool all_done = false;
+    while (rounds < 200 && total_inner < maxit) {
+        if (rounds == 0) {
+            bcopy_kernel<double><<<vg, 256, 0, st>>>(B, R, n, ld);
+        } else {
+            apply_interior_batch(p, true, X, w->q64.ptr, nb, ld, w->grid.ptr, w->spec.ptr, w->partial.ptr, st);
+            bresidual_kernel<<<vg, 256, 0, st>>>(B, w->q64.as<double>(), R, n, ld);
+        }
+        GOFD_CHECK_LAUNCH();
+        bnorms(p, w, R, nb, rn, st);
+        all_done = true;
+        std::vector<double> inv(nb), scale(nb);
+        for (int c = 0; c < nb; ++c) {
+            const double r = std::sqrt(rn[c]);
+            rel[c] = bn[c] > 0 ? r / bn[c] : 0.0;
+            const bool act = rel[c] > tol;
+            all_done &= !act;
+            inv[c] = act ? 1.0 / r : 0.0;
+            scale[c] = act ? r : 0.0;
+            if (act) ++outer[c];
+        }
+        if (all_done) break;
+        ++rounds;
+        const double itol = p->opt.inner_tol > 0 ? p->opt.inner_tol : 1e-4;
+        std::vector<double> colv(3 * nb);
+        for (int c = 0; c < nb; ++c) {
+            colv[c] = inv[c];
+            colv[nb + c] = scale[c];
+            // FP64: each column straight to its own tolerance; mixed: the inner FP32 tolerance
+            colv[2 * nb + c] = mode == GOFD_SOLVE_FP64 ? (scale[c] > 0 ? 0.5 * tol * bn[c] / scale[c] : 1.0) : itol;
+        }
+        GOFD_CUDA_TRY(cudaMemcpyAsync(w->colv.ptr, colv.data(), 8 * 3 * nb, cudaMemcpyHostToDevice, st));
+        const double* dinv = w->colv.as<double>();
+        const double* dscale = dinv + nb;
+        const double* drtol = dinv + 2 * nb;
+        int its;
+        if (mode == GOFD_SOLVE_FP64) {
+            // columns normalised to unit residual; converged columns are all zero and stay put
+            bscale_kernel<<<vg, 256, 0, st>>>(R, dinv, n, ld);
+            its = bpcg<double>(p, w, nb, w->d64.as<double>(), R, w->p64.as<double>(), w->q64.as<double>(),
+                               w->z64.as<double>(), drtol, maxit - total_inner, st);
+            baccumulate64_kernel<<<vg, 256, 0, st>>>(X, w->d64.as<double>(), dscale, n, ld);
+        } else {
+            bscale_to_f32_kernel<<<vg, 256, 0, st>>>(R, w->r32.as<float>(), dinv, n, ld);
+            its = bpcg<float>(p, w, nb, w->d32.as<float>(), w->r32.as<float>(), w->p32.as<float>(),
+                              w->q32.as<float>(), w->z32.as<float>(), drtol, maxit - total_inner, st);
+            baccumulate_kernel<<<vg, 256, 0, st>>>(X, w->d32.as<float>(), dscale, n, ld);
+        }
+        GOFD_CHECK_LAUNCH();
+        GOFD_CUDA_TRY(cudaStreamSynchronize(st));
+        total_inner += its;
+        for (int c = 0; c < nb; ++c)
+            if (scale[c] > 0) inner[c] += its;
+        if (its == 0) break;
+    }
+    for (int c = 0; c < nb; ++c) expand_interior(p, true, X + c * ld, U + c * p->nv, 0.0, st);
+    GOFD_CUDA_TRY(cudaStreamSynchronize(st));
+    auto t1 = std::chrono::steady_clock::now();
+    if (infos)
+        for (int c = 0; c < nb; ++c) {
+            gofd_solve_info& info = infos[c];
+            info.outer_iters = outer[c];
+            info.inner_iters = inner[c];
+            info.rel_res_fp64 = rel[c];
+            info.a_h = p->a_h;
+            info.min_colsum = p->min_colsum;
+            info.ic_shift = precond_shift(p);
+            const double dd = p->d;
+            info.h_within_strict_bound = p->h <= p->a_h / ((dd + 1) * std::sqrt(dd));
+            info.h_within_practical_bound = p->h <= p->a_h;
+            info.t_setup_ms = p->t_setup_ms;
+            info.t_solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+        }
+    if (!all_done) fail(GOFD_E_NOT_CONVERGED, "batched solver reached maxit before tol");
+}
+
+void apply_batch(gofd_problem* p, bool fp64, const void* x, void* y, int nb, int64_t ld, cudaStream_t st) {
+    BatchWork* w = ensure_batch(p, nb);
+    apply_interior_batch(p, fp64, x, y, nb, ld, w->grid.ptr, w->spec.ptr, w->partial.ptr, st);
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: time the batched FP32 product for each launch shape
+// ---------------------------------------------------------------------------
+double autotune(gofd_problem* p, int nb, cudaStream_t st) {
+    BatchWork* w = ensure_batch(p, nb);
+    const int64_t ld = w->ld;
+    GOFD_CUDA_TRY(cudaMemsetAsync(w->p32.ptr, 0, 4 * ld * nb, st));
+    cudaEvent_t a, b;
+    GOFD_CUDA_TRY(cudaEventCreate(&a));
+    GOFD_CUDA_TRY(cudaEventCreate(&b));
+    std::vector<int> shapes = p->d == 2 ? std::vector<int>{1, 2, 4} : std::vector<int>{0};
+    double best = 1e30;
+    int bl = 0, bc = 0, bt = 0;
+    for (int lpc : shapes)
+        for (int cols : shapes)
+            for (int tpr : {4, 8, 16, 32}) {
+                p->tune_lpc = lpc;
+                p->tune_cols = cols;
+                p->tune_tpr = tpr;
+                apply_interior_batch(p, false, w->p32.ptr, w->q32.ptr, nb, ld, w->grid.ptr, w->spec.ptr,
+                                     w->partial.ptr, st);   // warm
+                GOFD_CUDA_TRY(cudaEventRecord(a, st));
+                for (int r = 0; r < 5; ++r)
+                    apply_interior_batch(p, false, w->p32.ptr, w->q32.ptr, nb, ld, w->grid.ptr, w->spec.ptr,
+                                         w->partial.ptr, st);
+                GOFD_CUDA_TRY(cudaEventRecord(b, st));
+                GOFD_CUDA_TRY(cudaEventSynchronize(b));
+                float ms = 0;
+                GOFD_CUDA_TRY(cudaEventElapsedTime(&ms, a, b));
+                if (ms / 5 < best) {
+                    best = ms / 5;
+                    bl = lpc;
+                    bc = cols;
+                    bt = tpr;
+                }
+            }
+    p->tune_lpc = bl;
+    p->tune_cols = bc;
+    p->tune_tpr = bt;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return best;
+}
+
+}  // namespace gofd

@@ -79,6 +79,7 @@ struct Precond;   // defined in precond.cu
 struct Workspace;  // solver vectors, defined in solver.cu
 
 struct Adjoint;    // adjoint buffers, defined in adjoint.cu
+struct BatchWork;  // many-right-hand-side solver vectors, defined in batch.cu
 
 }  // namespace gofd
 
@@ -143,6 +144,7 @@ struct gofd_problem {
     gofd::DevBuf specB;        // 3D only: n x P x pitch0 complex
     gofd::DevBuf specT;        // 2D: transposed half spectrum, (P/2+1) x ldT complex
     int ldT = 0;               // 2D: leading dimension of specT (n rounded up to 16)
+    int tune_lpc = 0, tune_cols = 0, tune_tpr = 0;  // launch shapes picked by the autotuner (0 = default)
     gofd::DevBuf lamT64, lamT32;  // 2D: transposed scaled symbol
     gofd::DevBuf gridw;        // real [ngrid] (largest precision): A_FD v on the grid
     gofd::DevBuf xin;          // real [nint+1] compacted input (largest precision)
@@ -153,6 +155,7 @@ struct gofd_problem {
     gofd::Workspace* ws = nullptr;
     gofd::Precond* pc = nullptr;
     gofd::Adjoint* adj = nullptr;
+    gofd::BatchWork* batch = nullptr;
 
     double t_setup_ms = 0;
     std::string last_error;
@@ -169,8 +172,12 @@ void setup_coefficients(gofd_problem* p);
 // FFT-convolution apply (apply.cu)
 void setup_apply(gofd_problem* p);
 void setup_apply_2d(gofd_problem* p);
-void afd_2d_f32(gofd_problem* p, const float* x, const float* vgrid, float* wgrid, cudaStream_t st);
-void afd_2d_f64(gofd_problem* p, const double* x, const double* vgrid, double* wgrid, cudaStream_t st);
+// nb right-hand sides: inputs at x + b*xs (or vgrid + b*xs), outputs at wgrid + b*ws;
+// spec = batch spectrum buffer (nb x (P/2+1) x ldT complex) or NULL for one vector
+void afd_2d_f32(gofd_problem* p, const float* x, const float* vgrid, float* wgrid, int nb, int64_t xs, int64_t ws,
+                void* spec, cudaStream_t st);
+void afd_2d_f64(gofd_problem* p, const double* x, const double* vgrid, double* wgrid, int nb, int64_t xs,
+                int64_t ws, void* spec, cudaStream_t st);
 void apply_interior(gofd_problem* p, bool fp64, const void* x, void* y, cudaStream_t st);
 void afd_apply_grid(gofd_problem* p, bool fp64, const void* v, void* w, cudaStream_t st);
 void afd_apply_noalloc(int d, int n, const float* lam, const float* v, float* w, cudaStream_t st);
@@ -202,11 +209,19 @@ void precond_apply(gofd_problem* p, bool fp64, const void* r, void* z, cudaStrea
 int64_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t st);
 int grid_blocks(int64_t work, int threads, int cap = 152 * 16);
 void sort_packed_rows(const int32_t* ptr, int64_t nrows, int64_t* packed, int64_t nnz, cudaStream_t st);
+void apply_interior_batch(gofd_problem* p, bool fp64, const void* x, void* y, int nb, int64_t ld, void* grid_ws,
+                          void* spec_ws, void* partial_ws, cudaStream_t st);
 // w = A_FD I x on the grid for an interior-compacted x (n_int + 1 entries)
 void afd_of_interior(gofd_problem* p, bool fp64, const void* x, void* wgrid, cudaStream_t st);
 // adjoint (adjoint.cu)
 void adjoint(gofd_problem* p, gofd_solve_mode mode, const double* f, const double* u, const double* g, double tol,
              int maxit, double* grad_f, double* grad_x, gofd_solve_info* info, cudaStream_t st);
 void free_adjoint(gofd_problem* p);
+// many right-hand sides (batch.cu): F column c at F + c*ldf, U column c at U + c*nv
+void solve_batch(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs, int nb, const double* F, int64_t ldf,
+                 double tol, int maxit, double* U, gofd_solve_info* infos, cudaStream_t st);
+double autotune(gofd_problem* p, int nb, cudaStream_t st);
+void apply_batch(gofd_problem* p, bool fp64, const void* x, void* y, int nb, int64_t ld, cudaStream_t st);
+void free_batch(gofd_problem* p);
 
 }  // namespace gofd

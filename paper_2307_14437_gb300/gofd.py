@@ -153,6 +153,17 @@ class Problem:
         self._check(self._lib.gofd_apply_interior(self._h, _PREC[prec], _ptr(x), _ptr(y), _stream_ptr(stream)))
         return y
 
+    def apply_interior_batch(self, X, Y, stream=None):
+        """Y[c] = S X[c] for interior-compacted rows (X: nb x ld with ld >= n_int+1
+        and X[:, n_int] = 0; Y has the same shape and row stride)."""
+        torch = _torch()
+        prec = "fp64" if X.dtype == torch.float64 else "fp32"
+        if X.dim() != 2 or X.stride(1) != 1 or Y.stride() != X.stride():
+            raise TypeError("X and Y must be (nb, ld) with contiguous rows and the same strides")
+        self._check(self._lib.gofd_apply_interior_batch(self._h, _PREC[prec], int(X.shape[0]), _ptr(X),
+                                                        int(X.stride(0)), _ptr(Y), _stream_ptr(stream)))
+        return Y
+
     def apply_interior_profiled(self, x, y, stream=None):
         """apply_interior with per-stage CUDA-event times: returns [(name, ms), ...]."""
         torch = _torch()
@@ -196,6 +207,28 @@ class Problem:
         self._check(st)
         return u, {k: getattr(info, k) for k, _ in N.SolveInfo._fields_}
 
+    def solve_batch(self, F, rhs: str = "grid", mode: str = "mixed", tol: float = 1e-8, maxit: int = 100000,
+                    stream=None):
+        """Solve S u_c = b_c for the columns of F (nb x n_grid or nb x N_v, float64
+        CUDA, rows contiguous) in lock step; returns (U: nb x N_v, infos)."""
+        torch = _torch()
+        if F.dtype != torch.float64 or F.dim() != 2 or F.stride(1) != 1:
+            raise TypeError("F must be a float64 (nb, len) tensor with contiguous rows")
+        nb = F.shape[0]
+        U = torch.empty((nb, self.n_v), dtype=torch.float64, device=F.device)
+        infos = (N.SolveInfo * nb)()
+        st = self._lib.gofd_solve_batch(self._h, _MODES[mode], _RHS[rhs], int(nb), _ptr(F), int(F.stride(0)),
+                                        float(tol), int(maxit), _ptr(U), C.cast(infos, C.c_void_p),
+                                        _stream_ptr(stream))
+        self._check(st)
+        return U, [{k: getattr(i, k) for k, _ in N.SolveInfo._fields_} for i in infos]
+
+    def autotune(self, nb: int = 1, stream=None) -> float:
+        """Pick the fastest launch shapes of the batched product; returns ms per product."""
+        ms = C.c_double(0)
+        self._check(self._lib.gofd_autotune(self._h, int(nb), _stream_ptr(stream), C.byref(ms)))
+        return ms.value
+
     def adjoint(self, f, u, grad_u, mode: str = "mixed", tol: float = 1e-10, maxit: int = 100000, stream=None):
         """(dL/df, dL/dX) for the vertex-data solve u = S^{-1} h^{2s} D_h f given dL/du."""
         torch = _torch()
@@ -207,6 +240,43 @@ class Problem:
                                            _ptr(g), float(tol), int(maxit), _ptr(gf), _ptr(gx), C.byref(info),
                                            _stream_ptr(stream)))
         return gf, gx, {k: getattr(info, k) for k, _ in N.SolveInfo._fields_}
+
+
+def solve_many(problems, batches, rhs: str = "grid", mode: str = "mixed", tol: float = 1e-8,
+               maxit: int = 100000):
+    """Independent problems (meshes, grids) solved concurrently: problem i
+    solves the columns of batches[i] with solve_batch on a stream of its own,
+    from one host thread per problem (the C calls release the interpreter
+    lock).  Returns the list of (U, infos) in order."""
+    import threading
+    torch = _torch()
+    dev = torch.cuda.current_device()
+    streams = [torch.cuda.Stream() for _ in problems]
+    for s in streams:
+        s.wait_stream(torch.cuda.current_stream())
+    out = [None] * len(problems)
+    errs = [None] * len(problems)
+
+    def work(i):
+        try:
+            torch.cuda.set_device(dev)
+            with torch.cuda.stream(streams[i]):
+                out[i] = problems[i].solve_batch(batches[i], rhs=rhs, mode=mode, tol=tol, maxit=maxit,
+                                                 stream=streams[i])
+        except Exception as e:  # re-raised on the caller's thread
+            errs[i] = e
+
+    threads = [threading.Thread(target=work, args=(i,)) for i in range(len(problems))]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    for s in streams:
+        torch.cuda.current_stream().wait_stream(s)
+    for e in errs:
+        if e is not None:
+            raise e
+    return out
 
 
 def afd_apply_noalloc(d: int, n: int, lam_scaled, v, out=None, stream=None):

@@ -361,8 +361,8 @@ void setup_apply(gofd_problem* p) {
     const int64_t n = p->n[0];
     int64_t rowsA = p->nlines;
     size_t cbytes = sizeof(double2);
-    p->specA.alloc(cbytes * rowsA * p->pitch0);
-    if (d == 3) p->specB.alloc(cbytes * n * P * p->pitch0);
+    if (d == 1) p->specA.alloc(cbytes * rowsA * p->pitch0);   // 2D and 3D use their own layouts
+    (void)n;
     p->gridw.alloc(sizeof(double) * p->ngrid);
     p->xin.alloc(sizeof(double) * (p->nint + 1));
     p->yout.alloc(sizeof(double) * (p->nint + 1));
@@ -400,6 +400,7 @@ void setup_apply(gofd_problem* p) {
     set_smem_attrs<float>(limit);
     set_smem_attrs<double>(limit);
     if (d == 2) setup_apply_2d(p);
+    if (d == 3) setup_apply_3d(p);
 }
 
 // Optional stage markers: when non-null, an event is recorded on the stream
@@ -426,14 +427,18 @@ static void afd_core(gofd_problem* p, const ApplyCfg& c, const Real* x, const Re
         else afd_2d_f64(p, (const double*)x, (const double*)vgrid, (double*)wgrid, 1, 0, 0, nullptr, st);
         return;
     }
-    const int d = p->d, P = p->P, H = P / 2 + 1;
+    if (p->d == 3) {
+        if (sizeof(Real) == 4) afd_3d_f32(p, (const float*)x, (const float*)vgrid, (float*)wgrid, st);
+        else afd_3d_f64(p, (const double*)x, (const double*)vgrid, (double*)wgrid, st);
+        return;
+    }
+    // 1D: gather + real FFT, symbol, inverse real FFT
+    const int P = p->P, H = P / 2 + 1;
     const int64_t n = p->n[0];
     const C* tw = reinterpret_cast<const C*>(sizeof(Real) == 4 ? p->tw32.ptr : p->tw64.ptr);
     const Real* lam = reinterpret_cast<const Real*>(sizeof(Real) == 4 ? p->lam32.ptr : p->lam64.ptr);
     const Real* w = reinterpret_cast<const Real*>(sizeof(Real) == 4 ? p->ell_w32.ptr : p->ell_w64.ptr);
     C* A = p->specA.as<C>();
-    C* B = p->specB.as<C>();
-    const int tc = sizeof(Real) == 4 ? c.tc32 : c.tc64;
 
     // 1. gather + forward real FFT along axis 0
     {
@@ -446,41 +451,15 @@ static void afd_core(gofd_problem* p, const ApplyCfg& c, const Real* x, const Re
         x, p->ell_iidx.as<int32_t>(), w, p->nloc, p->line_run_ptr.as<int32_t>(), p->run_k0.as<int32_t>(), \
         p->run_len.as<int32_t>(), p->run_e0.as<int32_t>(), p->nlines, c.row, tw, A, p->pitch0, gfg, vgrid, \
         (int)n)
-        if (d == 1) ROWF(2);
-        else if (d == 2) ROWF(3);
-        else ROWF(4);
+        ROWF(2);
 #undef ROWF
         GOFD_CHECK_LAUNCH();
         mark_stage(st, "gather_row_fft");
     }
-    // 2. the other axes
-    const int threads_c = tc * c.col.nthr;
-    const size_t smc = col_smem<Real>(c, tc);
-    const unsigned cblocks = (unsigned)((H + tc - 1) / tc);
-    if (d == 1) {
-        spec_scale_kernel<Real><<<grid_blocks(H, 256), 256, 0, st>>>(A, lam, H);
-        GOFD_CHECK_LAUNCH();
-        mark_stage(st, "symbol_mul");
-    } else if (d == 2) {
-        ColDesc cd{0, p->pitch0, 0, p->pitch0, (int)n, (int)n, H, tc, 0, H, P};
-        col_fft_kernel<Real, 1><<<dim3(cblocks, 1), threads_c, smc, st>>>(A, A, cd, c.col, tw, lam);
-        GOFD_CHECK_LAUNCH();
-        mark_stage(st, "col_fft_conv");
-    } else {
-        const int64_t pt = p->pitch0;
-        ColDesc f{n * pt, pt, (int64_t)P * pt, pt, (int)n, P, H, tc, 0, 0, P};
-        col_fft_kernel<Real, 0><<<dim3(cblocks, (unsigned)n), threads_c, smc, st>>>(A, B, f, c.col, tw, lam);
-        GOFD_CHECK_LAUNCH();
-        mark_stage(st, "col_fft_fwd_axis1");
-        ColDesc m{pt, (int64_t)P * pt, pt, (int64_t)P * pt, (int)n, (int)n, H, tc, (int64_t)H, (int64_t)H * H, P};
-        col_fft_kernel<Real, 1><<<dim3(cblocks, (unsigned)P), threads_c, smc, st>>>(B, B, m, c.col, tw, lam);
-        GOFD_CHECK_LAUNCH();
-        mark_stage(st, "col_fft_conv_axis2");
-        ColDesc iv{(int64_t)P * pt, pt, n * pt, pt, P, (int)n, H, tc, 0, 0, P};
-        col_fft_kernel<Real, 2><<<dim3(cblocks, (unsigned)n), threads_c, smc, st>>>(B, A, iv, c.col, tw, lam);
-        GOFD_CHECK_LAUNCH();
-        mark_stage(st, "col_fft_inv_axis1");
-    }
+    // 2. 1D: the symbol multiply (2D and 3D take their own paths above)
+    spec_scale_kernel<Real><<<grid_blocks(H, 256), 256, 0, st>>>(A, lam, H);
+    GOFD_CHECK_LAUNCH();
+    mark_stage(st, "symbol_mul");
     // 3. inverse real FFT along axis 0
     {
         const int threads = c.lpc * c.row.nthr;

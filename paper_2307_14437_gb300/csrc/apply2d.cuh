@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(512) row_fwd_t_kernel(
 template <class Real, int N, int E>
 __global__ void __launch_bounds__(N / E > 256 ? N / E : 256) col_conv_t_kernel(typename Cplx<Real>::T* __restrict__ specT, int ld, int n,
                                                        int H, const typename Cplx<Real>::T* __restrict__ tw,
-                                                       const Real* __restrict__ lamT, int64_t sstride) {
+                                                       const Real* __restrict__ lamT, int64_t sstride, int pm) {
     using C = typename Cplx<Real>::T;
     specT += blockIdx.y * sstride;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -322,8 +322,16 @@ __global__ void __launch_bounds__(N / E > 256 ? N / E : 256) col_conv_t_kernel(t
     });
     fft_ct<false, N, E, false>(v, buf, t, g, tw, 1);
     {
-        // multiply by the (pre-scaled) symbol: row k_x1 folded to [0, N/2]
-        const Real* lc = lamT + (int64_t)(active ? col : 0) * H;
+        // multiply by the (pre-scaled) symbol: row k_x1 folded to [0, N/2].
+        // 2D (pm = 0): column = k_x0.  3D (pm = P): column = k_x0 * P + k_x1'
+        // with k_x1' folded too; the symbol row is (k_x0, fold(k_x1')).
+        const int cc = active ? col : 0;
+        int64_t lrow = cc;
+        if (pm) {
+            const int a = cc / pm, b = cc % pm;
+            lrow = (int64_t)a * H + (b <= pm / 2 ? b : pm - b);
+        }
+        const Real* lc = lamT + lrow * H;
         each_elem_r<ct_last<N, E, false>(), E>(t, nthr, N, [&](int i, int row) {
             const int fr = row <= N / 2 ? row : N - row;
             const Real l = __ldg(&lc[fr]);

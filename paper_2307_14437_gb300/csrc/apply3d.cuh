@@ -1,0 +1,82 @@
+// 3D stiffness product: kernels of the middle (axis 1, axis 2) stage.
+//
+// The axis-0 stages are the 2D row kernels over the n^2 grid lines: the
+// half spectrum is stored spec_T[k_x0][line] with line = k_1 + n k_2, so each
+// k_x0 plane is an n x n complex array (k_1 fastest).  Per plane the middle
+// stage is a 2D zero-padded FFT convolution:
+//
+//   plane_fwd_t   lines along k_1 (contiguous), forward FFT of length P over
+//                 the n nonzero entries, output stored transposed through a
+//                 shared-memory tile: M[k_x0][k_x1'][k_2] (k_2 fastest)
+//   col_conv_t    (shared with 2D) lines along k_2, contiguous in M: forward
+//                 FFT, times the symbol row (k_x0, k_x1'), inverse FFT, n kept
+//   plane_inv_t   transposed tile load of G lines along k_x1', inverse FFT of
+//                 length P, the n kept entries written back to spec_T
+//
+// G lines per CTA (at most 4: one named barrier id per line; at most
+// max(N/E, 256) threads per CTA).
+#pragma once
+
+#include "apply2d.cuh"
+
+namespace gofd {
+
+template <class Real, int N, int E>
+__global__ void __launch_bounds__(N / E > 256 ? N / E : 256) plane_fwd_t_kernel(
+    const typename Cplx<Real>::T* __restrict__ specT, int64_t ld, typename Cplx<Real>::T* __restrict__ M, int n,
+    int ngroups, const typename Cplx<Real>::T* __restrict__ tw) {
+    using C = typename Cplx<Real>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* sm = reinterpret_cast<C*>(smem_raw);
+    constexpr int nthr = N / E;
+    const int G = blockDim.x / nthr, msk = G - 1;
+    const int kx = blockIdx.x / ngroups, k20 = (blockIdx.x % ngroups) * G;
+    const int g = threadIdx.x / nthr, t = threadIdx.x % nthr;
+    const int k2 = k20 + g;
+    const bool active = k2 < n;
+    const C* line = specT + (int64_t)kx * ld + (int64_t)(active ? k2 : 0) * n;
+    C v[E];
+    each_elem_r<ct_radix_o(N, E, false, 0), E>(t, nthr, N, [&](int i, int pos) {
+        v[i] = (active && pos < n) ? line[pos] : cmk<C>(0.0, 0.0);
+    });
+    fft_ct<false, N, E, false>(v, sm + g * spad_len(N), t, g, tw, 1);
+    __syncthreads();   // the tile reuses the line buffers
+    each_elem_r<ct_last<N, E, false>(), E>(t, nthr, N, [&](int i, int pos) { sm[pos * G + (g ^ (pos & msk))] = v[i]; });
+    __syncthreads();
+    C* out = M + (int64_t)kx * N * n;
+    for (int i = threadIdx.x; i < N * G; i += blockDim.x) {
+        const int pos = i / G, l = i % G;
+        if (k20 + l < n) out[(int64_t)pos * n + k20 + l] = sm[pos * G + (l ^ (pos & msk))];
+    }
+}
+
+template <class Real, int N, int E>
+__global__ void __launch_bounds__(N / E > 256 ? N / E : 256) plane_inv_t_kernel(
+    const typename Cplx<Real>::T* __restrict__ M, int n, int ngroups, typename Cplx<Real>::T* __restrict__ specT,
+    int64_t ld, const typename Cplx<Real>::T* __restrict__ tw) {
+    using C = typename Cplx<Real>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C* sm = reinterpret_cast<C*>(smem_raw);
+    constexpr int nthr = N / E;
+    const int G = blockDim.x / nthr, msk = G - 1;
+    const int kx = blockIdx.x / ngroups, k20 = (blockIdx.x % ngroups) * G;
+    const C* in = M + (int64_t)kx * N * n;
+    for (int i = threadIdx.x; i < N * G; i += blockDim.x) {
+        const int pos = i / G, l = i % G;
+        sm[pos * G + (l ^ (pos & msk))] = (k20 + l < n) ? in[(int64_t)pos * n + k20 + l] : cmk<C>(0.0, 0.0);
+    }
+    __syncthreads();
+    const int g = threadIdx.x / nthr, t = threadIdx.x % nthr;
+    const int k2 = k20 + g;
+    C v[E];
+    each_elem_r<ct_radix_o(N, E, false, 0), E>(t, nthr, N, [&](int i, int pos) { v[i] = sm[pos * G + (g ^ (pos & msk))]; });
+    __syncthreads();   // the line buffers reuse the tile
+    fft_ct<true, N, E, false>(v, sm + g * spad_len(N), t, g, tw, 1);
+    if (k2 >= n) return;
+    C* line = specT + (int64_t)kx * ld + (int64_t)k2 * n;
+    each_elem_r<ct_last<N, E, false>(), E>(t, nthr, N, [&](int i, int pos) {
+        if (pos < n) line[pos] = v[i];
+    });
+}
+
+}  // namespace gofd

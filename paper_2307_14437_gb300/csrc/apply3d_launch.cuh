@@ -1,0 +1,93 @@
+// Host launchers of the 3D product, one precision per translation unit
+// (REAL is float or double): axis-0 row kernels over the n^2 grid lines,
+// then per k_x0 plane the (axis 1, axis 2) convolution of apply3d.cuh.
+#include "apply3d.cuh"
+
+namespace gofd {
+
+void mark_stage(cudaStream_t st, const char* name);
+
+namespace {
+
+using Real = REAL;
+using C = Cplx<Real>::T;
+
+constexpr int ct3_elems(int N) { return N >= 4096 ? 16 : 8; }
+int rows_per_cta(int nthr) { return std::max(1, std::min(4, 512 / nthr)); }
+int groups_per_cta(int nthr) { return std::max(1, std::min(4, 256 / nthr)); }
+size_t row_smem3(int N, int lpc) {
+    return sizeof(C) * std::max<size_t>((size_t)spad_len(N) * lpc, (size_t)(N + 1) * lpc);
+}
+size_t mid_smem3(int N, int G) { return sizeof(C) * std::max<size_t>((size_t)spad_len(N) * G, (size_t)N * G); }
+
+template <int P>
+void set_attrs3(int limit) {
+    constexpr int NR = P / 2, NC = P, ER = ct3_elems(NR), EC = ct3_elems(NC);
+    GOFD_CUDA_TRY(cudaFuncSetAttribute(row_fwd_t_kernel<Real, 4, NR, ER>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    GOFD_CUDA_TRY(cudaFuncSetAttribute(row_inv_t_kernel<Real, NR, ER>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    GOFD_CUDA_TRY(cudaFuncSetAttribute(plane_fwd_t_kernel<Real, NC, EC>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    GOFD_CUDA_TRY(cudaFuncSetAttribute(plane_inv_t_kernel<Real, NC, EC>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    GOFD_CUDA_TRY(cudaFuncSetAttribute(col_conv_t_kernel<Real, NC, EC>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+}
+
+template <int P>
+void run3(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, cudaStream_t st) {
+    constexpr int NR = P / 2, NC = P, ER = ct3_elems(NR), EC = ct3_elems(NC);
+    constexpr int tr = NR / ER, tc = NC / EC;
+    const int lpc = rows_per_cta(tr), G = groups_per_cta(tc);
+    const int n = p->n[0], H = P / 2 + 1, nlines = (int)p->nlines;
+    const C* tw = reinterpret_cast<const C*>(sizeof(Real) == 4 ? p->tw32.ptr : p->tw64.ptr);
+    const Real* lamT = reinterpret_cast<const Real*>(sizeof(Real) == 4 ? p->lamT32.ptr : p->lamT64.ptr);
+    const Real* w = reinterpret_cast<const Real*>(sizeof(Real) == 4 ? p->ell_w32.ptr : p->ell_w64.ptr);
+    C* S = p->specT.as<C>();
+    C* M = p->specM.as<C>();
+    const int64_t ld = p->ldT;
+    const unsigned rblocks = (unsigned)((nlines + lpc - 1) / lpc);
+    row_fwd_t_kernel<Real, 4, NR, ER><<<rblocks, lpc * tr, row_smem3(NR, lpc), st>>>(
+        x, p->ell_iidx.as<int32_t>(), w, p->nloc, p->line_run_ptr.as<int32_t>(), p->run_k0.as<int32_t>(),
+        p->run_len.as<int32_t>(), p->run_e0.as<int32_t>(), vgrid, nlines, n, tw, S, (int)ld, lpc, 0, 0);
+    GOFD_CHECK_LAUNCH();
+    mark_stage(st, "gather_row_fft");
+    const int ngroups = (n + G - 1) / G;
+    plane_fwd_t_kernel<Real, NC, EC><<<(unsigned)(H * ngroups), G * tc, mid_smem3(NC, G), st>>>(S, ld, M, n, ngroups, tw);
+    GOFD_CHECK_LAUNCH();
+    mark_stage(st, "plane_fft_axis1");
+    col_conv_t_kernel<Real, NC, EC><<<(unsigned)(((int64_t)H * P + G - 1) / G), G * tc, mid_smem3(NC, G), st>>>(
+        M, n, n, (int)((int64_t)H * P), tw, lamT, 0, P);
+    GOFD_CHECK_LAUNCH();
+    mark_stage(st, "conv_axis2");
+    plane_inv_t_kernel<Real, NC, EC><<<(unsigned)(H * ngroups), G * tc, mid_smem3(NC, G), st>>>(M, n, ngroups, S, ld, tw);
+    GOFD_CHECK_LAUNCH();
+    mark_stage(st, "plane_ifft_axis1");
+    row_inv_t_kernel<Real, NR, ER><<<rblocks, lpc * tr, row_smem3(NR, lpc), st>>>(S, (int)ld, nlines, n, tw, wgrid,
+                                                                                lpc, 0, 0);
+    GOFD_CHECK_LAUNCH();
+    mark_stage(st, "row_ifft");
+}
+
+}  // namespace
+
+void AFD3D_FN(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, cudaStream_t st) {
+    switch (p->P) {
+        case 32: run3<32>(p, x, vgrid, wgrid, st); break;
+        case 64: run3<64>(p, x, vgrid, wgrid, st); break;
+        case 128: run3<128>(p, x, vgrid, wgrid, st); break;
+        case 256: run3<256>(p, x, vgrid, wgrid, st); break;
+        case 512: run3<512>(p, x, vgrid, wgrid, st); break;
+        case 1024: run3<1024>(p, x, vgrid, wgrid, st); break;
+        default: fail(GOFD_E_GRID, "3D circulant length beyond 1024 (n > 513) is not supported");
+    }
+}
+
+void AFD3D_ATTR_FN(int limit, int P, size_t* need) {
+    switch (P) {
+#define ATTR(PP) case PP: set_attrs3<PP>(limit); break;
+        ATTR(32) ATTR(64) ATTR(128) ATTR(256) ATTR(512) ATTR(1024)
+#undef ATTR
+        default: fail(GOFD_E_GRID, "3D circulant length beyond 1024 (n > 513) is not supported");
+    }
+    const int tr = P / 2 / ct3_elems(P / 2), tc = P / ct3_elems(P);
+    *need = std::max(row_smem3(P / 2, rows_per_cta(tr)), mid_smem3(P, groups_per_cta(tc)));
+}
+
+}  // namespace gofd

@@ -142,10 +142,11 @@ struct gofd_problem {
     int pitch0 = 0;            // complex entries per spectrum row along axis 0 (>= P/2+1)
     gofd::DevBuf specA;        // complex, n_{d-1}..n_1 rows x pitch0 (largest precision)
     gofd::DevBuf specB;        // 3D only: n x P x pitch0 complex
-    gofd::DevBuf specT;        // 2D: transposed half spectrum, (P/2+1) x ldT complex
-    int ldT = 0;               // 2D: leading dimension of specT (n rounded up to 16)
+    gofd::DevBuf specT;        // 2D/3D: transposed half spectrum, (P/2+1) x ldT complex
+    int ldT = 0;               // leading dimension of specT (n^(d-1) rounded up to 16)
+    gofd::DevBuf specM;        // 3D: middle-stage buffer, (P/2+1) x P x n complex
     int tune_lpc = 0, tune_cols = 0, tune_tpr = 0;  // launch shapes picked by the autotuner (0 = default)
-    gofd::DevBuf lamT64, lamT32;  // 2D: transposed scaled symbol
+    gofd::DevBuf lamT64, lamT32;  // 2D/3D: scaled symbol with the axis order reversed
     gofd::DevBuf gridw;        // real [ngrid] (largest precision): A_FD v on the grid
     gofd::DevBuf xin;          // real [nint+1] compacted input (largest precision)
     gofd::DevBuf yout;         // real [nint]
@@ -172,6 +173,9 @@ void setup_coefficients(gofd_problem* p);
 // FFT-convolution apply (apply.cu)
 void setup_apply(gofd_problem* p);
 void setup_apply_2d(gofd_problem* p);
+void setup_apply_3d(gofd_problem* p);
+void afd_3d_f32(gofd_problem* p, const float* x, const float* vgrid, float* wgrid, cudaStream_t st);
+void afd_3d_f64(gofd_problem* p, const double* x, const double* vgrid, double* wgrid, cudaStream_t st);
 // nb right-hand sides: inputs at x + b*xs (or vgrid + b*xs), outputs at wgrid + b*ws;
 // spec = batch spectrum buffer (nb x (P/2+1) x ldT complex) or NULL for one vector
 void afd_2d_f32(gofd_problem* p, const float* x, const float* vgrid, float* wgrid, int nb, int64_t xs, int64_t ws,

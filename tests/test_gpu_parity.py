@@ -53,6 +53,9 @@ def _case(name):
     if name == "ball9":
         v, s = mg.ball_shell_mesh(shells=3, seed=mg.seed_for(3, 1))
         return 3, v, s, 9, 1.5, 2 ** 8
+    if name == "ball37_ragged":
+        v, s = mg.ball_shell_mesh(shells=5, seed=mg.seed_for(3, 2))
+        return 3, v, s, 37, 0.7, 2 ** 9
     if name == "aligned3":
         lo, hi, h = mg.grid_box(3, 7)
         v, s = mg.grid_aligned_mesh(3, -1.0, h, 4, origin_cells=1)
@@ -63,7 +66,7 @@ def _case(name):
     raise KeyError(name)
 
 
-SMALL = ["disk17", "disk37_ragged", "lshape33", "aligned2", "ball9", "aligned3", "interval33"]
+SMALL = ["disk17", "disk37_ragged", "lshape33", "aligned2", "ball9", "ball37_ragged", "aligned3", "interval33"]
 
 
 @pytest.fixture(scope="module")
@@ -74,7 +77,7 @@ def built():
         if name not in cache:
             d, v, s, n, alpha, M = _case(name)
             lo, hi, h = mg.grid_box(d, n)
-            ref = o.build(d, v, s, alpha, h, lo, hi, M=M)
+            ref = o.build(d, v, s, alpha, h, lo, hi, M=M, pruned=d == 3)
             gp = _gpu(v, s, alpha, h, lo, hi, filon_M=M)
             cache[name] = (gp, ref)
         return cache[name]

@@ -139,6 +139,9 @@ typedef struct {
  * element heights and a_h, the FD coefficients T by Filon quadrature with
  * Richardson extrapolation (Section 2.3), the circulant symbol (Section 2.2),
  * and, if requested, the IC preconditioner (Section 3.3).
+ * Grid limits: the same node count n on every axis, n <= 4097 in 1D and
+ * 2D, n <= 513 in 3D (circulant length P <= 8192, resp. 1024); beyond them
+ * GOFD_E_GRID.
  * Errors: GOFD_E_ARG, _DEGENERATE_SIMPLEX, _OUTSIDE_BOX, _GRID,
  * _TOO_FEW_GRID_NODES, _ZERO_COLSUM, _PRECOND, _CUDA, _NOMEM.
  */

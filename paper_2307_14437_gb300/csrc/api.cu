@@ -83,6 +83,7 @@ gofd_status gofd_build(int d, const double* vertices, int64_t n_v, const int32_t
         for (int i = 1; i < d; ++i)
             if (n[i] != n[0]) fail(GOFD_E_GRID, "the grid must have the same node count on every axis");
         if (n[0] > 4097) fail(GOFD_E_GRID, "at most 4097 grid nodes per axis (circulant length <= 8192)");
+        if (d == 3 && n[0] > 513) fail(GOFD_E_GRID, "3D: at most 513 grid nodes per axis (circulant length <= 1024)");
         int64_t ngrid = 1;
         for (int i = 0; i < d; ++i) ngrid *= n[i];
         if (ngrid > (int64_t)INT32_MAX) fail(GOFD_E_GRID, "more than 2^31-1 grid nodes");

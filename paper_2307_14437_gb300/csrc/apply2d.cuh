@@ -300,10 +300,11 @@ __global__ void __launch_bounds__(512) row_fwd_t_kernel(
 
 // ---------------------------------------------------------------------------
 // kernel 2: per spectrum column: FFT (n nonzero rows), symbol, inverse FFT
+// (ncols columns of stride ld; H = P/2+1 is the symbol's extent per axis)
 // ---------------------------------------------------------------------------
 template <class Real, int N, int E>
 __global__ void __launch_bounds__(N / E > 256 ? N / E : 256) col_conv_t_kernel(typename Cplx<Real>::T* __restrict__ specT, int ld, int n,
-                                                       int H, const typename Cplx<Real>::T* __restrict__ tw,
+                                                       int ncols, int H, const typename Cplx<Real>::T* __restrict__ tw,
                                                        const Real* __restrict__ lamT, int64_t sstride, int pm) {
     using C = typename Cplx<Real>::T;
     specT += blockIdx.y * sstride;
@@ -313,7 +314,7 @@ __global__ void __launch_bounds__(N / E > 256 ? N / E : 256) col_conv_t_kernel(t
     const int G = blockDim.x / nthr;
     const int g = threadIdx.x / nthr, t = threadIdx.x % nthr;
     const int col = blockIdx.x * G + g;
-    const bool active = col < H;
+    const bool active = col < ncols;
     C* buf = sm + g * spad_len(N);
     C* column = specT + (int64_t)(active ? col : 0) * ld;
     C v[E];

@@ -55,7 +55,7 @@ void run(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, int nb,
     GOFD_CHECK_LAUNCH();
     mark_stage(st, "gather_row_fft");
     col_conv_t_kernel<Real, NC, EC><<<dim3((unsigned)((H + G - 1) / G), nb), G * tc, col_smem(NC, G), st>>>(
-        S, p->ldT, n, H, tw, lamT, nb > 1 ? ss : 0, 0);
+        S, p->ldT, n, H, H, tw, lamT, nb > 1 ? ss : 0, 0);
     GOFD_CHECK_LAUNCH();
     mark_stage(st, "col_fft_conv");
     row_inv_t_kernel<Real, NR, ER><<<dim3(rblocks, nb), lpc * tr, row_smem(NR, lpc), st>>>(

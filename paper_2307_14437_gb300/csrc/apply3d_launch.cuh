@@ -53,7 +53,7 @@ void run3(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, cudaSt
     GOFD_CHECK_LAUNCH();
     mark_stage(st, "plane_fft_axis1");
     col_conv_t_kernel<Real, NC, EC><<<(unsigned)(((int64_t)H * P + G - 1) / G), G * tc, mid_smem3(NC, G), st>>>(
-        M, n, n, (int)((int64_t)H * P), tw, lamT, 0, P);
+        M, n, n, (int)((int64_t)H * P), H, tw, lamT, 0, P);
     GOFD_CHECK_LAUNCH();
     mark_stage(st, "conv_axis2");
     plane_inv_t_kernel<Real, NC, EC><<<(unsigned)(H * ngroups), G * tc, mid_smem3(NC, G), st>>>(M, n, ngroups, S, ld, tw);

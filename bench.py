@@ -248,9 +248,10 @@ def run_gofd(args):
         "col_fft_conv": 8 * n * H * 2 + 4 * H * H,
         "row_ifft": 8 * nl * H + 4 * n ** d,
         "scatter": inf["nnz_t"] * 8 + 4 * (nint + 1) + 4 * inf["nnz_t"] + 4 * nint,
-        "col_fft_fwd_axis1": 8 * nl * H + 8 * n * P * H,
-        "col_fft_conv_axis2": 2 * 8 * n * P * H + 4 * H ** 3,
-        "col_fft_inv_axis1": 8 * n * P * H + 8 * nl * H,
+        "plane_fft_axis1": 8 * nl * H + 8 * n * P * H,
+        "conv_axis2": 2 * 8 * n * P * H + 4 * H ** 3,
+        "plane_ifft_axis1": 8 * n * P * H + 8 * nl * H,
+        "symbol_mul": 2 * 8 * H + 4 * H,
     }
     pk = peaks()
     hbm = pk.get("hbm_gbs", 6800.0)

@@ -172,8 +172,10 @@ __device__ __forceinline__ Real sample(int k, const Runs& rs, const int32_t* __r
 // ---------------------------------------------------------------------------
 // kernel 1: gather + real FFT per grid line, transposed half spectrum out
 // ---------------------------------------------------------------------------
-template <class Real, int DP1, int N, int E>
-__global__ void __launch_bounds__(512) row_fwd_t_kernel(
+// MAXT / MINB: launch bounds (threads per CTA, CTAs per SM) the register
+// allocation is compiled for
+template <class Real, int DP1, int N, int E, int MAXT = 512, int MINB = 1>
+__global__ void __launch_bounds__(MAXT, MINB) row_fwd_t_kernel(
     const Real* __restrict__ x, const int32_t* __restrict__ iidx, const Real* __restrict__ w, int64_t nloc,
     const int32_t* __restrict__ run_ptr, const int32_t* __restrict__ run_k0, const int32_t* __restrict__ run_len,
     const int32_t* __restrict__ run_e0, const Real* __restrict__ vgrid, int nlines, int n,
@@ -302,8 +304,8 @@ __global__ void __launch_bounds__(512) row_fwd_t_kernel(
 // kernel 2: per spectrum column: FFT (n nonzero rows), symbol, inverse FFT
 // (ncols columns of stride ld; H = P/2+1 is the symbol's extent per axis)
 // ---------------------------------------------------------------------------
-template <class Real, int N, int E>
-__global__ void __launch_bounds__(N / E > 256 ? N / E : 256) col_conv_t_kernel(typename Cplx<Real>::T* __restrict__ specT, int ld, int n,
+template <class Real, int N, int E, int MAXT = (N / E > 256 ? N / E : 256), int MINB = 1>
+__global__ void __launch_bounds__(MAXT, MINB) col_conv_t_kernel(typename Cplx<Real>::T* __restrict__ specT, int ld, int n,
                                                        int ncols, int H, const typename Cplx<Real>::T* __restrict__ tw,
                                                        const Real* __restrict__ lamT, int64_t sstride, int pm) {
     using C = typename Cplx<Real>::T;
@@ -349,8 +351,8 @@ __global__ void __launch_bounds__(N / E > 256 ? N / E : 256) col_conv_t_kernel(t
 // ---------------------------------------------------------------------------
 // kernel 3: transposed tile in, inverse real FFT per line, n samples out
 // ---------------------------------------------------------------------------
-template <class Real, int N, int E>
-__global__ void __launch_bounds__(512) row_inv_t_kernel(const typename Cplx<Real>::T* __restrict__ specT, int ld,
+template <class Real, int N, int E, int MAXT = 512, int MINB = 1>
+__global__ void __launch_bounds__(MAXT, MINB) row_inv_t_kernel(const typename Cplx<Real>::T* __restrict__ specT, int ld,
                                                       int nlines, int n, const typename Cplx<Real>::T* __restrict__ tw,
                                                       Real* __restrict__ wgrid, int lpc, int64_t sstride,
                                                       int64_t wstride) {

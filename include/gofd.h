@@ -121,6 +121,9 @@ typedef struct {
     int precond_levels;        /* dependency levels of the IC factor (launches per triangular solve) */
     double ic_shift;
     double t_setup_ms;
+    int tune_lines_per_cta;    /* launch shapes in use (0 = built-in default; set by gofd_autotune):   */
+    int tune_cols_per_cta;     /*   grid lines per CTA of the row FFTs, columns per CTA of the column */
+    int tune_scatter_lanes;    /*   FFTs, lanes per row of the I^T scatter                            */
 } gofd_info;
 
 /*

@@ -311,6 +311,9 @@ gofd_status gofd_get_info(const gofd_problem* p, gofd_info* info) {
     info->precond_levels = gofd::precond_levels(p);
     info->ic_shift = gofd::precond_shift(p);
     info->t_setup_ms = p->t_setup_ms;
+    info->tune_lines_per_cta = p->tune_lpc;
+    info->tune_cols_per_cta = p->tune_cols;
+    info->tune_scatter_lanes = p->tune_tpr;
     return GOFD_OK;
 }
 

@@ -217,14 +217,11 @@ constexpr int SCATTER_LONG = 1024;
 // order, so the result does not depend on scheduling.
 constexpr int SCATTER_CHUNK = 2048;
 
+// Sum of one chunk of a long row by one CTA of 256 threads (fixed order:
+// strided lane sums, then a shared-memory tree); every thread returns it.
 template <class Real>
-__global__ void scatter_chunk_kernel(const int32_t* __restrict__ col, const Real* __restrict__ val,
-                                     const Real* __restrict__ w, const int32_t* __restrict__ cbeg,
-                                     const int32_t* __restrict__ cend, Real* __restrict__ partial, int64_t ws) {
-    __shared__ Real part[256];
-    w += blockIdx.y * ws;
-    partial += (int64_t)blockIdx.y * gridDim.x;
-    const int32_t b = cbeg[blockIdx.x], e = cend[blockIdx.x];
+__device__ __forceinline__ Real chunk_sum(const int32_t* __restrict__ col, const Real* __restrict__ val,
+                                          const Real* __restrict__ w, int32_t b, int32_t e, Real* part) {
     Real a0 = 0, a1 = 0;
     int a = b + threadIdx.x;
     for (; a + 256 < e; a += 512) {
@@ -239,32 +236,61 @@ __global__ void scatter_chunk_kernel(const int32_t* __restrict__ col, const Real
         if (threadIdx.x < o) part[threadIdx.x] += part[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) partial[blockIdx.x] = part[0];
+    return part[0];
 }
 
-template <class Real>
-__global__ void scatter_combine_kernel(const int32_t* __restrict__ rows, const int32_t* __restrict__ cptr,
-                                       int64_t nrows, const Real* __restrict__ partial, Real* __restrict__ y,
-                                       Real scale, int64_t nchunks, int64_t ys) {
-    partial += blockIdx.y * nchunks;
-    y += blockIdx.y * ys;
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrows; r += (int64_t)gridDim.x * blockDim.x) {
-        Real s = 0;
-        for (int c = cptr[r]; c < cptr[r + 1]; ++c) s += partial[c];
-        y[rows[r]] = s * scale;
-    }
-}
+// Long-row bookkeeping of the scatter (rows of I^T with more than
+// SCATTER_LONG entries, cut into chunks of SCATTER_CHUNK entries).
+struct LongRows {
+    const int32_t* cbeg;    // [nchunks] first entry of each chunk
+    const int32_t* cend;    // [nchunks] one past its last entry
+    const int32_t* crow;    // [nchunks] long-row index of each chunk
+    const int32_t* rows;    // [nrows] interior row of each long row
+    const int32_t* cptr;    // [nrows+1] chunks of each long row
+    int64_t nchunks, nrows;
+};
 
+// y_i = scale * sum_k val_k w[col_k] over row i of I^T, for nb right-hand sides
+// (grid y).  Blocks [0, nshort) take the rows of at most SCATTER_LONG entries,
+// TPR lanes per row; each further block takes one chunk of a long row, writes
+// its partial sum, and the last chunk of a row to finish (counted with an
+// atomic counter) adds the row's partials in chunk order.  Every sum has a
+// fixed order, so results are bitwise reproducible.
 template <class Real, int TPR>
-__global__ void scatter_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
-                               const Real* __restrict__ val, const Real* __restrict__ w, int64_t nint,
-                               Real* __restrict__ y, Real scale, int64_t ws, int64_t ys) {
+__global__ void __launch_bounds__(256) scatter_kernel(const int32_t* __restrict__ ptr, const int32_t* __restrict__ col,
+                                                      const Real* __restrict__ val, const Real* __restrict__ w,
+                                                      int64_t nint, Real* __restrict__ y, Real scale, int64_t ws,
+                                                      int64_t ys, unsigned nshort, LongRows lr, Real* partial,
+                                                      unsigned* counters) {
     w += blockIdx.y * ws;
     y += blockIdx.y * ys;
+    if (blockIdx.x >= nshort) {
+        __shared__ Real part[256];
+        __shared__ bool last;
+        const int64_t c = blockIdx.x - nshort;
+        Real* pp = partial + (int64_t)blockIdx.y * lr.nchunks;
+        unsigned* cnt = counters + (int64_t)blockIdx.y * lr.nrows;
+        const Real sum = chunk_sum<Real>(col, val, w, __ldg(&lr.cbeg[c]), __ldg(&lr.cend[c]), part);
+        const int r = __ldg(&lr.crow[c]);
+        const int c0 = __ldg(&lr.cptr[r]), c1 = __ldg(&lr.cptr[r + 1]);
+        if (threadIdx.x == 0) {
+            pp[c] = sum;
+            __threadfence();
+            last = atomicAdd(&cnt[r], 1u) == (unsigned)(c1 - c0 - 1);
+        }
+        __syncthreads();
+        if (last && threadIdx.x == 0) {
+            __threadfence();
+            Real acc = 0;
+            for (int k = c0; k < c1; ++k) acc += ((volatile Real*)pp)[k];
+            y[__ldg(&lr.rows[r])] = acc * scale;
+            cnt[r] = 0;   // ready for the next product
+        }
+        return;
+    }
     // the loop is uniform across each warp so that every lane reaches the
     // shuffles; four independent partial sums keep several loads in flight
-    // (the summation order is fixed, so results are deterministic)
-    const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+    const int64_t nthreads = (int64_t)nshort * blockDim.x;
     const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int lane = threadIdx.x % TPR;
     for (int64_t t0 = gid - (threadIdx.x & 31); t0 < nint * TPR; t0 += nthreads) {
@@ -368,7 +394,7 @@ void setup_apply(gofd_problem* p) {
     p->yout.alloc(sizeof(double) * (p->nint + 1));
     {
         // long rows of I^T and their chunks (set-up bookkeeping on the host)
-        std::vector<int32_t> ptr(p->nint + 1), rows, cptr(1, 0), cb, ce;
+        std::vector<int32_t> ptr(p->nint + 1), rows, cptr(1, 0), cb, ce, cr;
         GOFD_CUDA_TRY(cudaMemcpy(ptr.data(), p->csr_ptr.ptr, 4 * (p->nint + 1), cudaMemcpyDeviceToHost));
         for (int64_t i = 0; i < p->nint; ++i)
             if (ptr[i + 1] - ptr[i] > SCATTER_LONG) {
@@ -376,6 +402,7 @@ void setup_apply(gofd_problem* p) {
                 for (int32_t a = ptr[i]; a < ptr[i + 1]; a += SCATTER_CHUNK) {
                     cb.push_back(a);
                     ce.push_back(std::min(a + SCATTER_CHUNK, ptr[i + 1]));
+                    cr.push_back((int32_t)rows.size() - 1);
                 }
                 cptr.push_back((int32_t)cb.size());
             }
@@ -385,8 +412,12 @@ void setup_apply(gofd_problem* p) {
         p->long_chunk_ptr.alloc(4 * cptr.size());
         p->chunk_beg.alloc(4 * (cb.size() + 1));
         p->chunk_end.alloc(4 * (ce.size() + 1));
+        p->chunk_row.alloc(4 * (cr.size() + 1));
         p->long_partial.alloc(8 * (cb.size() + 1));
+        p->long_cnt.alloc(4 * (rows.size() + 1));
+        GOFD_CUDA_TRY(cudaMemset(p->long_cnt.ptr, 0, 4 * (rows.size() + 1)));
         if (!rows.empty()) {
+            GOFD_CUDA_TRY(cudaMemcpy(p->chunk_row.ptr, cr.data(), 4 * cr.size(), cudaMemcpyHostToDevice));
             GOFD_CUDA_TRY(cudaMemcpy(p->long_rows.ptr, rows.data(), 4 * rows.size(), cudaMemcpyHostToDevice));
             GOFD_CUDA_TRY(cudaMemcpy(p->long_chunk_ptr.ptr, cptr.data(), 4 * cptr.size(), cudaMemcpyHostToDevice));
             GOFD_CUDA_TRY(cudaMemcpy(p->chunk_beg.ptr, cb.data(), 4 * cb.size(), cudaMemcpyHostToDevice));
@@ -472,39 +503,37 @@ static void afd_core(gofd_problem* p, const ApplyCfg& c, const Real* x, const Re
 }
 
 // y_b = scale * I^T w_b for nb right-hand sides (w_b = wgrid + b ws, y_b = y + b ys);
-// partial: nb x n_long_chunks scratch for the long rows (NULL: the handle's, nb = 1)
+// partial / counters: nb x n_long_chunks reals and nb x n_long_rows zeroed
+// counters for the long rows (NULL: the handle's, nb = 1).  One launch.
 template <class Real>
 static void scatter_b(gofd_problem* p, const Real* wgrid, Real* y, Real scale, int nb, int64_t ws, int64_t ys,
-                      Real* partial, cudaStream_t st) {
+                      Real* partial, unsigned* counters, cudaStream_t st) {
     const Real* val = reinterpret_cast<const Real*>(sizeof(Real) == 4 ? p->csr_val32.ptr : p->csr_val64.ptr);
     const double avg = p->nint ? (double)p->nnz_t / p->nint : 0;
     const int threads = 256;
     int tpr = avg > 96 ? 32 : (avg > 24 ? 8 : 4);
     if (p->tune_tpr == 4 || p->tune_tpr == 8 || p->tune_tpr == 16 || p->tune_tpr == 32) tpr = p->tune_tpr;
+    LongRows lr{p->chunk_beg.as<int32_t>(), p->chunk_end.as<int32_t>(), p->chunk_row.as<int32_t>(),
+                p->long_rows.as<int32_t>(), p->long_chunk_ptr.as<int32_t>(), p->n_long_chunks, p->n_long_rows};
+    Real* part = partial ? partial : reinterpret_cast<Real*>(p->long_partial.ptr);
+    unsigned* cnt = counters ? counters : p->long_cnt.as<unsigned>();
+    const unsigned nshort = (unsigned)grid_blocks(p->nint * tpr, threads, 1 << 20);
+    const dim3 grid(nshort + (unsigned)p->n_long_chunks, nb);
 #define SCAT(TPR)                                                                                              \
-    scatter_kernel<Real, TPR><<<dim3(grid_blocks(p->nint * TPR, threads, 1 << 20), nb), threads, 0, st>>>(       \
-        p->csr_ptr.as<int32_t>(), p->csr_col.as<int32_t>(), val, wgrid, p->nint, y, scale, ws, ys)
+    scatter_kernel<Real, TPR><<<grid, threads, 0, st>>>(p->csr_ptr.as<int32_t>(), p->csr_col.as<int32_t>(), val,  \
+                                                        wgrid, p->nint, y, scale, ws, ys, nshort, lr, part, cnt)
     if (tpr == 32) SCAT(32);
     else if (tpr == 16) SCAT(16);
     else if (tpr == 8) SCAT(8);
     else SCAT(4);
 #undef SCAT
     GOFD_CHECK_LAUNCH();
-    if (p->n_long_rows > 0) {
-        Real* part = partial ? partial : reinterpret_cast<Real*>(p->long_partial.ptr);
-        scatter_chunk_kernel<Real><<<dim3((unsigned)p->n_long_chunks, nb), 256, 0, st>>>(
-            p->csr_col.as<int32_t>(), val, wgrid, p->chunk_beg.as<int32_t>(), p->chunk_end.as<int32_t>(), part, ws);
-        scatter_combine_kernel<Real><<<dim3(grid_blocks(p->n_long_rows, 128), nb), 128, 0, st>>>(
-            p->long_rows.as<int32_t>(), p->long_chunk_ptr.as<int32_t>(), p->n_long_rows, part, y, scale,
-            p->n_long_chunks, ys);
-        GOFD_CHECK_LAUNCH();
-    }
     mark_stage(st, "scatter");
 }
 
 template <class Real>
 static void scatter(gofd_problem* p, const Real* wgrid, Real* y, Real scale, cudaStream_t st) {
-    scatter_b<Real>(p, wgrid, y, scale, 1, 0, 0, nullptr, st);
+    scatter_b<Real>(p, wgrid, y, scale, 1, 0, 0, nullptr, nullptr, st);
 }
 
 template <class Real>
@@ -552,15 +581,15 @@ int apply_interior_profiled(gofd_problem* p, bool fp64, const void* x, void* y, 
 // slot zero), Y[b] = y + b ld.  2D: one launch sequence over the batch with
 // the scratch of the batch workspace; otherwise one product per vector.
 void apply_interior_batch(gofd_problem* p, bool fp64, const void* x, void* y, int nb, int64_t ld, void* grid_ws,
-                          void* spec_ws, void* partial_ws, cudaStream_t st) {
+                          void* spec_ws, void* partial_ws, void* counter_ws, cudaStream_t st) {
     if (p->d == 2) {
         const int64_t ws = p->ngrid;
         if (fp64) {
             afd_2d_f64(p, (const double*)x, nullptr, (double*)grid_ws, nb, ld, ws, spec_ws, st);
-            scatter_b<double>(p, (const double*)grid_ws, (double*)y, 1.0, nb, ws, ld, (double*)partial_ws, st);
+            scatter_b<double>(p, (const double*)grid_ws, (double*)y, 1.0, nb, ws, ld, (double*)partial_ws, (unsigned*)counter_ws, st);
         } else {
             afd_2d_f32(p, (const float*)x, nullptr, (float*)grid_ws, nb, ld, ws, spec_ws, st);
-            scatter_b<float>(p, (const float*)grid_ws, (float*)y, 1.0f, nb, ws, ld, (float*)partial_ws, st);
+            scatter_b<float>(p, (const float*)grid_ws, (float*)y, 1.0f, nb, ws, ld, (float*)partial_ws, (unsigned*)counter_ws, st);
         }
         return;
     }
@@ -621,8 +650,8 @@ void scatter_grid_f64(gofd_problem* p, const double* f, double* y, double scale,
 // the input and the output from the caller and keeps its spectrum scratch in
 // a fixed file-scope device array instead of any allocation.  Every GPU that
 // loads the library holds that array (8.1 MiB plus a 16 KiB twiddle table)
-// until the process exits.  It launches the same kernels as the handle-based
-// product.
+// until the process exits.  It launches the generic line-FFT kernels of this
+// file (gather-free row FFTs, column FFTs, inverse row FFTs).
 // ===========================================================================
 namespace gofd {
 

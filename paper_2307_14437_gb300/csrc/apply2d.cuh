@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(MAXT, MINB) row_fwd_t_kernel(
     }
     __syncthreads();
     // transposed tile: element (k, line g) at k*lpc + (g ^ (k & (lpc-1)))
-    const int msk = lpc - 1;
+    const int msk = lpc - 1, lsh = __ffs(lpc) - 1;   // lpc is a power of two
 #pragma unroll
     for (int j = 0; j < JMAX; ++j) {
         const int k = t + j * nthr;
@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(MAXT, MINB) row_fwd_t_kernel(
     __syncthreads();
     const int total = (N + 1) * lpc;
     for (int i = threadIdx.x; i < total; i += blockDim.x) {
-        const int k = i / lpc, l = i % lpc;
+        const int k = i >> lsh, l = i & msk;
         const int ln = blockIdx.x * lpc + l;
         if (ln < nlines) specT[(int64_t)k * ld + ln] = sm[k * lpc + (l ^ (k & msk))];
     }
@@ -362,10 +362,10 @@ __global__ void __launch_bounds__(MAXT, MINB) row_inv_t_kernel(const typename Cp
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* sm = reinterpret_cast<C*>(smem_raw);
     constexpr int nthr = N / E;
-    const int msk = lpc - 1;
+    const int msk = lpc - 1, lsh = __ffs(lpc) - 1;   // lpc is a power of two
     const int total = (N + 1) * lpc;
     for (int i = threadIdx.x; i < total; i += blockDim.x) {
-        const int k = i / lpc, l = i % lpc;
+        const int k = i >> lsh, l = i & msk;
         const int ln = blockIdx.x * lpc + l;
         sm[k * lpc + (l ^ (k & msk))] = (ln < nlines) ? specT[(int64_t)k * ld + ln] : cmk<C>(0.0, 0.0);
     }

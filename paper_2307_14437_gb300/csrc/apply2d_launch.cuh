@@ -15,12 +15,12 @@ using C = Cplx<Real>::T;
 constexpr int ct_elems_row(int N) { return N >= 4096 ? 16 : 8; }
 constexpr int ct_elems_col(int N) { return N >= 4096 ? 16 : 8; }
 int lines_per_cta(int nthr, int tuned) {
-    if (tuned > 0 && tuned * nthr <= 512 && tuned <= 4) return tuned;
+    if (tuned > 0 && (tuned & (tuned - 1)) == 0 && tuned * nthr <= 512 && tuned <= 4) return tuned;
     return std::max(1, std::min(4, 512 / nthr));
 }
 // the column kernel is compiled for at most max(N/E, 256) threads per CTA
 int cols_per_cta(int nthr, int tuned) {
-    if (tuned > 0 && tuned * nthr <= std::max(nthr, 256) && tuned <= 4) return tuned;
+    if (tuned > 0 && (tuned & (tuned - 1)) == 0 && tuned * nthr <= std::max(nthr, 256) && tuned <= 4) return tuned;
     return std::max(1, std::min(4, 256 / nthr));
 }
 size_t row_smem(int N, int lpc) { return sizeof(C) * std::max<size_t>((size_t)spad_len(N) * lpc, (size_t)(N + 1) * lpc); }

@@ -29,7 +29,7 @@ __global__ void __launch_bounds__(N / E > 256 ? N / E : 256) plane_fwd_t_kernel(
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* sm = reinterpret_cast<C*>(smem_raw);
     constexpr int nthr = N / E;
-    const int G = blockDim.x / nthr, msk = G - 1;
+    const int G = blockDim.x / nthr, msk = G - 1, gsh = __ffs(G) - 1;   // G is a power of two
     const int kx = blockIdx.x / ngroups, k20 = (blockIdx.x % ngroups) * G;
     const int g = threadIdx.x / nthr, t = threadIdx.x % nthr;
     const int k2 = k20 + g;
@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(N / E > 256 ? N / E : 256) plane_fwd_t_kernel(
     __syncthreads();
     C* out = M + (int64_t)kx * N * n;
     for (int i = threadIdx.x; i < N * G; i += blockDim.x) {
-        const int pos = i / G, l = i % G;
+        const int pos = i >> gsh, l = i & msk;
         if (k20 + l < n) out[(int64_t)pos * n + k20 + l] = sm[pos * G + (l ^ (pos & msk))];
     }
 }
@@ -58,11 +58,11 @@ __global__ void __launch_bounds__(N / E > 256 ? N / E : 256) plane_inv_t_kernel(
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* sm = reinterpret_cast<C*>(smem_raw);
     constexpr int nthr = N / E;
-    const int G = blockDim.x / nthr, msk = G - 1;
+    const int G = blockDim.x / nthr, msk = G - 1, gsh = __ffs(G) - 1;   // G is a power of two
     const int kx = blockIdx.x / ngroups, k20 = (blockIdx.x % ngroups) * G;
     const C* in = M + (int64_t)kx * N * n;
     for (int i = threadIdx.x; i < N * G; i += blockDim.x) {
-        const int pos = i / G, l = i % G;
+        const int pos = i >> gsh, l = i & msk;
         sm[pos * G + (l ^ (pos & msk))] = (k20 + l < n) ? in[(int64_t)pos * n + k20 + l] : cmk<C>(0.0, 0.0);
     }
     __syncthreads();

@@ -31,7 +31,7 @@ struct BatchWork {
     int64_t ld = 0;
     DevBuf b64, x64, r64, p64, q64, z64, d64;
     DevBuf r32, p32, q32, z32, d32;
-    DevBuf grid, spec, partial;
+    DevBuf grid, spec, partial, counters;
     DevBuf red, cnt, scal, colv;
     std::vector<BScal> host;
 };
@@ -221,6 +221,8 @@ static BatchWork* ensure_batch(gofd_problem* p, int nb) {
     w->grid.alloc(8 * p->ngrid * nb);
     if (p->d == 2) w->spec.alloc(sizeof(double2) * (size_t)(p->P / 2 + 1) * p->ldT * nb);
     w->partial.alloc(8 * (p->n_long_chunks + 1) * nb);
+    w->counters.alloc(4 * (p->n_long_rows + 1) * nb);
+    GOFD_CUDA_TRY(cudaMemset(w->counters.ptr, 0, 4 * (p->n_long_rows + 1) * nb));
     w->red.alloc(8 * BRED_BLOCKS * nb);
     w->cnt.alloc(sizeof(unsigned) * nb);
     GOFD_CUDA_TRY(cudaMemset(w->cnt.ptr, 0, sizeof(unsigned) * nb));
@@ -280,7 +282,7 @@ static int bpcg(gofd_problem* p, BatchWork* w, int nb, V* D, V* R, V* Pd, V* Q, 
     }
     int it = 0;
     while (it < maxit) {
-        apply_interior_batch(p, f64, Pd, Q, nb, ld, w->grid.ptr, w->spec.ptr, w->partial.ptr, st);
+        apply_interior_batch(p, f64, Pd, Q, nb, ld, w->grid.ptr, w->spec.ptr, w->partial.ptr, w->counters.ptr, st);
         bdot_kernel<V><<<rg, BRED_THREADS, 0, st>>>(Pd, Q, n, ld, red, cnt, s, 2);
         bupdate_kernel<V><<<rg, BRED_THREADS, 0, st>>>(D, R, Pd, Q, n, ld, red, cnt, s, pc ? 1 : 0);
         if (pc) {
@@ -322,7 +324,7 @@ void solve_batch(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs, int nb, co
         if (rounds == 0) {
             bcopy_kernel<double><<<vg, 256, 0, st>>>(B, R, n, ld);
         } else {
-            apply_interior_batch(p, true, X, w->q64.ptr, nb, ld, w->grid.ptr, w->spec.ptr, w->partial.ptr, st);
+            apply_interior_batch(p, true, X, w->q64.ptr, nb, ld, w->grid.ptr, w->spec.ptr, w->partial.ptr, w->counters.ptr, st);
             bresidual_kernel<<<vg, 256, 0, st>>>(B, w->q64.as<double>(), R, n, ld);
         }
         GOFD_CHECK_LAUNCH();
@@ -395,7 +397,7 @@ void solve_batch(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs, int nb, co
 
 void apply_batch(gofd_problem* p, bool fp64, const void* x, void* y, int nb, int64_t ld, cudaStream_t st) {
     BatchWork* w = ensure_batch(p, nb);
-    apply_interior_batch(p, fp64, x, y, nb, ld, w->grid.ptr, w->spec.ptr, w->partial.ptr, st);
+    apply_interior_batch(p, fp64, x, y, nb, ld, w->grid.ptr, w->spec.ptr, w->partial.ptr, w->counters.ptr, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -418,11 +420,11 @@ double autotune(gofd_problem* p, int nb, cudaStream_t st) {
                 p->tune_cols = cols;
                 p->tune_tpr = tpr;
                 apply_interior_batch(p, false, w->p32.ptr, w->q32.ptr, nb, ld, w->grid.ptr, w->spec.ptr,
-                                     w->partial.ptr, st);   // warm
+                                     w->partial.ptr, w->counters.ptr, st);   // warm
                 GOFD_CUDA_TRY(cudaEventRecord(a, st));
                 for (int r = 0; r < 5; ++r)
                     apply_interior_batch(p, false, w->p32.ptr, w->q32.ptr, nb, ld, w->grid.ptr, w->spec.ptr,
-                                         w->partial.ptr, st);
+                                         w->partial.ptr, w->counters.ptr, st);
                 GOFD_CUDA_TRY(cudaEventRecord(b, st));
                 GOFD_CUDA_TRY(cudaEventSynchronize(b));
                 float ms = 0;

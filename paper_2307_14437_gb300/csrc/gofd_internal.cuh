@@ -127,7 +127,8 @@ struct gofd_problem {
     int64_t nnz_t = 0;
     gofd::DevBuf colsum;       // double[nint]  D_h over interior vertices
     gofd::DevBuf long_rows;    // int32 [n_long_rows] rows of I^T with more than 1024 entries
-    gofd::DevBuf long_chunk_ptr, chunk_beg, chunk_end;  // chunks of the long rows
+    gofd::DevBuf long_chunk_ptr, chunk_beg, chunk_end, chunk_row;  // chunks of the long rows
+    gofd::DevBuf long_cnt;     // unsigned [n_long_rows] chunk counters (zero between products)
     gofd::DevBuf long_partial; // chunk partial sums (largest precision)
     int64_t n_long_rows = 0, n_long_chunks = 0;
     double a_h = 0, min_colsum = 0;
@@ -213,8 +214,10 @@ void precond_apply(gofd_problem* p, bool fp64, const void* r, void* z, cudaStrea
 int64_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t st);
 int grid_blocks(int64_t work, int threads, int cap = 152 * 16);
 void sort_packed_rows(const int32_t* ptr, int64_t nrows, int64_t* packed, int64_t nnz, cudaStream_t st);
+// partial_ws: nb x n_long_chunks reals (8 bytes each), counter_ws: nb x n_long_rows
+// unsigned, zero on entry and on exit
 void apply_interior_batch(gofd_problem* p, bool fp64, const void* x, void* y, int nb, int64_t ld, void* grid_ws,
-                          void* spec_ws, void* partial_ws, cudaStream_t st);
+                          void* spec_ws, void* partial_ws, void* counter_ws, cudaStream_t st);
 // w = A_FD I x on the grid for an interior-compacted x (n_int + 1 entries)
 void afd_of_interior(gofd_problem* p, bool fp64, const void* x, void* wgrid, cudaStream_t st);
 // adjoint (adjoint.cu)

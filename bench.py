@@ -192,6 +192,9 @@ def run_gofd(args):
     t0 = time.perf_counter()
     prob = Problem(v, s, alpha, h, lo, hi)
     t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    prob.autotune(nb=1)                      # launch shapes of the product (part of the set-up)
+    t_tune = time.perf_counter() - t0
     inf = prob.info()
     d, n_loc, n_v, nint, P = inf["d"], inf["n_loc"], inf["n_v"], inf["n_interior"], inf["P"]
     B32 = b_alg(d, n_loc, n_v, inf["n_grid"], P, 4)
@@ -286,6 +289,8 @@ def run_gofd(args):
     if not args.no_pcg and args.workload == "lshape1024":
         for a in ALPHAS:
             pa = prob if a == alpha else Problem(v, s, a, h, lo, hi)
+            if pa is not prob:
+                pa.autotune(nb=1)
             f = torch.ones(pa.n_grid, dtype=torch.float64, device=dev)
             row = {"setup_s": round(t_setup, 3) if a == alpha else None}
             for mode in ("mixed", "fp64"):
@@ -327,7 +332,11 @@ def run_gofd(args):
                 "config": {"workload": WORKLOADS[args.workload] + ", FP32 stiffness product (%d vertices, %d interior)"
                                        % (n_v, nint),
                            "l2": "flushed (256 MB write) before every timed step",
-                           "n_loc": n_loc, "setup_s": round(t_setup, 3)},
+                           "n_loc": n_loc, "setup_s": round(t_setup, 3), "autotune_s": round(t_tune, 3),
+                           "launch_shapes": {"lines_per_cta": inf["tune_lines_per_cta"],
+                                             "cols_per_cta": inf["tune_cols_per_cta"],
+                                             "scatter_lanes": inf["tune_scatter_lanes"],
+                                             "col_elems": inf["tune_col_elems"]}},
                 "roofline": roofline, "e2e": e2e, "pcg": pcg,
                 "gpu_launches": 4 * args.steps, "clocks": clk}
         if world == 1 and not args.no_cpu and args.workload == "lshape1024":

@@ -123,7 +123,8 @@ typedef struct {
     double t_setup_ms;
     int tune_lines_per_cta;    /* launch shapes in use (0 = built-in default; set by gofd_autotune):   */
     int tune_cols_per_cta;     /*   grid lines per CTA of the row FFTs, columns per CTA of the column */
-    int tune_scatter_lanes;    /*   FFTs, lanes per row of the I^T scatter                            */
+    int tune_scatter_lanes;    /*   FFTs, lanes per row of the I^T scatter,                           */
+    int tune_col_elems;        /*   elements per thread of the column FFTs                            */
 } gofd_info;
 
 /*
@@ -264,13 +265,16 @@ gofd_status gofd_solve_batch(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs
 
 /*
  * gofd_autotune -- time the batched FP32 product with nb columns for each
- * launch shape (grid lines per CTA in the row FFTs, columns per CTA in the
- * column FFTs, lanes per row in the scatter) and keep the fastest in the
- * handle for all later products.  *best_ms (may be NULL) receives its time
- * per product of nb columns.  The FFT shapes leave every result bit
- * unchanged; the scatter's lanes per row change the order of its row sums,
- * so products may differ in the last bits between shapes (each shape is
- * reproducible run to run).  Uses the batch workspace of gofd_solve_batch.
+ * launch shape (elements per thread of the column FFTs, grid lines per CTA
+ * in the row FFTs, columns per CTA in the column FFTs, lanes per row in the
+ * scatter; one choice at a time with the others at their best so far) and
+ * keep the fastest in the handle for all later products.  *best_ms (may be
+ * NULL) receives its time per product of nb columns.  CTA shapes leave every
+ * result bit unchanged; the column elements per thread (the FFT's radix
+ * plan) and the scatter's lanes per row change the rounding order, so
+ * products may differ in the last bits between choices (each choice is
+ * reproducible run to run).  Uses the batch workspace of gofd_solve_batch
+ * and drops the solvers' captured CUDA graphs.
  */
 gofd_status gofd_autotune(gofd_problem* p, int nb, void* stream, double* best_ms);
 

@@ -314,6 +314,7 @@ gofd_status gofd_get_info(const gofd_problem* p, gofd_info* info) {
     info->tune_lines_per_cta = p->tune_lpc;
     info->tune_cols_per_cta = p->tune_cols;
     info->tune_scatter_lanes = p->tune_tpr;
+    info->tune_col_elems = p->tune_cole;
     return GOFD_OK;
 }
 

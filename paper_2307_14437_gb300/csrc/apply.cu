@@ -262,6 +262,7 @@ __global__ void __launch_bounds__(256) scatter_kernel(const int32_t* __restrict_
                                                       int64_t nint, Real* __restrict__ y, Real scale, int64_t ws,
                                                       int64_t ys, unsigned nshort, LongRows lr, Real* partial,
                                                       unsigned* counters) {
+    pdl_enter();
     w += blockIdx.y * ws;
     y += blockIdx.y * ys;
     if (blockIdx.x >= nshort) {
@@ -520,8 +521,8 @@ static void scatter_b(gofd_problem* p, const Real* wgrid, Real* y, Real scale, i
     const unsigned nshort = (unsigned)grid_blocks(p->nint * tpr, threads, 1 << 20);
     const dim3 grid(nshort + (unsigned)p->n_long_chunks, nb);
 #define SCAT(TPR)                                                                                              \
-    scatter_kernel<Real, TPR><<<grid, threads, 0, st>>>(p->csr_ptr.as<int32_t>(), p->csr_col.as<int32_t>(), val,  \
-                                                        wgrid, p->nint, y, scale, ws, ys, nshort, lr, part, cnt)
+    launch_pdl(scatter_kernel<Real, TPR>, grid, dim3(threads), 0, st, p->csr_ptr.as<int32_t>(),                   \
+               p->csr_col.as<int32_t>(), val, wgrid, p->nint, y, scale, ws, ys, nshort, lr, part, cnt)
     if (tpr == 32) SCAT(32);
     else if (tpr == 16) SCAT(16);
     else if (tpr == 8) SCAT(8);

@@ -31,6 +31,10 @@ __device__ __forceinline__ void group_sync(int g, int nthr) {
         __syncthreads();
         return;
     }
+    if (nthr == 32) {   // one warp per line
+        __syncwarp();
+        return;
+    }
     switch (g) {
         case 0: asm volatile("bar.sync 1, %0;" ::"r"(nthr) : "memory"); break;
         case 1: asm volatile("bar.sync 2, %0;" ::"r"(nthr) : "memory"); break;
@@ -181,6 +185,7 @@ __global__ void __launch_bounds__(MAXT, MINB) row_fwd_t_kernel(
     const int32_t* __restrict__ run_e0, const Real* __restrict__ vgrid, int nlines, int n,
     const typename Cplx<Real>::T* __restrict__ tw, typename Cplx<Real>::T* __restrict__ specT, int ld, int lpc,
     int64_t xstride, int64_t sstride) {
+    pdl_enter();
     using C = typename Cplx<Real>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* sm = reinterpret_cast<C*>(smem_raw);
@@ -308,6 +313,7 @@ template <class Real, int N, int E, int MAXT = (N / E > 256 ? N / E : 256), int 
 __global__ void __launch_bounds__(MAXT, MINB) col_conv_t_kernel(typename Cplx<Real>::T* __restrict__ specT, int ld, int n,
                                                        int ncols, int H, const typename Cplx<Real>::T* __restrict__ tw,
                                                        const Real* __restrict__ lamT, int64_t sstride, int pm) {
+    pdl_enter();
     using C = typename Cplx<Real>::T;
     specT += blockIdx.y * sstride;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -356,6 +362,7 @@ __global__ void __launch_bounds__(MAXT, MINB) row_inv_t_kernel(const typename Cp
                                                       int nlines, int n, const typename Cplx<Real>::T* __restrict__ tw,
                                                       Real* __restrict__ wgrid, int lpc, int64_t sstride,
                                                       int64_t wstride) {
+    pdl_enter();
     using C = typename Cplx<Real>::T;
     specT += blockIdx.y * sstride;
     wgrid += blockIdx.y * wstride;

@@ -14,6 +14,23 @@ using C = Cplx<Real>::T;
 // elements per thread (largest radix) of the row and column transforms
 constexpr int ct_elems_row(int N) { return N >= 4096 ? 16 : 8; }
 constexpr int ct_elems_col(int N) { return N >= 4096 ? 16 : 8; }
+// column transform: 8, 16 or 32 elements per thread (32 only in FP32 and for
+// lines of at least 1024: one warp or more per column); tuned > 0 selects one,
+// 0 the default (32 for FP32 lines >= 2048, else the table above)
+// launch bounds of the column kernel: at most max(N/E, 256) threads; with 32
+// elements per thread the registers are capped for two CTAs per SM
+constexpr int col_maxt(int N, int E) { return N / E > 256 ? N / E : 256; }
+constexpr int col_minb(int E) { return E == 32 ? 2 : 1; }
+template <int N, int E>
+constexpr auto col_kernel() { return col_conv_t_kernel<Real, N, E, col_maxt(N, E), col_minb(E)>; }
+
+int col_elems(int N, int tuned) {
+    const bool fp32 = sizeof(Real) == 4;
+    auto ok = [&](int e) { return e == 8 || (e == 16 && N >= 512) || (e == 32 && fp32 && N >= 1024); };
+    if (tuned > 0 && ok(tuned)) return tuned;
+    if (fp32 && N >= 2048) return 32;
+    return ct_elems_col(N);
+}
 int lines_per_cta(int nthr, int tuned) {
     if (tuned > 0 && (tuned & (tuned - 1)) == 0 && tuned * nthr <= 512 && tuned <= 4) return tuned;
     return std::max(1, std::min(4, 512 / nthr));
@@ -28,19 +45,23 @@ size_t col_smem(int N, int G) { return sizeof(C) * (size_t)spad_len(N) * G; }
 
 template <int N>
 void set_attrs(int limit) {
-    constexpr int ER = ct_elems_row(N / 2), EC = ct_elems_col(N);
+    constexpr int ER = ct_elems_row(N / 2);
     GOFD_CUDA_TRY(cudaFuncSetAttribute(row_fwd_t_kernel<Real, 3, N / 2, ER>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
     GOFD_CUDA_TRY(cudaFuncSetAttribute(row_inv_t_kernel<Real, N / 2, ER>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
-    GOFD_CUDA_TRY(cudaFuncSetAttribute(col_conv_t_kernel<Real, N, EC>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    GOFD_CUDA_TRY(cudaFuncSetAttribute(col_kernel<N, 8>(), cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    if constexpr (N >= 512)
+        GOFD_CUDA_TRY(cudaFuncSetAttribute(col_kernel<N, 16>(), cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    if constexpr (N >= 1024 && sizeof(Real) == 4)
+        GOFD_CUDA_TRY(cudaFuncSetAttribute(col_kernel<N, 32>(), cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
 }
 
 // P = circulant length (column lines), rows use P/2; nb right-hand sides with
 // strides xs (input), ws (output grid) and the batch spectrum buffer
-template <int P>
-void run(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, int nb, int64_t xs, int64_t ws, C* S,
-         cudaStream_t st) {
+template <int P, int EC>
+void run_e(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, int nb, int64_t xs, int64_t ws, C* S,
+           cudaStream_t st) {
     constexpr int NR = P / 2, NC = P;
-    constexpr int ER = ct_elems_row(NR), EC = ct_elems_col(NC);
+    constexpr int ER = ct_elems_row(NR);
     constexpr int tr = NR / ER, tc = NC / EC;
     const int lpc = lines_per_cta(tr, p->tune_lpc), G = cols_per_cta(tc, p->tune_cols);
     const int n = p->n[0], H = P / 2 + 1, nlines = (int)p->nlines;
@@ -49,19 +70,28 @@ void run(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, int nb,
     const Real* w = reinterpret_cast<const Real*>(sizeof(Real) == 4 ? p->ell_w32.ptr : p->ell_w64.ptr);
     const int64_t ss = (int64_t)H * p->ldT;
     const unsigned rblocks = (unsigned)((nlines + lpc - 1) / lpc);
-    row_fwd_t_kernel<Real, 3, NR, ER><<<dim3(rblocks, nb), lpc * tr, row_smem(NR, lpc), st>>>(
-        x, p->ell_iidx.as<int32_t>(), w, p->nloc, p->line_run_ptr.as<int32_t>(), p->run_k0.as<int32_t>(),
-        p->run_len.as<int32_t>(), p->run_e0.as<int32_t>(), vgrid, nlines, n, tw, S, p->ldT, lpc, xs, nb > 1 ? ss : 0);
-    GOFD_CHECK_LAUNCH();
+    const int64_t sb = nb > 1 ? ss : 0;
+    launch_pdl(row_fwd_t_kernel<Real, 3, NR, ER>, dim3(rblocks, nb), dim3(lpc * tr), row_smem(NR, lpc), st, x,
+               p->ell_iidx.as<int32_t>(), w, p->nloc, p->line_run_ptr.as<int32_t>(), p->run_k0.as<int32_t>(),
+               p->run_len.as<int32_t>(), p->run_e0.as<int32_t>(), vgrid, nlines, n, tw, S, p->ldT, lpc, xs, sb);
     mark_stage(st, "gather_row_fft");
-    col_conv_t_kernel<Real, NC, EC><<<dim3((unsigned)((H + G - 1) / G), nb), G * tc, col_smem(NC, G), st>>>(
-        S, p->ldT, n, H, H, tw, lamT, nb > 1 ? ss : 0, 0);
-    GOFD_CHECK_LAUNCH();
+    launch_pdl(col_kernel<NC, EC>(), dim3((unsigned)((H + G - 1) / G), nb), dim3(G * tc), col_smem(NC, G), st, S,
+               p->ldT, n, H, H, tw, lamT, sb, 0);
     mark_stage(st, "col_fft_conv");
-    row_inv_t_kernel<Real, NR, ER><<<dim3(rblocks, nb), lpc * tr, row_smem(NR, lpc), st>>>(
-        S, p->ldT, nlines, n, tw, wgrid, lpc, nb > 1 ? ss : 0, ws);
-    GOFD_CHECK_LAUNCH();
+    launch_pdl(row_inv_t_kernel<Real, NR, ER>, dim3(rblocks, nb), dim3(lpc * tr), row_smem(NR, lpc), st, S, p->ldT,
+               nlines, n, tw, wgrid, lpc, sb, ws);
     mark_stage(st, "row_ifft");
+}
+
+template <int P>
+void run(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, int nb, int64_t xs, int64_t ws, C* S,
+         cudaStream_t st) {
+    const int e = col_elems(P, p->tune_cole);
+    if constexpr (P >= 1024 && sizeof(Real) == 4)
+        if (e == 32) return run_e<P, 32>(p, x, vgrid, wgrid, nb, xs, ws, S, st);
+    if constexpr (P >= 512)
+        if (e == 16) return run_e<P, 16>(p, x, vgrid, wgrid, nb, xs, ws, S, st);
+    run_e<P, 8>(p, x, vgrid, wgrid, nb, xs, ws, S, st);
 }
 
 }  // namespace
@@ -90,11 +120,14 @@ void AFD2D_ATTR_FN(int limit, int P, size_t* need) {
 #undef ATTR
         default: fail(GOFD_E_GRID, "unsupported circulant length");
     }
-    const int tr = P / 2 / ct_elems_row(P / 2), tc = P / ct_elems_col(P);
+    const int tr = P / 2 / ct_elems_row(P / 2);
     size_t nd = 0;
     for (int k = 1; k <= 4; ++k) {   // every shape the autotuner may pick
         if (k * tr <= 512) nd = std::max(nd, row_smem(P / 2, k));
-        if (k * tc <= std::max(tc, 256)) nd = std::max(nd, col_smem(P, k));
+        for (int e : {8, 16, 32}) {
+            const int tc = P / e;
+            if (tc >= 1 && k * tc <= std::max(tc, 256)) nd = std::max(nd, col_smem(P, k));
+        }
     }
     *need = nd;
 }

@@ -25,6 +25,7 @@ template <class Real, int N, int E>
 __global__ void __launch_bounds__(N / E > 256 ? N / E : 256) plane_fwd_t_kernel(
     const typename Cplx<Real>::T* __restrict__ specT, int64_t ld, typename Cplx<Real>::T* __restrict__ M, int n,
     int ngroups, const typename Cplx<Real>::T* __restrict__ tw) {
+    pdl_enter();
     using C = typename Cplx<Real>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* sm = reinterpret_cast<C*>(smem_raw);
@@ -54,6 +55,7 @@ template <class Real, int N, int E>
 __global__ void __launch_bounds__(N / E > 256 ? N / E : 256) plane_inv_t_kernel(
     const typename Cplx<Real>::T* __restrict__ M, int n, int ngroups, typename Cplx<Real>::T* __restrict__ specT,
     int64_t ld, const typename Cplx<Real>::T* __restrict__ tw) {
+    pdl_enter();
     using C = typename Cplx<Real>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* sm = reinterpret_cast<C*>(smem_raw);

@@ -13,6 +13,9 @@ using Real = REAL;
 using C = Cplx<Real>::T;
 
 constexpr int ct3_elems(int N) { return N >= 4096 ? 16 : 8; }
+// elements per thread of the axis-2 column transform: 8 or 16 (tuned > 0
+// selects, 0 the default 8)
+int col3_elems(int N, int tuned) { return (tuned == 16 && N >= 512) ? 16 : 8; }
 int rows_per_cta(int nthr) { return std::max(1, std::min(4, 512 / nthr)); }
 int groups_per_cta(int nthr) { return std::max(1, std::min(4, 256 / nthr)); }
 size_t row_smem3(int N, int lpc) {
@@ -28,13 +31,15 @@ void set_attrs3(int limit) {
     GOFD_CUDA_TRY(cudaFuncSetAttribute(plane_fwd_t_kernel<Real, NC, EC>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
     GOFD_CUDA_TRY(cudaFuncSetAttribute(plane_inv_t_kernel<Real, NC, EC>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
     GOFD_CUDA_TRY(cudaFuncSetAttribute(col_conv_t_kernel<Real, NC, EC>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    if constexpr (NC >= 512)
+        GOFD_CUDA_TRY(cudaFuncSetAttribute(col_conv_t_kernel<Real, NC, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
 }
 
-template <int P>
-void run3(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, cudaStream_t st) {
+template <int P, int ECC>
+void run3_e(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, cudaStream_t st) {
     constexpr int NR = P / 2, NC = P, ER = ct3_elems(NR), EC = ct3_elems(NC);
-    constexpr int tr = NR / ER, tc = NC / EC;
-    const int lpc = rows_per_cta(tr), G = groups_per_cta(tc);
+    constexpr int tr = NR / ER, tc = NC / EC, tcc = NC / ECC;
+    const int lpc = rows_per_cta(tr), G = groups_per_cta(tc), GC = groups_per_cta(tcc);
     const int n = p->n[0], H = P / 2 + 1, nlines = (int)p->nlines;
     const C* tw = reinterpret_cast<const C*>(sizeof(Real) == 4 ? p->tw32.ptr : p->tw64.ptr);
     const Real* lamT = reinterpret_cast<const Real*>(sizeof(Real) == 4 ? p->lamT32.ptr : p->lamT64.ptr);
@@ -43,26 +48,31 @@ void run3(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, cudaSt
     C* M = p->specM.as<C>();
     const int64_t ld = p->ldT;
     const unsigned rblocks = (unsigned)((nlines + lpc - 1) / lpc);
-    row_fwd_t_kernel<Real, 4, NR, ER><<<rblocks, lpc * tr, row_smem3(NR, lpc), st>>>(
-        x, p->ell_iidx.as<int32_t>(), w, p->nloc, p->line_run_ptr.as<int32_t>(), p->run_k0.as<int32_t>(),
-        p->run_len.as<int32_t>(), p->run_e0.as<int32_t>(), vgrid, nlines, n, tw, S, (int)ld, lpc, 0, 0);
-    GOFD_CHECK_LAUNCH();
+    launch_pdl(row_fwd_t_kernel<Real, 4, NR, ER>, dim3(rblocks), dim3(lpc * tr), row_smem3(NR, lpc), st, x,
+               p->ell_iidx.as<int32_t>(), w, p->nloc, p->line_run_ptr.as<int32_t>(), p->run_k0.as<int32_t>(),
+               p->run_len.as<int32_t>(), p->run_e0.as<int32_t>(), vgrid, nlines, n, tw, S, (int)ld, lpc,
+               (int64_t)0, (int64_t)0);
     mark_stage(st, "gather_row_fft");
     const int ngroups = (n + G - 1) / G;
-    plane_fwd_t_kernel<Real, NC, EC><<<(unsigned)(H * ngroups), G * tc, mid_smem3(NC, G), st>>>(S, ld, M, n, ngroups, tw);
-    GOFD_CHECK_LAUNCH();
+    launch_pdl(plane_fwd_t_kernel<Real, NC, EC>, dim3((unsigned)(H * ngroups)), dim3(G * tc), mid_smem3(NC, G), st,
+               (const C*)S, ld, M, n, ngroups, tw);
     mark_stage(st, "plane_fft_axis1");
-    col_conv_t_kernel<Real, NC, EC><<<(unsigned)(((int64_t)H * P + G - 1) / G), G * tc, mid_smem3(NC, G), st>>>(
-        M, n, n, (int)((int64_t)H * P), H, tw, lamT, 0, P);
-    GOFD_CHECK_LAUNCH();
+    launch_pdl(col_conv_t_kernel<Real, NC, ECC>, dim3((unsigned)(((int64_t)H * P + GC - 1) / GC)), dim3(GC * tcc),
+               mid_smem3(NC, GC), st, M, n, n, (int)((int64_t)H * P), H, tw, lamT, (int64_t)0, P);
     mark_stage(st, "conv_axis2");
-    plane_inv_t_kernel<Real, NC, EC><<<(unsigned)(H * ngroups), G * tc, mid_smem3(NC, G), st>>>(M, n, ngroups, S, ld, tw);
-    GOFD_CHECK_LAUNCH();
+    launch_pdl(plane_inv_t_kernel<Real, NC, EC>, dim3((unsigned)(H * ngroups)), dim3(G * tc), mid_smem3(NC, G), st,
+               (const C*)M, n, ngroups, S, ld, tw);
     mark_stage(st, "plane_ifft_axis1");
-    row_inv_t_kernel<Real, NR, ER><<<rblocks, lpc * tr, row_smem3(NR, lpc), st>>>(S, (int)ld, nlines, n, tw, wgrid,
-                                                                                lpc, 0, 0);
-    GOFD_CHECK_LAUNCH();
+    launch_pdl(row_inv_t_kernel<Real, NR, ER>, dim3(rblocks), dim3(lpc * tr), row_smem3(NR, lpc), st, (const C*)S,
+               (int)ld, nlines, n, tw, wgrid, lpc, (int64_t)0, (int64_t)0);
     mark_stage(st, "row_ifft");
+}
+
+template <int P>
+void run3(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, cudaStream_t st) {
+    if constexpr (P >= 512)
+        if (col3_elems(P, p->tune_cole) == 16) return run3_e<P, 16>(p, x, vgrid, wgrid, st);
+    run3_e<P, ct3_elems(P)>(p, x, vgrid, wgrid, st);
 }
 
 }  // namespace

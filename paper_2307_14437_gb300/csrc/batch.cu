@@ -34,6 +34,19 @@ struct BatchWork {
     DevBuf grid, spec, partial, counters;
     DevBuf red, cnt, scal, colv;
     std::vector<BScal> host;
+    // own stream (joined to the caller's by events) so that `check` block-PCG
+    // iterations are captured once as a CUDA graph per precision and batch size
+    cudaStream_t gs = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    int graph_nb[2] = {0, 0};
+    ~BatchWork() {
+        for (auto& g : graph)
+            if (g) cudaGraphExecDestroy(g);
+        if (ev_in) cudaEventDestroy(ev_in);
+        if (ev_out) cudaEventDestroy(ev_out);
+        if (gs) cudaStreamDestroy(gs);
+    }
 };
 
 // ---------------------------------------------------------------------------
@@ -228,6 +241,9 @@ static BatchWork* ensure_batch(gofd_problem* p, int nb) {
     GOFD_CUDA_TRY(cudaMemset(w->cnt.ptr, 0, sizeof(unsigned) * nb));
     w->scal.alloc(sizeof(BScal) * nb);
     w->colv.alloc(8 * 3 * nb);
+    GOFD_CUDA_TRY(cudaStreamCreateWithFlags(&w->gs, cudaStreamNonBlocking));
+    GOFD_CUDA_TRY(cudaEventCreateWithFlags(&w->ev_in, cudaEventDisableTiming));
+    GOFD_CUDA_TRY(cudaEventCreateWithFlags(&w->ev_out, cudaEventDisableTiming));
     w->host.resize(nb);
     return w;
 }
@@ -281,7 +297,7 @@ static int bpcg(gofd_problem* p, BatchWork* w, int nb, V* D, V* R, V* Pd, V* Q, 
         GOFD_CHECK_LAUNCH();
     }
     int it = 0;
-    while (it < maxit) {
+    auto iteration = [&]() {
         apply_interior_batch(p, f64, Pd, Q, nb, ld, w->grid.ptr, w->spec.ptr, w->partial.ptr, w->counters.ptr, st);
         bdot_kernel<V><<<rg, BRED_THREADS, 0, st>>>(Pd, Q, n, ld, red, cnt, s, 2);
         bupdate_kernel<V><<<rg, BRED_THREADS, 0, st>>>(D, R, Pd, Q, n, ld, red, cnt, s, pc ? 1 : 0);
@@ -291,7 +307,39 @@ static int bpcg(gofd_problem* p, BatchWork* w, int nb, V* D, V* R, V* Pd, V* Q, 
         }
         bupdate_p_kernel<V><<<vg, 256, 0, st>>>(Pd, ZZ, n, ld, s);
         GOFD_CHECK_LAUNCH();
-        ++it;
+    };
+    const int gi = f64 ? 1 : 0;
+    if (w->graph[gi] && w->graph_nb[gi] != nb) {
+        cudaGraphExecDestroy(w->graph[gi]);
+        w->graph[gi] = nullptr;
+    }
+    if (!w->graph[gi] && st == w->gs && maxit >= check) {
+        cudaGraph_t g = nullptr;
+        GOFD_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        try {
+            for (int k = 0; k < check; ++k) iteration();
+        } catch (...) {
+            cudaStreamEndCapture(st, &g);
+            if (g) cudaGraphDestroy(g);
+            throw;
+        }
+        GOFD_CUDA_TRY(cudaStreamEndCapture(st, &g));
+        const cudaError_t e = cudaGraphInstantiate(&w->graph[gi], g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            w->graph[gi] = nullptr;
+            fail(GOFD_E_CUDA, std::string("graph instantiation: ") + cudaGetErrorString(e));
+        }
+        w->graph_nb[gi] = nb;
+    }
+    while (it < maxit) {
+        if (w->graph[gi] && st == w->gs && it % check == 0 && it + check <= maxit) {
+            GOFD_CUDA_TRY(cudaGraphLaunch(w->graph[gi], st));
+            it += check;
+        } else {
+            iteration();
+            ++it;
+        }
         if (it % check == 0 || it == maxit) {
             read_bscal(w, nb, st);
             bool all = true;
@@ -303,9 +351,20 @@ static int bpcg(gofd_problem* p, BatchWork* w, int nb, V* D, V* R, V* Pd, V* Q, 
 }
 
 void solve_batch(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs, int nb, const double* F, int64_t ldf,
-                 double tol, int maxit, double* U, gofd_solve_info* infos, cudaStream_t st) {
+                 double tol, int maxit, double* U, gofd_solve_info* infos, cudaStream_t caller) {
     auto t0 = std::chrono::steady_clock::now();
     BatchWork* w = ensure_batch(p, nb);
+    const cudaStream_t st = w->gs;
+    GOFD_CUDA_TRY(cudaEventRecord(w->ev_in, caller));
+    GOFD_CUDA_TRY(cudaStreamWaitEvent(st, w->ev_in, 0));
+    struct Join {
+        BatchWork* w;
+        cudaStream_t caller;
+        ~Join() {
+            cudaEventRecord(w->ev_out, w->gs);
+            cudaStreamWaitEvent(caller, w->ev_out, 0);
+        }
+    } join{w, caller};
     const int64_t n = p->nint, ld = w->ld;
     double* B = w->b64.as<double>();
     double* X = w->x64.as<double>();
@@ -405,37 +464,55 @@ void apply_batch(gofd_problem* p, bool fp64, const void* x, void* y, int nb, int
 // ---------------------------------------------------------------------------
 double autotune(gofd_problem* p, int nb, cudaStream_t st) {
     BatchWork* w = ensure_batch(p, nb);
+    invalidate_graphs(p);
+    for (auto& g : w->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
     const int64_t ld = w->ld;
     GOFD_CUDA_TRY(cudaMemsetAsync(w->p32.ptr, 0, 4 * ld * nb, st));
     cudaEvent_t a, b;
     GOFD_CUDA_TRY(cudaEventCreate(&a));
     GOFD_CUDA_TRY(cudaEventCreate(&b));
-    std::vector<int> shapes = p->d == 2 ? std::vector<int>{1, 2, 4} : std::vector<int>{0};
-    double best = 1e30;
-    int bl = 0, bc = 0, bt = 0;
-    for (int lpc : shapes)
-        for (int cols : shapes)
-            for (int tpr : {4, 8, 16, 32}) {
-                p->tune_lpc = lpc;
-                p->tune_cols = cols;
-                p->tune_tpr = tpr;
-                apply_interior_batch(p, false, w->p32.ptr, w->q32.ptr, nb, ld, w->grid.ptr, w->spec.ptr,
-                                     w->partial.ptr, w->counters.ptr, st);   // warm
-                GOFD_CUDA_TRY(cudaEventRecord(a, st));
-                for (int r = 0; r < 5; ++r)
-                    apply_interior_batch(p, false, w->p32.ptr, w->q32.ptr, nb, ld, w->grid.ptr, w->spec.ptr,
-                                         w->partial.ptr, w->counters.ptr, st);
-                GOFD_CUDA_TRY(cudaEventRecord(b, st));
-                GOFD_CUDA_TRY(cudaEventSynchronize(b));
-                float ms = 0;
-                GOFD_CUDA_TRY(cudaEventElapsedTime(&ms, a, b));
-                if (ms / 5 < best) {
-                    best = ms / 5;
-                    bl = lpc;
-                    bc = cols;
-                    bt = tpr;
-                }
+    // coordinate descent over the four choices (each swept with the others
+    // at their current best): column elements per thread, lines per CTA of
+    // the row transforms, columns per CTA, scatter lanes per row
+    auto time_current = [&]() {
+        apply_interior_batch(p, false, w->p32.ptr, w->q32.ptr, nb, ld, w->grid.ptr, w->spec.ptr, w->partial.ptr,
+                             w->counters.ptr, st);   // warm
+        GOFD_CUDA_TRY(cudaEventRecord(a, st));
+        for (int r = 0; r < 5; ++r)
+            apply_interior_batch(p, false, w->p32.ptr, w->q32.ptr, nb, ld, w->grid.ptr, w->spec.ptr,
+                                 w->partial.ptr, w->counters.ptr, st);
+        GOFD_CUDA_TRY(cudaEventRecord(b, st));
+        GOFD_CUDA_TRY(cudaEventSynchronize(b));
+        float ms = 0;
+        GOFD_CUDA_TRY(cudaEventElapsedTime(&ms, a, b));
+        return ms / 5.0;
+    };
+    const std::vector<int> shapes = p->d == 2 ? std::vector<int>{1, 2, 4} : std::vector<int>{0};
+    const std::vector<int> elems = p->d == 1 ? std::vector<int>{0} : std::vector<int>{8, 16, 32};
+    const std::vector<int> lanes = {4, 8, 16, 32};
+    p->tune_cole = p->tune_lpc = p->tune_cols = p->tune_tpr = 0;
+    double best = time_current();
+    int be = 0, bl = 0, bc = 0, bt = 0;
+    auto sweep = [&](int* field, const std::vector<int>& vals, int* keep) {
+        for (int v : vals) {
+            *field = v;
+            const double t = time_current();
+            if (t < best) {
+                best = t;
+                *keep = v;
             }
+        }
+        *field = *keep;
+    };
+    sweep(&p->tune_cole, elems, &be);
+    sweep(&p->tune_lpc, shapes, &bl);
+    sweep(&p->tune_cols, shapes, &bc);
+    sweep(&p->tune_tpr, lanes, &bt);
+    p->tune_cole = be;
     p->tune_lpc = bl;
     p->tune_cols = bc;
     p->tune_tpr = bt;

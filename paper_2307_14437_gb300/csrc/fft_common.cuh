@@ -80,17 +80,39 @@ template <bool INV, class C> __device__ __forceinline__ C twc16(C a, int j) {
     return cmul(a, cmk<C>(c, s));
 }
 
+// cos of 2 pi k / 32 for odd k (even k: cos16(k/2))
+__host__ __device__ constexpr double cos32_odd(int k) {
+    switch (k & 31) {
+        case 1: case 31: return 0.98078528040323044913;
+        case 3: case 29: return 0.83146961230254523708;
+        case 5: case 27: return 0.55557023301960222474;
+        case 7: case 25: return 0.19509032201612826785;
+        case 9: case 23: return -0.19509032201612826785;
+        case 11: case 21: return -0.55557023301960222474;
+        case 13: case 19: return -0.83146961230254523708;
+        default: return -0.98078528040323044913;   // 15, 17
+    }
+}
+
+// multiply by exp(-+ 2 pi i j / 32); even j take the 16-point path unchanged
+template <bool INV, class C> __device__ __forceinline__ C twc32(C a, int j) {
+    j &= 31;
+    if ((j & 1) == 0) return twc16<INV>(a, j >> 1);
+    const double c = cos32_odd(j), sn = cos32_odd(j - 8);   // sin(2 pi j/32) = cos(2 pi (j-8)/32)
+    return cmul(a, cmk<C>(c, INV ? sn : -sn));
+}
+
 __host__ __device__ constexpr int bitrev(int x, int bits) {
     int r = 0;
     for (int i = 0; i < bits; ++i) r |= ((x >> i) & 1) << (bits - 1 - i);
     return r;
 }
 
-// In-register DFT of length R (power of two <= 16), natural order in and out:
+// In-register DFT of length R (power of two <= 32), natural order in and out:
 // v[k] <- sum_r v[r] exp(-+2 pi i r k / R).  Radix-2 decimation in frequency,
 // then a compile-time bit-reversal permutation.
 template <int R, bool INV, class C> __device__ __forceinline__ void dft_reg(C* v) {
-    constexpr int LOG = (R == 2) ? 1 : (R == 4) ? 2 : (R == 8) ? 3 : 4;
+    constexpr int LOG = (R == 2) ? 1 : (R == 4) ? 2 : (R == 8) ? 3 : (R == 16) ? 4 : 5;
 #pragma unroll
     for (int st = 0; st < LOG; ++st) {
         const int span = R >> (st + 1);
@@ -100,8 +122,8 @@ template <int R, bool INV, class C> __device__ __forceinline__ void dft_reg(C* v
             for (int j = 0; j < span; ++j) {
                 C a = v[blk + j], b = v[blk + j + span];
                 v[blk + j] = cadd(a, b);
-                // twiddle exp(-2 pi i j / (2 span)) = index j * 16 / (2 span) of the 16-table
-                v[blk + j + span] = twc16<INV>(csub(a, b), j * (16 / (2 * span)));
+                // twiddle exp(-2 pi i j / (2 span)) = index j * 32 / (2 span) of the 32-table
+                v[blk + j + span] = twc32<INV>(csub(a, b), j * (32 / (2 * span)));
             }
         }
     }

@@ -32,6 +32,41 @@ struct Error {
 [[noreturn]] inline void fail(gofd_status c, const std::string& m) { throw Error{c, m}; }
 
 // ---------------------------------------------------------------------------
+// programmatic dependent launch
+//
+// The kernels of the product are launched with programmatic stream
+// serialization: a kernel's CTAs may be scheduled while the previous kernel in
+// the stream is still running.  Each such kernel first lets its own successor
+// be scheduled (launch_dependents) and then waits until its predecessor has
+// completed and its memory is visible (griddepcontrol.wait, a no-op for an
+// ordinary launch); it touches no memory before that wait.  Every CTA waits,
+// so a kernel completes only after its predecessor has, and the ordering is
+// transitive.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_enter() {
+#if defined(__CUDA_ARCH__)
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+#endif
+}
+
+template <class... KArgs, class... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    GOFD_CUDA_TRY(cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...));
+}
+
+// ---------------------------------------------------------------------------
 // device buffers owned by the handle
 // ---------------------------------------------------------------------------
 struct DevBuf {
@@ -147,6 +182,7 @@ struct gofd_problem {
     int ldT = 0;               // leading dimension of specT (n^(d-1) rounded up to 16)
     gofd::DevBuf specM;        // 3D: middle-stage buffer, (P/2+1) x P x n complex
     int tune_lpc = 0, tune_cols = 0, tune_tpr = 0;  // launch shapes picked by the autotuner (0 = default)
+    int tune_cole = 0;         // elements per thread of the column transforms (0 = default)
     gofd::DevBuf lamT64, lamT32;  // 2D/3D: scaled symbol with the axis order reversed
     gofd::DevBuf gridw;        // real [ngrid] (largest precision): A_FD v on the grid
     gofd::DevBuf xin;          // real [nint+1] compacted input (largest precision)
@@ -196,6 +232,7 @@ void expand_interior(gofd_problem* p, bool fp64, const void* y, void* u, double 
 void solve(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs, const double* f, double tol,
            int maxit, bool init_zero, double* u, gofd_solve_info* info, cudaStream_t st);
 void free_workspace(gofd_problem* p);
+void invalidate_graphs(gofd_problem* p);   // drop captured solver iterations
 void solve_core(gofd_problem* p, gofd_solve_mode mode, const double* b, double tol, int maxit, bool init_zero,
                 double* x, gofd_solve_info* info, cudaStream_t st);
 void assemble_rhs(gofd_problem* p, gofd_rhs rhs, const double* f, double* b, cudaStream_t st);

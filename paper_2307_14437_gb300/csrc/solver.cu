@@ -37,10 +37,32 @@ struct Workspace {
     DevBuf d32, r32, p32, q32, z32;
     DevBuf partial, counter, scal;
     Scal* host = nullptr;   // pinned
+    // the solver runs on its own stream, ordered after / before the caller's
+    // stream by events, so that `check` PCG iterations can be captured once as
+    // a CUDA graph and replayed (one graph per precision)
+    cudaStream_t gs = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
     ~Workspace() {
+        for (auto& g : graph)
+            if (g) cudaGraphExecDestroy(g);
+        if (ev_in) cudaEventDestroy(ev_in);
+        if (ev_out) cudaEventDestroy(ev_out);
+        if (gs) cudaStreamDestroy(gs);
         if (host) cudaFreeHost(host);
     }
 };
+
+// The captured iterations depend on the launch shapes; a new choice of shapes
+// (the autotuner) drops them.
+void invalidate_graphs(gofd_problem* p) {
+    if (!p->ws) return;
+    for (auto& g : p->ws->graph)
+        if (g) {
+            cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+}
 
 // ---------------------------------------------------------------------------
 // fixed-order block reduction helpers
@@ -224,6 +246,9 @@ static Workspace* ensure_ws(gofd_problem* p) {
     GOFD_CUDA_TRY(cudaMemset(w->p64.ptr, 0, 8 * n1));
     GOFD_CUDA_TRY(cudaMemset(w->p32.ptr, 0, 4 * n1));
     GOFD_CUDA_TRY(cudaMallocHost((void**)&w->host, sizeof(Scal)));
+    GOFD_CUDA_TRY(cudaStreamCreateWithFlags(&w->gs, cudaStreamNonBlocking));
+    GOFD_CUDA_TRY(cudaEventCreateWithFlags(&w->ev_in, cudaEventDisableTiming));
+    GOFD_CUDA_TRY(cudaEventCreateWithFlags(&w->ev_out, cudaEventDisableTiming));
     p->ws = w;
     return w;
 }
@@ -279,7 +304,7 @@ static int pcg(gofd_problem* p, Workspace* w, V* d, V* r, V* pv, V* q, V* z, dou
     }
     int it = 0;
     double rel = 1.0;
-    while (it < maxit) {
+    auto iteration = [&]() {
         apply_interior(p, fp64, pv, q, st);
         dot_pq_kernel<V><<<RED_BLOCKS, RED_THREADS, 0, st>>>(pv, q, n, part, cnt, s);
         update_xr_kernel<V><<<RED_BLOCKS, RED_THREADS, 0, st>>>(d, r, pv, q, n, part, cnt, s, pc ? 1 : 0);
@@ -289,7 +314,36 @@ static int pcg(gofd_problem* p, Workspace* w, V* d, V* r, V* pv, V* q, V* z, dou
         }
         update_p_kernel<V><<<nb, 256, 0, st>>>(pv, zz, n, s);
         GOFD_CHECK_LAUNCH();
-        ++it;
+    };
+    // `check` iterations as one CUDA graph (the vectors of a precision are
+    // always the workspace's, so the graph is built once per handle)
+    cudaGraphExec_t& graph = w->graph[fp64 ? 1 : 0];
+    if (!graph && st == w->gs && maxit >= check) {
+        cudaGraph_t g = nullptr;
+        GOFD_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        try {
+            for (int k = 0; k < check; ++k) iteration();
+        } catch (...) {
+            cudaStreamEndCapture(st, &g);
+            if (g) cudaGraphDestroy(g);
+            throw;
+        }
+        GOFD_CUDA_TRY(cudaStreamEndCapture(st, &g));
+        const cudaError_t e = cudaGraphInstantiate(&graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            graph = nullptr;
+            fail(GOFD_E_CUDA, std::string("graph instantiation: ") + cudaGetErrorString(e));
+        }
+    }
+    while (it < maxit) {
+        if (graph && st == w->gs && it % check == 0 && it + check <= maxit) {
+            GOFD_CUDA_TRY(cudaGraphLaunch(graph, st));
+            it += check;
+        } else {
+            iteration();
+            ++it;
+        }
         if (it % check == 0 || it == maxit) {
             read_scal(w, st);
             if (w->host->bad) break;
@@ -306,9 +360,22 @@ static int pcg(gofd_problem* p, Workspace* w, V* d, V* r, V* pv, V* q, V* z, dou
 // Solve S x = b on the interior unknowns (b, x: device, n_int (+1) FP64 each,
 // x[n_int] = 0 on exit).  x holds the initial guess unless init_zero.
 void solve_core(gofd_problem* p, gofd_solve_mode mode, const double* b, double tol, int maxit, bool init_zero,
-                double* x, gofd_solve_info* info, cudaStream_t st) {
+                double* x, gofd_solve_info* info, cudaStream_t caller) {
     auto t0 = std::chrono::steady_clock::now();
     Workspace* w = ensure_ws(p);
+    // run on the workspace's stream, after the caller's pending work; the
+    // caller's stream waits for the solve on every exit path
+    const cudaStream_t st = w->gs;
+    GOFD_CUDA_TRY(cudaEventRecord(w->ev_in, caller));
+    GOFD_CUDA_TRY(cudaStreamWaitEvent(st, w->ev_in, 0));
+    struct Join {
+        Workspace* w;
+        cudaStream_t caller;
+        ~Join() {
+            cudaEventRecord(w->ev_out, w->gs);
+            cudaStreamWaitEvent(caller, w->ev_out, 0);
+        }
+    } join{w, caller};
     const int64_t n = p->nint;
     const int nb = grid_blocks(n, 256);
     double* r = w->r64.as<double>();

@@ -58,6 +58,12 @@ WORKLOADS = {
     "batch48": "48 instances (16 ring disks + 16 L-shapes, 5e3-1.5e5 vertices log-uniform, alpha cycling "
                "0.5/1/1.5, grids 256^2-2048^2) x 8 right-hand sides (f=1 + 7 Gaussian bumps, width 0.1)",
 }
+# DRAM bytes per launch of each product kernel (dram__bytes_read.sum +
+# dram__bytes_write.sum) from one `ncu --set full` capture of the current
+# kernels; profiles/product_kernels_lshape1024_fp32.md gives the command.
+NCU_DRAM_BYTES = {
+    "lshape1024": {"gather_row_fft": 19201024, "col_fft_conv": 12678400, "row_ifft": 8425984, "scatter": 22080000},
+}
 BATCH_METRIC = "batched block-PCG: right-hand sides solved to rel-res 1e-8 per second (mixed), 1 GB300"
 BATCH_RHS = 8
 
@@ -260,7 +266,9 @@ def run_gofd(args):
     hbm = pk.get("hbm_gbs", 6800.0)
     achieved = kbytes[dom] / (stage_ms[dom] * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(achieved / hbm, 4), "traffic": None,
+                "frac": round(achieved / hbm, 4), "traffic": NCU_DRAM_BYTES.get(args.workload, {}).get(dom),
+                "traffic_source": "ncu --set full, one launch (profiles/)" if dom in NCU_DRAM_BYTES.get(
+                    args.workload, {}) else None,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if "hbm_gbs" in pk else "fallback 6.8 TB/s",
                 "stage_ms": {k: round(vv, 5) for k, vv in stage_ms.items()},
                 "stage_GBps": {k: round(kbytes[k] / (stage_ms[k] * 1e-3) / 1e9, 1) for k in stage_ms if k in kbytes},

@@ -262,10 +262,11 @@ __global__ void __launch_bounds__(256) scatter_kernel(const int32_t* __restrict_
                                                       int64_t nint, Real* __restrict__ y, Real scale, int64_t ws,
                                                       int64_t ys, unsigned nshort, LongRows lr, Real* partial,
                                                       unsigned* counters) {
-    pdl_enter();
+    pdl_trigger();
     w += blockIdx.y * ws;
     y += blockIdx.y * ys;
     if (blockIdx.x >= nshort) {
+        pdl_wait();
         __shared__ Real part[256];
         __shared__ bool last;
         const int64_t c = blockIdx.x - nshort;
@@ -289,33 +290,67 @@ __global__ void __launch_bounds__(256) scatter_kernel(const int32_t* __restrict_
         }
         return;
     }
-    // the loop is uniform across each warp so that every lane reaches the
-    // shuffles; four independent partial sums keep several loads in flight
+    // Short rows: TPR lanes per row; lane l accumulates the entries
+    // b + l + (4k + u) TPR of its row in partial sum u (u < 4), then the sums
+    // are combined as (s0 + s1) + (s2 + s3) and across the lanes by shuffles.
+    // The loop is uniform across each warp so that every lane reaches the
+    // shuffles.  The first row group's bounds and first entries are set-up
+    // data, loaded before waiting for the kernel that writes w.
     const int64_t nthreads = (int64_t)nshort * blockDim.x;
     const int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int lane = threadIdx.x % TPR;
-    for (int64_t t0 = gid - (threadIdx.x & 31); t0 < nint * TPR; t0 += nthreads) {
-        const int64_t i = (t0 + (threadIdx.x & 31)) / TPR;
-        Real acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
-        if (i < nint && ptr[i + 1] - ptr[i] <= SCATTER_LONG) {
-            const int b = ptr[i], e = ptr[i + 1];
-            int a = b + lane;
-            for (; a + 3 * TPR < e; a += 4 * TPR) {
-                const int c0 = __ldg(&col[a]), c1 = __ldg(&col[a + TPR]);
-                const int c2 = __ldg(&col[a + 2 * TPR]), c3 = __ldg(&col[a + 3 * TPR]);
-                const Real v0 = __ldg(&val[a]), v1 = __ldg(&val[a + TPR]);
-                const Real v2 = __ldg(&val[a + 2 * TPR]), v3 = __ldg(&val[a + 3 * TPR]);
-                acc0 += v0 * __ldg(&w[c0]);
-                acc1 += v1 * __ldg(&w[c1]);
-                acc2 += v2 * __ldg(&w[c2]);
-                acc3 += v3 * __ldg(&w[c3]);
-            }
-            for (; a < e; a += TPR) acc0 += __ldg(&val[a]) * __ldg(&w[__ldg(&col[a])]);
+    int64_t t0 = gid - (threadIdx.x & 31);
+    int b, e, c4[4];
+    bool mine;   // a row of at most SCATTER_LONG entries (written here)
+    Real v4[4];
+    auto bounds = [&](int64_t tt) {
+        const int64_t i = (tt + (threadIdx.x & 31)) / TPR;
+        b = e = 0;
+        mine = false;
+        if (i < nint) {
+            b = __ldg(&ptr[i]);
+            e = __ldg(&ptr[i + 1]);
+            mine = e - b <= SCATTER_LONG;
+            if (!mine) e = b;   // a long row: the chunk blocks take it
         }
-        Real acc = (acc0 + acc1) + (acc2 + acc3);
+    };
+    auto first4 = [&]() {
 #pragma unroll
-        for (int o = TPR / 2; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o, TPR);
-        if (lane == 0 && i < nint && ptr[i + 1] - ptr[i] <= SCATTER_LONG) y[i] = acc * scale;
+        for (int u = 0; u < 4; ++u) {
+            const int a = b + lane + u * TPR;
+            c4[u] = a < e ? __ldg(&col[a]) : -1;
+            v4[u] = a < e ? __ldg(&val[a]) : (Real)0;
+        }
+    };
+    bounds(t0);
+    first4();
+    pdl_wait();
+    for (; t0 < nint * TPR; t0 += nthreads) {
+        if (t0 != gid - (threadIdx.x & 31)) {
+            bounds(t0);
+            first4();
+        }
+        Real acc[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u] = c4[u] >= 0 ? v4[u] * __ldg(&w[c4[u]]) : (Real)0;
+        for (int a = b + lane + 4 * TPR; a < e; a += 4 * TPR) {
+            int cc[4];
+            Real vv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const bool ok = a + u * TPR < e;
+                cc[u] = ok ? __ldg(&col[a + u * TPR]) : -1;
+                vv[u] = ok ? __ldg(&val[a + u * TPR]) : (Real)0;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (cc[u] >= 0) acc[u] += vv[u] * __ldg(&w[cc[u]]);
+        }
+        Real sum = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+#pragma unroll
+        for (int o = TPR / 2; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o, TPR);
+        const int64_t i = (t0 + (threadIdx.x & 31)) / TPR;
+        if (lane == 0 && mine) y[i] = sum * scale;
     }
 }
 

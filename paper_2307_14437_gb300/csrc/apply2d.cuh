@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(MAXT, MINB) row_fwd_t_kernel(
     const int32_t* __restrict__ run_e0, const Real* __restrict__ vgrid, int nlines, int n,
     const typename Cplx<Real>::T* __restrict__ tw, typename Cplx<Real>::T* __restrict__ specT, int ld, int lpc,
     int64_t xstride, int64_t sstride) {
-    pdl_enter();
+    pdl_trigger();
     using C = typename Cplx<Real>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* sm = reinterpret_cast<C*>(smem_raw);
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(MAXT, MINB) row_fwd_t_kernel(
     Runs rs;
     rs.n = 0;
     rs.rb = 0;
-    if (active && !vgrid) {
+    if (active && !vgrid) {   // set-up tables: read before the predecessor completes
         rs.rb = __ldg(&run_ptr[line]);
         rs.n = __ldg(&run_ptr[line + 1]) - rs.rb;
         for (int r = 0; r < 2; ++r)
@@ -212,6 +212,7 @@ __global__ void __launch_bounds__(MAXT, MINB) row_fwd_t_kernel(
                 rs.e0[r] = __ldg(&run_e0[rs.rb + r]);
             }
     }
+    pdl_wait();
     // pass-0 inputs z[m] = (v[2m], v[2m+1]) gathered straight into registers
     C v[E];
     if (vgrid || rs.n > 2) {

@@ -481,15 +481,16 @@ double autotune(gofd_problem* p, int nb, cudaStream_t st) {
     auto time_current = [&]() {
         apply_interior_batch(p, false, w->p32.ptr, w->q32.ptr, nb, ld, w->grid.ptr, w->spec.ptr, w->partial.ptr,
                              w->counters.ptr, st);   // warm
+        constexpr int reps = 10;
         GOFD_CUDA_TRY(cudaEventRecord(a, st));
-        for (int r = 0; r < 5; ++r)
+        for (int r = 0; r < reps; ++r)
             apply_interior_batch(p, false, w->p32.ptr, w->q32.ptr, nb, ld, w->grid.ptr, w->spec.ptr,
                                  w->partial.ptr, w->counters.ptr, st);
         GOFD_CUDA_TRY(cudaEventRecord(b, st));
         GOFD_CUDA_TRY(cudaEventSynchronize(b));
         float ms = 0;
         GOFD_CUDA_TRY(cudaEventElapsedTime(&ms, a, b));
-        return ms / 5.0;
+        return ms / reps;
     };
     const std::vector<int> shapes = p->d == 2 ? std::vector<int>{1, 2, 4} : std::vector<int>{0};
     const std::vector<int> elems = p->d == 1 ? std::vector<int>{0} : std::vector<int>{8, 16, 32};

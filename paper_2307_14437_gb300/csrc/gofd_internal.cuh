@@ -39,15 +39,24 @@ struct Error {
 // the stream is still running.  Each such kernel first lets its own successor
 // be scheduled (launch_dependents) and then waits until its predecessor has
 // completed and its memory is visible (griddepcontrol.wait, a no-op for an
-// ordinary launch); it touches no memory before that wait.  Every CTA waits,
-// so a kernel completes only after its predecessor has, and the ordering is
-// transitive.
+// ordinary launch).  Before that wait a kernel only reads data that no kernel
+// of the product writes (set-up tables: runs, CSR structure and weights) and
+// writes nothing.  Every CTA waits, so a kernel completes only after its
+// predecessor has, and the ordering is transitive.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void pdl_enter() {
+__device__ __forceinline__ void pdl_trigger() {
 #if defined(__CUDA_ARCH__)
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
+}
+__device__ __forceinline__ void pdl_wait() {
+#if defined(__CUDA_ARCH__)
     asm volatile("griddepcontrol.wait;" ::: "memory");
 #endif
+}
+__device__ __forceinline__ void pdl_enter() {
+    pdl_trigger();
+    pdl_wait();
 }
 
 template <class... KArgs, class... Args>

@@ -9,8 +9,9 @@ flushed (256 MB write) before every timed step.  The headline value is the
 algorithmic bytes of one product divided by its time (GB/s).  Beside it:
 per-kernel times and the roofline of the dominant kernel, the same product
 end to end through the host-buffer C-ABI call, time to relative residual 1e-8
-for mixed-precision refinement vs plain FP64 PCG at alpha in {0.5, 1, 1.5},
-and the FP64 CPU oracle timed on the host cores.
+for mixed-precision refinement vs plain FP64 PCG at alpha in {0.5, 1, 1.5}
+and on the 2048^2 graded-disk configuration (alpha = 1.2, vertex data), and
+the FP64 CPU oracle timed on the host cores.
 
 Multi-GPU runs (torchrun) execute independent replicas (the product does not
 shard): no data-path collective; the aggregate value sums all ranks' bytes
@@ -257,9 +258,7 @@ def run_gofd(args):
         "col_fft_conv": 8 * n * H * 2 + 4 * H * H,
         "row_ifft": 8 * nl * H + 4 * n ** d,
         "scatter": inf["nnz_t"] * 8 + 4 * (nint + 1) + 4 * inf["nnz_t"] + 4 * nint,
-        "plane_fft_axis1": 8 * nl * H + 8 * n * P * H,
-        "conv_axis2": 2 * 8 * n * P * H + 4 * H ** 3,
-        "plane_ifft_axis1": 8 * n * P * H + 8 * nl * H,
+        "axis12_conv": 2 * 8 * nl * H + 4 * H ** 3,   # planes read and written, symbol; middle buffer in L2
         "symbol_mul": 2 * 8 * H + 4 * H,
     }
     pk = peaks()
@@ -330,6 +329,28 @@ def run_gofd(args):
                 "outer_iters": info["outer_iters"], "rel_res_fp64": info["rel_res_fp64"],
                 "levels": pi["precond_levels"], "factor_nnz": pi["precond_nnz"], "build_s": round(t_pc, 3)}
             pp.close()
+    if not args.no_pcg and args.workload in ("lshape1024", "graded2048"):
+        # the 2048^2 configuration: graded disk, alpha = 1.2, vertex data f_target (GoFD-3)
+        if args.workload == "graded2048":
+            pg, vg = prob, v
+        else:
+            vg_, sg_, ag_, hg_, log_, hig_ = workload("graded2048")
+            pg, vg = Problem(vg_, sg_, ag_, hg_, log_, hig_), vg_
+            pg.autotune(nb=1)
+        ft = torch.tensor(mg.target_bump(vg), device=dev)
+        row = {}
+        for mode in ("mixed", "fp64"):
+            pg.solve(ft, rhs="vertex", mode=mode, tol=1e-8)   # warm
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            _, info = pg.solve(ft, rhs="vertex", mode=mode, tol=1e-8)
+            torch.cuda.synchronize()
+            row[mode] = {"s": round(time.perf_counter() - t1, 5), "inner_iters": info["inner_iters"],
+                         "outer_iters": info["outer_iters"], "rel_res_fp64": info["rel_res_fp64"]}
+        row["speedup_mixed_vs_fp64"] = round(row["fp64"]["s"] / row["mixed"]["s"], 3)
+        pcg["graded disk 2048^2 alpha=1.2, f_target vertex data"] = row
+        if pg is not prob:
+            pg.close()
     clk = clocks.stop()
 
     if rank == 0:

@@ -84,10 +84,13 @@ typedef struct {
     int64_t filon_M;           /* finest Filon panel count M; 0 = paper default (2^14 in 1D/2D, 2^11 in 3D), raised
                                   so that the coarsest Richardson level keeps M/2^(levels-1) >= n                      */
     int richardson_levels;     /* Filon levels M, M/2, ...; 0 = 4                                                     */
-    uint64_t wait_budget_cycles; /* bound on every device-side spin wait (clock64 cycles); 0 = 2e9                    */
+    uint64_t wait_budget_cycles; /* bound on device-side spin waits (clock64 cycles); 0 = 2e9.  No kernel of this
+                                    build spins on a flag; the field is kept for ABI stability                    */
     double inner_tol;          /* mixed mode: relative reduction of each inner FP32 PCG; 0 = 1e-4                   */
-    int check_every;           /* iterations between host convergence checks; 0 = 8                                  */
+    int check_every;           /* iterations between convergence checks (on the device); 0 = 8                      */
     int ordering;              /* IC unknown order: 0 natural vertex order, 1 multicolour (shorter dependency chains)  */
+    int chunk_planes;          /* 3D: spectrum planes k_x0 per chunk of the axis-1/axis-2 stage; 0 = as many as fit a
+                                  1 GiB middle buffer.  Bounds memory; results do not depend on it                    */
 } gofd_options;
 
 typedef struct {
@@ -101,6 +104,7 @@ typedef struct {
     int h_within_practical_bound; /* h <= a_h  (Remark 3.5)                                              */
     double t_setup_ms;         /* gofd_build wall time                                                   */
     double t_solve_ms;         /* this solve's wall time                                                 */
+    int device_loop;           /* 1: the PCG iterations ran as a device-side CUDA graph loop, 0: host loop */
 } gofd_solve_info;
 
 typedef struct {
@@ -216,8 +220,13 @@ gofd_status gofd_apply_interior_profiled(gofd_problem* p, gofd_precision prec, c
  *   u_dev   device, N_v doubles: initial guess on entry (ignored if init_zero),
  *           the solution on exit with boundary entries 0
  *   info    optional (may be NULL)
- * The stream is synchronised at every convergence check.  Returns
- * GOFD_E_NOT_CONVERGED (with u holding the last iterate) if maxit is reached.
+ * The solve runs on a stream of the handle, after the caller's pending work
+ * on `stream`, and the caller's stream waits for it; the call returns when
+ * the solve is done.  Each inner PCG runs as one CUDA graph launch: a
+ * device-side loop whose control kernel tests the residual every
+ * check_every iterations (info->device_loop says whether it was used).
+ * Returns GOFD_E_NOT_CONVERGED (with u holding the last iterate) if maxit is
+ * reached.
  */
 gofd_status gofd_solve(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs,
                        const double* f_dev, double tol, int maxit, int init_zero,

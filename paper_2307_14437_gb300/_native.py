@@ -25,14 +25,15 @@ RHS_GRID, RHS_VERTEX = 0, 1
 class Options(C.Structure):
     _fields_ = [("precond", C.c_int), ("ic_level", C.c_int), ("filon_M", C.c_int64),
                 ("richardson_levels", C.c_int), ("wait_budget_cycles", C.c_uint64),
-                ("inner_tol", C.c_double), ("check_every", C.c_int), ("ordering", C.c_int)]
+                ("inner_tol", C.c_double), ("check_every", C.c_int), ("ordering", C.c_int),
+                ("chunk_planes", C.c_int)]
 
 
 class SolveInfo(C.Structure):
     _fields_ = [("outer_iters", C.c_int), ("inner_iters", C.c_int), ("rel_res_fp64", C.c_double),
                 ("ic_shift", C.c_double), ("a_h", C.c_double), ("min_colsum", C.c_double),
                 ("h_within_strict_bound", C.c_int), ("h_within_practical_bound", C.c_int),
-                ("t_setup_ms", C.c_double), ("t_solve_ms", C.c_double)]
+                ("t_setup_ms", C.c_double), ("t_solve_ms", C.c_double), ("device_loop", C.c_int)]
 
 
 class Info(C.Structure):

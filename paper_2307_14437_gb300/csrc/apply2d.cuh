@@ -313,7 +313,8 @@ __global__ void __launch_bounds__(MAXT, MINB) row_fwd_t_kernel(
 template <class Real, int N, int E, int MAXT = (N / E > 256 ? N / E : 256), int MINB = 1>
 __global__ void __launch_bounds__(MAXT, MINB) col_conv_t_kernel(typename Cplx<Real>::T* __restrict__ specT, int ld, int n,
                                                        int ncols, int H, const typename Cplx<Real>::T* __restrict__ tw,
-                                                       const Real* __restrict__ lamT, int64_t sstride, int pm) {
+                                                       const Real* __restrict__ lamT, int64_t sstride, int pm,
+                                                       int64_t col0) {
     pdl_enter();
     using C = typename Cplx<Real>::T;
     specT += blockIdx.y * sstride;
@@ -333,13 +334,15 @@ __global__ void __launch_bounds__(MAXT, MINB) col_conv_t_kernel(typename Cplx<Re
     fft_ct<false, N, E, false>(v, buf, t, g, tw, 1);
     {
         // multiply by the (pre-scaled) symbol: row k_x1 folded to [0, N/2].
-        // 2D (pm = 0): column = k_x0.  3D (pm = P): column = k_x0 * P + k_x1'
-        // with k_x1' folded too; the symbol row is (k_x0, fold(k_x1')).
-        const int cc = active ? col : 0;
+        // 2D (pm = 0): column = k_x0.  3D (pm = P): column col0 + col =
+        // k_x0 * P + k_x1' with k_x1' folded too; the symbol row is
+        // (k_x0, fold(k_x1')).
+        const int64_t cc = (active ? col : 0) + col0;
         int64_t lrow = cc;
         if (pm) {
-            const int a = cc / pm, b = cc % pm;
-            lrow = (int64_t)a * H + (b <= pm / 2 ? b : pm - b);
+            const int64_t a = cc / pm;
+            const int b = (int)(cc % pm);
+            lrow = a * H + (b <= pm / 2 ? b : pm - b);
         }
         const Real* lc = lamT + lrow * H;
         each_elem_r<ct_last<N, E, false>(), E>(t, nthr, N, [&](int i, int row) {

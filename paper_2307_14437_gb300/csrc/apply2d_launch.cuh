@@ -76,7 +76,7 @@ void run_e(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, int n
                p->run_len.as<int32_t>(), p->run_e0.as<int32_t>(), vgrid, nlines, n, tw, S, p->ldT, lpc, xs, sb);
     mark_stage(st, "gather_row_fft");
     launch_pdl(col_kernel<NC, EC>(), dim3((unsigned)((H + G - 1) / G), nb), dim3(G * tc), col_smem(NC, G), st, S,
-               p->ldT, n, H, H, tw, lamT, sb, 0);
+               p->ldT, n, H, H, tw, lamT, sb, 0, (int64_t)0);
     mark_stage(st, "col_fft_conv");
     launch_pdl(row_inv_t_kernel<Real, NR, ER>, dim3(rblocks, nb), dim3(lpc * tr), row_smem(NR, lpc), st, S, p->ldT,
                nlines, n, tw, wgrid, lpc, sb, ws);

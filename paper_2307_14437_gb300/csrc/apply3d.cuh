@@ -7,7 +7,9 @@
 //
 //   plane_fwd_t   lines along k_1 (contiguous), forward FFT of length P over
 //                 the n nonzero entries, output stored transposed through a
-//                 shared-memory tile: M[k_x0][k_x1'][k_2] (k_2 fastest)
+//                 shared-memory tile: M[k_x0 - k0][k_x1'][k_2] (k_2 fastest)
+//
+// The planes are taken in chunks [k0, k0 + K) that bound the size of M.
 //   col_conv_t    (shared with 2D) lines along k_2, contiguous in M: forward
 //                 FFT, times the symbol row (k_x0, k_x1'), inverse FFT, n kept
 //   plane_inv_t   transposed tile load of G lines along k_x1', inverse FFT of
@@ -24,14 +26,14 @@ namespace gofd {
 template <class Real, int N, int E>
 __global__ void __launch_bounds__(N / E > 256 ? N / E : 256) plane_fwd_t_kernel(
     const typename Cplx<Real>::T* __restrict__ specT, int64_t ld, typename Cplx<Real>::T* __restrict__ M, int n,
-    int ngroups, const typename Cplx<Real>::T* __restrict__ tw) {
+    int ngroups, int kx0, const typename Cplx<Real>::T* __restrict__ tw) {
     pdl_enter();
     using C = typename Cplx<Real>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* sm = reinterpret_cast<C*>(smem_raw);
     constexpr int nthr = N / E;
     const int G = blockDim.x / nthr, msk = G - 1, gsh = __ffs(G) - 1;   // G is a power of two
-    const int kx = blockIdx.x / ngroups, k20 = (blockIdx.x % ngroups) * G;
+    const int kl = blockIdx.x / ngroups, kx = kx0 + kl, k20 = (blockIdx.x % ngroups) * G;
     const int g = threadIdx.x / nthr, t = threadIdx.x % nthr;
     const int k2 = k20 + g;
     const bool active = k2 < n;
@@ -44,7 +46,7 @@ __global__ void __launch_bounds__(N / E > 256 ? N / E : 256) plane_fwd_t_kernel(
     __syncthreads();   // the tile reuses the line buffers
     each_elem_r<ct_last<N, E, false>(), E>(t, nthr, N, [&](int i, int pos) { sm[pos * G + (g ^ (pos & msk))] = v[i]; });
     __syncthreads();
-    C* out = M + (int64_t)kx * N * n;
+    C* out = M + (int64_t)kl * N * n;   // plane kl of the chunk
     for (int i = threadIdx.x; i < N * G; i += blockDim.x) {
         const int pos = i >> gsh, l = i & msk;
         if (k20 + l < n) out[(int64_t)pos * n + k20 + l] = sm[pos * G + (l ^ (pos & msk))];
@@ -53,16 +55,16 @@ __global__ void __launch_bounds__(N / E > 256 ? N / E : 256) plane_fwd_t_kernel(
 
 template <class Real, int N, int E>
 __global__ void __launch_bounds__(N / E > 256 ? N / E : 256) plane_inv_t_kernel(
-    const typename Cplx<Real>::T* __restrict__ M, int n, int ngroups, typename Cplx<Real>::T* __restrict__ specT,
-    int64_t ld, const typename Cplx<Real>::T* __restrict__ tw) {
+    const typename Cplx<Real>::T* __restrict__ M, int n, int ngroups, int kx0,
+    typename Cplx<Real>::T* __restrict__ specT, int64_t ld, const typename Cplx<Real>::T* __restrict__ tw) {
     pdl_enter();
     using C = typename Cplx<Real>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* sm = reinterpret_cast<C*>(smem_raw);
     constexpr int nthr = N / E;
     const int G = blockDim.x / nthr, msk = G - 1, gsh = __ffs(G) - 1;   // G is a power of two
-    const int kx = blockIdx.x / ngroups, k20 = (blockIdx.x % ngroups) * G;
-    const C* in = M + (int64_t)kx * N * n;
+    const int kl = blockIdx.x / ngroups, kx = kx0 + kl, k20 = (blockIdx.x % ngroups) * G;
+    const C* in = M + (int64_t)kl * N * n;
     for (int i = threadIdx.x; i < N * G; i += blockDim.x) {
         const int pos = i >> gsh, l = i & msk;
         sm[pos * G + (l ^ (pos & msk))] = (k20 + l < n) ? in[(int64_t)pos * n + k20 + l] : cmk<C>(0.0, 0.0);

@@ -54,15 +54,19 @@ void run3_e(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, cuda
                (int64_t)0, (int64_t)0);
     mark_stage(st, "gather_row_fft");
     const int ngroups = (n + G - 1) / G;
-    launch_pdl(plane_fwd_t_kernel<Real, NC, EC>, dim3((unsigned)(H * ngroups)), dim3(G * tc), mid_smem3(NC, G), st,
-               (const C*)S, ld, M, n, ngroups, tw);
-    mark_stage(st, "plane_fft_axis1");
-    launch_pdl(col_conv_t_kernel<Real, NC, ECC>, dim3((unsigned)(((int64_t)H * P + GC - 1) / GC)), dim3(GC * tcc),
-               mid_smem3(NC, GC), st, M, n, n, (int)((int64_t)H * P), H, tw, lamT, (int64_t)0, P);
-    mark_stage(st, "conv_axis2");
-    launch_pdl(plane_inv_t_kernel<Real, NC, EC>, dim3((unsigned)(H * ngroups)), dim3(G * tc), mid_smem3(NC, G), st,
-               (const C*)M, n, ngroups, S, ld, tw);
-    mark_stage(st, "plane_ifft_axis1");
+    // planes k_x0 in chunks of p->midK so that the chunk's middle buffer
+    // stays in L2 from the axis-1 FFT through the inverse
+    for (int k0 = 0; k0 < H; k0 += p->midK) {
+        const int kc = std::min(p->midK, H - k0);
+        launch_pdl(plane_fwd_t_kernel<Real, NC, EC>, dim3((unsigned)(kc * ngroups)), dim3(G * tc), mid_smem3(NC, G),
+                   st, (const C*)S, ld, M, n, ngroups, k0, tw);
+        launch_pdl(col_conv_t_kernel<Real, NC, ECC>, dim3((unsigned)(((int64_t)kc * P + GC - 1) / GC)),
+                   dim3(GC * tcc), mid_smem3(NC, GC), st, M, n, n, (int)((int64_t)kc * P), H, tw, lamT, (int64_t)0,
+                   P, (int64_t)k0 * P);
+        launch_pdl(plane_inv_t_kernel<Real, NC, EC>, dim3((unsigned)(kc * ngroups)), dim3(G * tc), mid_smem3(NC, G),
+                   st, (const C*)M, n, ngroups, k0, S, ld, tw);
+    }
+    mark_stage(st, "axis12_conv");
     launch_pdl(row_inv_t_kernel<Real, NR, ER>, dim3(rblocks), dim3(lpc * tr), row_smem3(NR, lpc), st, (const C*)S,
                (int)ld, nlines, n, tw, wgrid, lpc, (int64_t)0, (int64_t)0);
     mark_stage(st, "row_ifft");

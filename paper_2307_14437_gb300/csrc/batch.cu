@@ -32,7 +32,7 @@ struct BatchWork {
     DevBuf b64, x64, r64, p64, q64, z64, d64;
     DevBuf r32, p32, q32, z32, d32;
     DevBuf grid, spec, partial, counters;
-    DevBuf red, cnt, scal, colv;
+    DevBuf red, cnt, scal, colv, ctl;
     std::vector<BScal> host;
     // own stream (joined to the caller's by events) so that `check` block-PCG
     // iterations are captured once as a CUDA graph per precision and batch size
@@ -40,6 +40,7 @@ struct BatchWork {
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int graph_nb[2] = {0, 0};
+    bool no_graph = false;
     ~BatchWork() {
         for (auto& g : graph)
             if (g) cudaGraphExecDestroy(g);
@@ -164,6 +165,23 @@ __global__ void bupdate_p_kernel(V* __restrict__ Pp, const V* __restrict__ Z, in
         p[i] = (V)((double)z[i] + b * (double)p[i]);
 }
 
+// device-side loop control of the block PCG: ctl = {iterations done, maxit}
+__global__ void bloop_arm_kernel(int* ctl, int maxit) {
+    ctl[0] = 0;
+    ctl[1] = maxit;
+}
+
+__global__ void bloop_continue_kernel(cudaGraphConditionalHandle h, const BScal* s, int nb, int* ctl, int check) {
+    int all = 1;
+    for (int c = threadIdx.x; c < nb; c += blockDim.x) all &= s[c].done != 0;
+    all = __syncthreads_and(all);
+    if (threadIdx.x == 0) {
+        ctl[0] += check;
+        const bool more = !all && ctl[0] + check <= ctl[1];
+        cudaGraphSetConditional(h, more ? 1u : 0u);
+    }
+}
+
 __global__ void bset_start_kernel(BScal* s, const double* __restrict__ rtol, int nb) {
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < nb; c += gridDim.x * blockDim.x) {
         BScal& x = s[c];
@@ -241,6 +259,7 @@ static BatchWork* ensure_batch(gofd_problem* p, int nb) {
     GOFD_CUDA_TRY(cudaMemset(w->cnt.ptr, 0, sizeof(unsigned) * nb));
     w->scal.alloc(sizeof(BScal) * nb);
     w->colv.alloc(8 * 3 * nb);
+    w->ctl.alloc(sizeof(int) * 2);
     GOFD_CUDA_TRY(cudaStreamCreateWithFlags(&w->gs, cudaStreamNonBlocking));
     GOFD_CUDA_TRY(cudaEventCreateWithFlags(&w->ev_in, cudaEventDisableTiming));
     GOFD_CUDA_TRY(cudaEventCreateWithFlags(&w->ev_out, cudaEventDisableTiming));
@@ -313,33 +332,33 @@ static int bpcg(gofd_problem* p, BatchWork* w, int nb, V* D, V* R, V* Pd, V* Q, 
         cudaGraphExecDestroy(w->graph[gi]);
         w->graph[gi] = nullptr;
     }
-    if (!w->graph[gi] && st == w->gs && maxit >= check) {
-        cudaGraph_t g = nullptr;
-        GOFD_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    if (!w->graph[gi] && !w->no_graph && st == w->gs && maxit >= check) {
         try {
-            for (int k = 0; k < check; ++k) iteration();
-        } catch (...) {
-            cudaStreamEndCapture(st, &g);
-            if (g) cudaGraphDestroy(g);
-            throw;
-        }
-        GOFD_CUDA_TRY(cudaStreamEndCapture(st, &g));
-        const cudaError_t e = cudaGraphInstantiate(&w->graph[gi], g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) {
+            build_loop_graph(st, check, iteration, [&](cudaGraphConditionalHandle h) {
+                bloop_continue_kernel<<<1, 128, 0, st>>>(h, s, nb, w->ctl.as<int>(), check);
+            }, &w->graph[gi]);
+            w->graph_nb[gi] = nb;
+        } catch (const Error&) {   // no device-side loop here: iterate from the host
             w->graph[gi] = nullptr;
-            fail(GOFD_E_CUDA, std::string("graph instantiation: ") + cudaGetErrorString(e));
+            w->no_graph = true;
+            cudaGetLastError();
         }
-        w->graph_nb[gi] = nb;
     }
-    while (it < maxit) {
-        if (w->graph[gi] && st == w->gs && it % check == 0 && it + check <= maxit) {
-            GOFD_CUDA_TRY(cudaGraphLaunch(w->graph[gi], st));
-            it += check;
-        } else {
-            iteration();
-            ++it;
-        }
+    bool done = false;
+    if (w->graph[gi] && st == w->gs && maxit >= check) {
+        bloop_arm_kernel<<<1, 1, 0, st>>>(w->ctl.as<int>(), maxit);
+        GOFD_CHECK_LAUNCH();
+        GOFD_CUDA_TRY(cudaGraphLaunch(w->graph[gi], st));
+        int hc[2] = {0, 0};
+        GOFD_CUDA_TRY(cudaMemcpyAsync(hc, w->ctl.ptr, sizeof hc, cudaMemcpyDeviceToHost, st));
+        read_bscal(w, nb, st);
+        it = hc[0];
+        done = true;
+        for (int c = 0; c < nb; ++c) done &= w->host[c].done != 0;
+    }
+    while (!done && it < maxit) {
+        iteration();
+        ++it;
         if (it % check == 0 || it == maxit) {
             read_bscal(w, nb, st);
             bool all = true;
@@ -450,6 +469,7 @@ void solve_batch(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs, int nb, co
             info.h_within_practical_bound = p->h <= p->a_h;
             info.t_setup_ms = p->t_setup_ms;
             info.t_solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+            info.device_loop = !w->no_graph && (w->graph[0] || w->graph[1]);
         }
     if (!all_done) fail(GOFD_E_NOT_CONVERGED, "batched solver reached maxit before tol");
 }

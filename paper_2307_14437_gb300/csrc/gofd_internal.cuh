@@ -76,6 +76,49 @@ inline void launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
 }
 
 // ---------------------------------------------------------------------------
+// device-side solver loops: a CUDA graph whose conditional while node runs
+// `check` iterations (body, captured from stream st) followed by a control
+// kernel (control(handle), which calls cudaGraphSetConditional) as long as the
+// control kernel asks for more.  *exec receives the instantiated graph.
+// ---------------------------------------------------------------------------
+template <class Body, class Control>
+void build_loop_graph(cudaStream_t st, int check, Body& body, Control control, cudaGraphExec_t* exec) {
+    cudaGraph_t g = nullptr;
+    GOFD_CUDA_TRY(cudaGraphCreate(&g, 0));
+    struct Guard {
+        cudaGraph_t g;
+        ~Guard() { cudaGraphDestroy(g); }
+    } guard{g};
+    cudaGraphConditionalHandle h;
+    GOFD_CUDA_TRY(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp = {};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    GOFD_CUDA_TRY(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
+    cudaGraph_t bodyg = cp.conditional.phGraph_out[0];
+    GOFD_CUDA_TRY(cudaStreamBeginCaptureToGraph(st, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    try {
+        for (int k = 0; k < check; ++k) body();
+        control(h);
+        GOFD_CUDA_TRY(cudaGetLastError());
+    } catch (...) {
+        cudaGraph_t tmp = nullptr;
+        cudaStreamEndCapture(st, &tmp);
+        throw;
+    }
+    cudaGraph_t out = nullptr;
+    GOFD_CUDA_TRY(cudaStreamEndCapture(st, &out));
+    const cudaError_t e = cudaGraphInstantiate(exec, g, 0);
+    if (e != cudaSuccess) {
+        *exec = nullptr;
+        fail(GOFD_E_CUDA, std::string("graph instantiation: ") + cudaGetErrorString(e));
+    }
+}
+
+// ---------------------------------------------------------------------------
 // device buffers owned by the handle
 // ---------------------------------------------------------------------------
 struct DevBuf {
@@ -189,7 +232,8 @@ struct gofd_problem {
     gofd::DevBuf specB;        // 3D only: n x P x pitch0 complex
     gofd::DevBuf specT;        // 2D/3D: transposed half spectrum, (P/2+1) x ldT complex
     int ldT = 0;               // leading dimension of specT (n^(d-1) rounded up to 16)
-    gofd::DevBuf specM;        // 3D: middle-stage buffer, (P/2+1) x P x n complex
+    gofd::DevBuf specM;        // 3D: middle-stage buffer for midK planes, midK x P x n complex
+    int midK = 0;              // 3D: planes k_x0 per chunk of the middle stage
     int tune_lpc = 0, tune_cols = 0, tune_tpr = 0;  // launch shapes picked by the autotuner (0 = default)
     int tune_cole = 0;         // elements per thread of the column transforms (0 = default)
     gofd::DevBuf lamT64, lamT32;  // 2D/3D: scaled symbol with the axis order reversed

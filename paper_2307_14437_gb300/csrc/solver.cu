@@ -29,8 +29,25 @@ struct Scal {
     double rr;      // (r, r)
     double aux;
     int bad;        // breakdown flag
+    int it;         // iterations done by the device-side loop
+    double stop_rr; // the device-side loop stops once rr <= stop_rr
+    int maxit;      // ... or when another `check` iterations would pass maxit
     int pad;
 };
+
+// Device-side loop control: arm before the loop, decide after every `check`
+// iterations whether the conditional (while) node of the graph runs again.
+__global__ void loop_arm_kernel(Scal* s, double stop_rr, int maxit) {
+    s->it = 0;
+    s->stop_rr = stop_rr;
+    s->maxit = maxit;
+}
+
+__global__ void loop_continue_kernel(cudaGraphConditionalHandle h, Scal* s, int check) {
+    s->it += check;
+    const bool more = !s->bad && s->rr > s->stop_rr && s->it + check <= s->maxit;
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+}
 
 struct Workspace {
     DevBuf x64, r64, b64, p64, q64, z64, d64;
@@ -43,6 +60,7 @@ struct Workspace {
     cudaStream_t gs = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    bool no_graph = false;   // building the loop graph failed once: host-driven loop
     ~Workspace() {
         for (auto& g : graph)
             if (g) cudaGraphExecDestroy(g);
@@ -315,35 +333,37 @@ static int pcg(gofd_problem* p, Workspace* w, V* d, V* r, V* pv, V* q, V* z, dou
         update_p_kernel<V><<<nb, 256, 0, st>>>(pv, zz, n, s);
         GOFD_CHECK_LAUNCH();
     };
-    // `check` iterations as one CUDA graph (the vectors of a precision are
-    // always the workspace's, so the graph is built once per handle)
+    // The iterations run as one CUDA graph: a conditional while node whose
+    // body is `check` iterations and a kernel that decides on the device
+    // whether to go on (converged, breakdown or maxit reached), so the host
+    // does not wait between checks.  The vectors of a precision are always
+    // the workspace's, so the graph is built once per handle.
     cudaGraphExec_t& graph = w->graph[fp64 ? 1 : 0];
-    if (!graph && st == w->gs && maxit >= check) {
-        cudaGraph_t g = nullptr;
-        GOFD_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    if (!graph && !w->no_graph && st == w->gs && maxit >= check) {
         try {
-            for (int k = 0; k < check; ++k) iteration();
-        } catch (...) {
-            cudaStreamEndCapture(st, &g);
-            if (g) cudaGraphDestroy(g);
-            throw;
-        }
-        GOFD_CUDA_TRY(cudaStreamEndCapture(st, &g));
-        const cudaError_t e = cudaGraphInstantiate(&graph, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) {
+            build_loop_graph(st, check, iteration, [&](cudaGraphConditionalHandle h) {
+                loop_continue_kernel<<<1, 1, 0, st>>>(h, s, check);
+            }, &graph);
+        } catch (const Error&) {   // no device-side loop here: iterate from the host
             graph = nullptr;
-            fail(GOFD_E_CUDA, std::string("graph instantiation: ") + cudaGetErrorString(e));
+            w->no_graph = true;
+            cudaGetLastError();
         }
     }
-    while (it < maxit) {
-        if (graph && st == w->gs && it % check == 0 && it + check <= maxit) {
-            GOFD_CUDA_TRY(cudaGraphLaunch(graph, st));
-            it += check;
-        } else {
-            iteration();
-            ++it;
-        }
+    bool done = false;
+    if (graph && st == w->gs && maxit >= check) {
+        loop_arm_kernel<<<1, 1, 0, st>>>(s, rtol * rtol * r0 * r0, maxit);
+        GOFD_CHECK_LAUNCH();
+        GOFD_CUDA_TRY(cudaGraphLaunch(graph, st));
+        read_scal(w, st);
+        it = w->host->it;
+        rel = std::sqrt(w->host->rr) / r0;
+        done = w->host->bad || rel <= rtol;
+    }
+    // without the graph, or for the last iterations before maxit: one by one
+    while (!done && it < maxit) {
+        iteration();
+        ++it;
         if (it % check == 0 || it == maxit) {
             read_scal(w, st);
             if (w->host->bad) break;
@@ -443,6 +463,7 @@ void solve_core(gofd_problem* p, gofd_solve_mode mode, const double* b, double t
         info->h_within_practical_bound = p->h <= p->a_h;
         info->t_setup_ms = p->t_setup_ms;
         info->t_solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
+        info->device_loop = !w->no_graph && (w->graph[0] || w->graph[1]);
     }
     if (!converged) fail(GOFD_E_NOT_CONVERGED, "solver reached maxit before tol");
 }

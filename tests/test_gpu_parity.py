@@ -196,6 +196,16 @@ def test_solve_residual(built, name, mode):
     assert np.all(u[ref.boundary] == 0.0)
 
 
+def test_solver_iterations_run_as_device_loop(built):
+    gp, ref = built("disk37_ragged")
+    f = torch.ones(ref.n_grid, dtype=torch.float64, device="cuda")
+    for mode in ("mixed", "fp64"):
+        u, info = gp.solve(f, mode=mode, tol=1e-9)
+        assert info["device_loop"] == 1, info
+        b = o.rhs_grid(ref, np.ones(ref.n_grid))
+        assert np.linalg.norm(b - o.stiffness_apply(ref, u.cpu().numpy())) <= 1.05e-9 * np.linalg.norm(b)
+
+
 def test_solve_vertex_rhs_equals_grid_rhs_for_constant_f(built):
     # (GoFD-1) and (GoFD-3) give the same system for f = 1
     gp, ref = built("disk17")
@@ -288,3 +298,34 @@ def test_c1_solve_against_closed_form(c1):
     # (exam-2): u = (2/pi) (1-|x|^2)^{1/2}; the FM error is O(h) in L2
     err = o.lumped_l2(ref.verts, ref.simp, u - o.ball_exact(ref.verts, 0.5))
     assert err < 0.02, err
+
+
+def test_3d_afd_ragged_129():
+    # n = 129 (P = 256, a ragged tail in every axis); A_FD v against the
+    # oracle's zero-padded FFT convolution built from the same coefficients
+    # (T itself is pinned at small sizes above)
+    v, s = mg.ball_shell_mesh(shells=6, seed=mg.seed_for(3, 3))
+    lo, hi, h = mg.grid_box(3, 129)
+    gp = _gpu(v, s, 1.3, h, lo, hi, filon_M=2 ** 11)
+    T = gp.coefficients().reshape((129,) * 3)
+    lam = o.symbol(T, 256)
+    x = mg.random_vector(129 ** 3, 51)
+    want = o.afd_apply_fft(lam, x.reshape((129,) * 3), 256).ravel()
+    got64 = gp.afd_apply(torch.tensor(x, device="cuda")).cpu().numpy()
+    got32 = gp.afd_apply(torch.tensor(x, device="cuda", dtype=torch.float32)).cpu().numpy().astype(np.float64)
+    assert _rel(got64, want) < 1e-12
+    assert _rel(got32, want) < 1e-5
+    gp.close()
+
+
+def test_3d_products_do_not_depend_on_plane_chunks(built):
+    # the axis-1/axis-2 stage over chunks of 5 planes (13 chunks at P = 128)
+    # gives the same products, bit for bit, as over all planes at once
+    gp, ref = built("ball37_ragged")
+    d, v, s, n, alpha, M = _case("ball37_ragged")
+    lo, hi, h = mg.grid_box(d, n)
+    gc = _gpu(v, s, alpha, h, lo, hi, filon_M=M, chunk_planes=5)
+    u = torch.tensor(mg.random_vector(len(v), 52), device="cuda")
+    for dt in (torch.float64, torch.float32):
+        assert torch.equal(gc.apply(u.to(dt)), gp.apply(u.to(dt)))
+    gc.close()

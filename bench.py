@@ -21,6 +21,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -291,6 +292,33 @@ def run_gofd(args):
     e2e = {"value": round(world * B32 / (e2e_t * 1e-3) / 1e9, 2), "unit": "GB/s",
            "h2d_bytes_per_step": 4 * n_v, "d2h_bytes_per_step": 4 * n_v, "ms_per_step": round(e2e_t, 4)}
 
+    # the FP64 product: bound by FP64 arithmetic (its FFT passes); roofline
+    # against the measured FP64 FMA rate, with the unpruned FFT flop count
+    # 2 x 2.5 P^d log2(P^d) per product as the algorithmic work
+    from paper_2307_14437_gb300.gofd import fma_rates
+    fp64_peak, fp32_peak = fma_rates()
+    x64 = x.double()
+    y64 = torch.empty_like(x64)
+    for _ in range(3):
+        prob.apply_interior(x64, y64)
+    ev64 = []
+    for i in range(20):
+        flush.fill_(float(i))
+        a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a_.record(stream)
+        prob.apply_interior(x64, y64)
+        b_.record(stream)
+        ev64.append((a_, b_))
+    torch.cuda.synchronize()
+    ms64 = statistics.mean(a_.elapsed_time(b_) for a_, b_ in ev64)
+    fft_flops = 2 * 2.5 * P ** d * math.log2(P ** d)
+    roofline_fp64 = {"bound": "fp64_alu", "ms_per_product": round(ms64, 4),
+                     "achieved": round(fft_flops / (ms64 * 1e-3) / 1e9, 1), "peak": round(fp64_peak, 1),
+                     "unit": "GFLOP/s", "frac": round(fft_flops / (ms64 * 1e-3) / 1e9 / fp64_peak, 4),
+                     "work": "2 x 2.5 P^d log2 P^d flops per product (unpruned FFTs)",
+                     "peak_source": "measured FP64 FMA rate (gofd_fma_rates), this run",
+                     "fp32_fma_gflops": round(fp32_peak, 1)}
+
     # time to relative residual 1e-8: mixed refinement vs plain FP64 PCG
     pcg = {}
     if not args.no_pcg and args.workload == "lshape1024":
@@ -351,6 +379,42 @@ def run_gofd(args):
         pcg["graded disk 2048^2 alpha=1.2, f_target vertex data"] = row
         if pg is not prob:
             pg.close()
+    if not args.no_pcg and args.workload == "lshape1024":
+        # the small unit-disk configuration: FP64 PCG to 1e-10, f = 1, against
+        # the closed form u = (2/pi) (1 - |x|^2)^(1/2) (alpha = 1, Section 5)
+        v1, s1 = mg.disk_ring_mesh(rings=25, seed=mg.seed_for(1))
+        lo1, hi1, h1 = mg.grid_box(2, 128)
+        p1 = Problem(v1, s1, 1.0, h1, lo1, hi1)
+        f1 = torch.ones(p1.n_grid, dtype=torch.float64, device=dev)
+        p1.solve(f1, mode="fp64", tol=1e-10)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        u1, info1 = p1.solve(f1, mode="fp64", tol=1e-10)
+        torch.cuda.synchronize()
+        ex = (2.0 / math.pi) * np.sqrt(np.maximum(0.0, 1.0 - np.sum(v1 ** 2, axis=1)))
+        err = np.abs(u1.cpu().numpy() - ex)
+        pcg["unit disk 128^2 alpha=1 FP64 to 1e-10"] = {
+            "s": round(time.perf_counter() - t1, 5), "inner_iters": info1["inner_iters"],
+            "rel_res_fp64": info1["rel_res_fp64"], "max_abs_err_vs_closed_form": float(err.max()),
+            "rel_l2_err_vs_closed_form": float(np.linalg.norm(err) / np.linalg.norm(ex))}
+        p1.close()
+    if not args.no_pcg and args.workload == "ball256":
+        # the ball configuration: mixed vs FP64 PCG to 1e-8, f = 1, and the
+        # closed form u = C (1 - |x|^2)^(3/4), C = 0.300901 (alpha = 1.5, d = 3)
+        f3 = torch.ones(prob.n_grid, dtype=torch.float64, device=dev)
+        row = {}
+        for mode in ("mixed", "fp64"):
+            prob.solve(f3, mode=mode, tol=1e-8)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            u3, info3 = prob.solve(f3, mode=mode, tol=1e-8)
+            torch.cuda.synchronize()
+            row[mode] = {"s": round(time.perf_counter() - t1, 5), "inner_iters": info3["inner_iters"],
+                         "outer_iters": info3["outer_iters"], "rel_res_fp64": info3["rel_res_fp64"]}
+        row["speedup_mixed_vs_fp64"] = round(row["fp64"]["s"] / row["mixed"]["s"], 3)
+        ex = 0.300901 * np.maximum(0.0, 1.0 - np.sum(v ** 2, axis=1)) ** 0.75
+        row["rel_l2_err_vs_closed_form"] = float(np.linalg.norm(u3.cpu().numpy() - ex) / np.linalg.norm(ex))
+        pcg["ball 256^3 alpha=1.5 f=1"] = row
     clk = clocks.stop()
 
     if rank == 0:
@@ -366,7 +430,7 @@ def run_gofd(args):
                                              "cols_per_cta": inf["tune_cols_per_cta"],
                                              "scatter_lanes": inf["tune_scatter_lanes"],
                                              "col_elems": inf["tune_col_elems"]}},
-                "roofline": roofline, "e2e": e2e, "pcg": pcg,
+                "roofline": roofline, "roofline_fp64_product": roofline_fp64, "e2e": e2e, "pcg": pcg,
                 "gpu_launches": 4 * args.steps, "clocks": clk}
         if world == 1 and not args.no_cpu and args.workload == "lshape1024":
             try:

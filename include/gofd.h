@@ -362,6 +362,16 @@ gofd_status gofd_afd_apply(gofd_problem* p, gofd_precision prec,
 gofd_status gofd_afd_apply_noalloc(int d, int n, const float* lambda_dev, const float* v_dev,
                                    float* w_dev, void* stream);
 
+/*
+ * gofd_fma_rates -- measured fused multiply-add throughput of the current
+ * device in GFLOP/s (2 flops per FMA), FP64 and FP32 (either pointer may be
+ * NULL): independent FMA chains on every SM, timed with CUDA events on
+ * `stream` (synchronised).  A measurement utility with no counterpart in the
+ * paper: the FP64 product is bound by FP64 arithmetic, and its roofline
+ * needs this peak.  Takes about a tenth of a second.
+ */
+gofd_status gofd_fma_rates(void* stream, double* fp64_gflops, double* fp32_gflops);
+
 /* gofd_destroy -- free the handle and all of its device memory (NULL is a no-op). */
 void gofd_destroy(gofd_problem* p);
 

@@ -71,6 +71,7 @@ EXPORTS = {
     "gofd_afd_apply": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "gofd_afd_apply_noalloc": (C.c_int, [C.c_int, C.c_int, _P, _P, _P, _P]),
     "gofd_destroy": (None, [_P]),
+    "gofd_fma_rates": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "gofd_last_error": (C.c_char_p, [_P]),
 }
 

@@ -280,6 +280,16 @@ def solve_many(problems, batches, rhs: str = "grid", mode: str = "mixed", tol: f
     return out
 
 
+def fma_rates(stream=None):
+    """Measured FP64 and FP32 FMA throughput of the current device (GFLOP/s)."""
+    lib = N.load()
+    f64, f32 = C.c_double(0), C.c_double(0)
+    st = lib.gofd_fma_rates(_stream_ptr(stream), C.byref(f64), C.byref(f32))
+    if st != 0:
+        raise GofdError(st, "gofd_fma_rates failed")
+    return f64.value, f32.value
+
+
 def afd_apply_noalloc(d: int, n: int, lam_scaled, v, out=None, stream=None):
     """w = A_FD v (FP32) through the entry point that allocates nothing.
 

@@ -139,6 +139,22 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def shard(items, rank, world):
+    """This rank's share of independent work items (round robin; no collective)."""
+    return items[rank::world]
+
+
+def max_over_ranks(value, world, device):
+    """The largest value over the ranks (the slowest rank's time); one all-reduce."""
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def cpu_baseline(steps_cap=None, budget_s=20.0):
     """The FP64 oracle's stiffness product on the host cores, at full size."""
     import scipy.fft
@@ -234,12 +250,7 @@ def run_gofd(args):
     barrier()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     ms = statistics.mean(step_ms)
-    ms_max = ms
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, world, dev)
     value = world * B32 / (ms_max * 1e-3) / 1e9
 
     # per-kernel times (events after each launch), same L2 flush
@@ -478,7 +489,8 @@ def run_batch(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    specs = mg.batch_instances()[rank::world]          # instances are independent: shard, no collective
+    all_specs = mg.batch_instances()
+    specs = shard(all_specs, rank, world)              # instances are independent: shard, no collective
     meshes, probs, Fs, rows = {}, [], [], []
     t0 = time.perf_counter()
     for sp in specs:
@@ -564,13 +576,10 @@ def run_batch(args):
         - (BATCH_RHS - 1) * 4 * (inf["P"] // 2 + 1) ** 2        # the symbol is read once per batch
     hbm = peaks().get("hbm_gbs", 6800.0)
     clk = clocks.stop()
-    nsolves = world * len(probs) * BATCH_RHS
-    t_max = t_batch
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([t_batch], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    nsolves = len(all_specs) * BATCH_RHS                # all ranks together
+    t_max = max_over_ranks(t_batch, world, dev)
+    t_single = max_over_ranks(t_single, world, dev)
+    t_e2e = max_over_ranks(t_e2e, world, dev)
     if rank == 0:
         line = {"metric": BATCH_METRIC, "value": round(nsolves / t_max, 3), "unit": "solves/s", "n_gpus": world,
                 "steps": steps, "warmup": warm, "ms_per_step": round(1e3 * t_max, 2), "higher_is_better": True,

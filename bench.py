@@ -512,6 +512,7 @@ def run_batch(args):
     t1 = time.perf_counter()
     for pr, r in zip(probs, rows):
         r["tuned_ms_per_product"] = round(pr.autotune(nb=BATCH_RHS), 4)
+        r["batch_chunk"] = pr.info()["tune_batch_chunk"]
     t_tune = time.perf_counter() - t1
     torch.cuda.synchronize()
 

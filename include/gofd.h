@@ -128,7 +128,8 @@ typedef struct {
     int tune_lines_per_cta;    /* launch shapes in use (0 = built-in default; set by gofd_autotune):   */
     int tune_cols_per_cta;     /*   grid lines per CTA of the row FFTs, columns per CTA of the column */
     int tune_scatter_lanes;    /*   FFTs, lanes per row of the I^T scatter,                           */
-    int tune_col_elems;        /*   elements per thread of the column FFTs                            */
+    int tune_col_elems;        /*   elements per thread of the column FFTs,                           */
+    int tune_batch_chunk;      /*   columns per sub-batch of the 2D batched product (0 = all)         */
 } gofd_info;
 
 /*
@@ -277,7 +278,8 @@ gofd_status gofd_solve_batch(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs
  * launch shape (elements per thread of the column FFTs, grid lines per CTA
  * in the row FFTs, columns per CTA in the column FFTs, lanes per row in the
  * scatter; one choice at a time with the others at their best so far) and
- * keep the fastest in the handle for all later products.  *best_ms (may be
+ * keep the fastest in the handle for all later products; with nb > 1 in 2D
+ * also the number of columns per sub-batch of the batched product.  *best_ms (may be
  * NULL) receives its time per product of nb columns.  CTA shapes leave every
  * result bit unchanged; the column elements per thread (the FFT's radix
  * plan) and the scatter's lanes per row change the rounding order, so

@@ -315,6 +315,7 @@ gofd_status gofd_get_info(const gofd_problem* p, gofd_info* info) {
     info->tune_cols_per_cta = p->tune_cols;
     info->tune_scatter_lanes = p->tune_tpr;
     info->tune_col_elems = p->tune_cole;
+    info->tune_batch_chunk = p->tune_bchunk;
     return GOFD_OK;
 }
 

@@ -619,13 +619,25 @@ int apply_interior_profiled(gofd_problem* p, bool fp64, const void* x, void* y, 
 void apply_interior_batch(gofd_problem* p, bool fp64, const void* x, void* y, int nb, int64_t ld, void* grid_ws,
                           void* spec_ws, void* partial_ws, void* counter_ws, cudaStream_t st) {
     if (p->d == 2) {
+        // columns in sub-batches of p->tune_bchunk (0: all at once); each
+        // sub-batch reuses the first workspace slots, so a small one keeps its
+        // spectra in L2
         const int64_t ws = p->ngrid;
-        if (fp64) {
-            afd_2d_f64(p, (const double*)x, nullptr, (double*)grid_ws, nb, ld, ws, spec_ws, st);
-            scatter_b<double>(p, (const double*)grid_ws, (double*)y, 1.0, nb, ws, ld, (double*)partial_ws, (unsigned*)counter_ws, st);
-        } else {
-            afd_2d_f32(p, (const float*)x, nullptr, (float*)grid_ws, nb, ld, ws, spec_ws, st);
-            scatter_b<float>(p, (const float*)grid_ws, (float*)y, 1.0f, nb, ws, ld, (float*)partial_ws, (unsigned*)counter_ws, st);
+        const int cs = (p->tune_bchunk > 0 && p->tune_bchunk < nb) ? p->tune_bchunk : nb;
+        const size_t b = fp64 ? 8 : 4;
+        for (int c0 = 0; c0 < nb; c0 += cs) {
+            const int k = std::min(cs, nb - c0);
+            const char* xc = (const char*)x + (int64_t)c0 * ld * b;
+            char* yc = (char*)y + (int64_t)c0 * ld * b;
+            if (fp64) {
+                afd_2d_f64(p, (const double*)xc, nullptr, (double*)grid_ws, k, ld, ws, spec_ws, st);
+                scatter_b<double>(p, (const double*)grid_ws, (double*)yc, 1.0, k, ws, ld, (double*)partial_ws,
+                                  (unsigned*)counter_ws, st);
+            } else {
+                afd_2d_f32(p, (const float*)xc, nullptr, (float*)grid_ws, k, ld, ws, spec_ws, st);
+                scatter_b<float>(p, (const float*)grid_ws, (float*)yc, 1.0f, k, ws, ld, (float*)partial_ws,
+                                 (unsigned*)counter_ws, st);
+            }
         }
         return;
     }

@@ -515,9 +515,9 @@ double autotune(gofd_problem* p, int nb, cudaStream_t st) {
     const std::vector<int> shapes = p->d == 2 ? std::vector<int>{1, 2, 4} : std::vector<int>{0};
     const std::vector<int> elems = p->d == 1 ? std::vector<int>{0} : std::vector<int>{8, 16, 32};
     const std::vector<int> lanes = {4, 8, 16, 32};
-    p->tune_cole = p->tune_lpc = p->tune_cols = p->tune_tpr = 0;
+    p->tune_cole = p->tune_lpc = p->tune_cols = p->tune_tpr = p->tune_bchunk = 0;
     double best = time_current();
-    int be = 0, bl = 0, bc = 0, bt = 0;
+    int be = 0, bl = 0, bc = 0, bt = 0, bk = 0;
     auto sweep = [&](int* field, const std::vector<int>& vals, int* keep) {
         for (int v : vals) {
             *field = v;
@@ -533,6 +533,13 @@ double autotune(gofd_problem* p, int nb, cudaStream_t st) {
     sweep(&p->tune_lpc, shapes, &bl);
     sweep(&p->tune_cols, shapes, &bc);
     sweep(&p->tune_tpr, lanes, &bt);
+    if (p->d == 2 && nb > 1) {
+        std::vector<int> chunks;
+        for (int k : {1, 2, 4})
+            if (k < nb) chunks.push_back(k);
+        sweep(&p->tune_bchunk, chunks, &bk);
+    }
+    p->tune_bchunk = bk;
     p->tune_cole = be;
     p->tune_lpc = bl;
     p->tune_cols = bc;

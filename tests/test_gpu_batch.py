@@ -214,3 +214,26 @@ def test_batch_argument_errors(built):
     X = torch.zeros((2, 3), dtype=torch.float64, device="cuda")
     with pytest.raises(GofdError):
         gp.apply_interior_batch(X, torch.zeros_like(X))   # ld < n_int + 1
+
+
+def test_tuned_batched_product_equals_single_products(built):
+    # whatever shapes and sub-batch size the tuner picks, every column of the
+    # batched product equals the single-vector product with the same shapes
+    from paper_2307_14437_gb300 import Problem
+    _, ref = built("disk65")
+    gp = Problem(ref.verts, ref.simp, ref.alpha, ref.h, ref.box_lo, ref.box_hi, filon_M=2 ** 10)
+    gp.autotune(nb=5)
+    info = gp.info()
+    assert info["tune_batch_chunk"] in (0, 1, 2, 4)
+    U = np.stack([mg.random_vector(len(ref.verts), 1100 + c) for c in range(5)])
+    X, iv = _compact(gp, U, pad=3)
+    nint = len(iv)
+    for dt in (torch.float32, torch.float64):
+        Xd = torch.tensor(X, device="cuda", dtype=dt)
+        Yd = torch.empty_like(Xd)
+        gp.apply_interior_batch(Xd, Yd)
+        for c in range(5):
+            y1 = torch.empty(nint, device="cuda", dtype=dt)
+            gp.apply_interior(Xd[c, :nint + 1].contiguous(), y1)
+            assert torch.equal(Yd[c, :nint], y1), (dt, c, info)
+    gp.close()

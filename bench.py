@@ -391,6 +391,27 @@ def run_gofd(args):
         if pg is not prob:
             pg.close()
     if not args.no_pcg and args.workload == "lshape1024":
+        # the paper's preconditioner in its own setting, h_FD about a_h (Section
+        # 3.3, Remark 3.5): the same L-shape mesh on a 385^2 grid, alpha 1 and
+        # 1.8 (s = 0.9), plain CG against IC(1) of the 5- and 9-point stencil
+        # matrices (multicolour order), mixed precision to 1e-8
+        lo_c, hi_c, h_c = mg.grid_box(2, 385)
+        ic = {}
+        for a in (1.0, 1.8):
+            for pat in (0, 5, 9):
+                pp = Problem(v, s, a, h_c, lo_c, hi_c, precond=pat, ordering=1 if pat else 0)
+                f = torch.ones(pp.n_grid, dtype=torch.float64, device=dev)
+                pp.solve(f, mode="mixed", tol=1e-8)
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                _, info = pp.solve(f, mode="mixed", tol=1e-8)
+                torch.cuda.synchronize()
+                ic[f"alpha={a} {'plain CG' if pat == 0 else f'IC(1) {pat}-point'}"] = {
+                    "s": round(time.perf_counter() - t1, 5), "inner_iters": info["inner_iters"],
+                    "rel_res_fp64": info["rel_res_fp64"], "h_over_a_h": round(h_c / info["a_h"], 3)}
+                pp.close()
+        pcg["L-shape 385^2 (h about a_h): preconditioners"] = ic
+    if not args.no_pcg and args.workload == "lshape1024":
         # the small unit-disk configuration: FP64 PCG to 1e-10, f = 1, against
         # the closed form u = (2/pi) (1 - |x|^2)^(1/2) (alpha = 1, Section 5)
         v1, s1 = mg.disk_ring_mesh(rings=25, seed=mg.seed_for(1))

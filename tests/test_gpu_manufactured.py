@@ -1,0 +1,76 @@
+"""Manufactured solutions with k > 0 on the unit disk (Section 5, (exam-0) and
+(exam-2)): for
+
+    f = 2^{2s} Gamma(1+s+k) Gamma(d/2+s+k) / (k! Gamma(d/2+k)) P_k^{(s, d/2-1)}(2|x|^2 - 1)
+
+the exact solution of (FL-1) on the unit ball is
+u = (1 - |x|^2)_+^s P_k^{(s, d/2-1)}(2|x|^2 - 1).  The GPU solves (GoFD-3) with
+vertex data on a ladder of ring meshes (overlay box 1.1 times the domain and
+h_FD about a_h, as the paper takes them) and the mass-lumped L2 error must
+fall at least at the rate the paper reports for fixed meshes,
+O(h^{min(1, s+1/2)}) (Example 5.1, Remark 3.6).  On these meshes the observed
+vertex-error order for smooth data can exceed it (the FP64 oracle gives 1.26
+at s = 1/2 and 0.84 at s = 1/4 on the same ladder), so the paper's order is a
+lower bound here (minus 0.15 for the finite ladder).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import meshgen as mg
+from oracle import gofd as o
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+special = pytest.importorskip("scipy.special")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2307_14437_gb300 import build_native
+    build_native.build()
+
+
+def _jacobi(k, s, d, r2):
+    return special.eval_jacobi(k, s, d / 2.0 - 1.0, 2.0 * r2 - 1.0)
+
+
+def _rhs(k, s, d, x):
+    r2 = np.sum(x * x, axis=1)
+    c = 2.0 ** (2 * s) * math.gamma(1 + s + k) * math.gamma(d / 2 + s + k) / (math.factorial(k) * math.gamma(d / 2 + k))
+    return c * _jacobi(k, s, d, r2)
+
+
+def _exact(k, s, d, x):
+    r2 = np.sum(x * x, axis=1)
+    return np.maximum(0.0, 1.0 - r2) ** s * _jacobi(k, s, d, r2)
+
+
+def _error(rings, alpha, k):
+    from paper_2307_14437_gb300 import Problem
+    v, s = mg.disk_ring_mesh(rings=rings, seed=mg.seed_for(6, rings))
+    n = int(round(5.3 * rings)) + 1                   # h_FD about a_h
+    lo, hi, h = mg.grid_box(2, n, -1.1, 1.1)
+    gp = Problem(v, s, alpha, h, lo, hi)
+    sv = alpha / 2
+    f = torch.tensor(_rhs(k, sv, 2, v), device="cuda")
+    u, info = gp.solve(f, rhs="vertex", mode="mixed", tol=1e-10)
+    assert info["rel_res_fp64"] <= 1e-10
+    gp.close()
+    ue = _exact(k, sv, 2, v)
+    return o.lumped_l2(v, s, u.cpu().numpy() - ue) / o.lumped_l2(v, s, ue)
+
+
+@pytest.mark.parametrize("alpha,k", [(1.0, 3), (0.5, 2)])
+def test_manufactured_solution_converges_at_the_paper_rate(alpha, k):
+    ladder = [24, 48, 96]
+    errs = [_error(r, alpha, k) for r in ladder]
+    rate = math.log(errs[1] / errs[2]) / math.log(ladder[2] / ladder[1])
+    expect = min(1.0, alpha / 2 + 0.5)
+    assert errs[2] < errs[1] < errs[0], errs
+    assert rate >= expect - 0.15, (rate, expect, errs)
+    assert errs[2] < 0.04, errs

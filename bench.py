@@ -392,10 +392,11 @@ def run_gofd(args):
             pg.close()
     if not args.no_pcg and args.workload == "lshape1024":
         # the paper's preconditioner in its own setting, h_FD about a_h (Section
-        # 3.3, Remark 3.5): the same L-shape mesh on a 385^2 grid, alpha 1 and
-        # 1.8 (s = 0.9), plain CG against IC(1) of the 5- and 9-point stencil
-        # matrices (multicolour order), mixed precision to 1e-8
-        lo_c, hi_c, h_c = mg.grid_box(2, 385)
+        # 3.3, Remark 3.5): the same L-shape mesh on the grid with h just below
+        # a_h, alpha 1 and 1.8 (s = 0.9), plain CG against IC(1) of the 5- and
+        # 9-point stencil matrices (multicolour order), mixed precision to 1e-8
+        n_c = int(math.ceil(2.0 / inf["a_h"])) + 1
+        lo_c, hi_c, h_c = mg.grid_box(2, n_c)
         ic = {}
         for a in (1.0, 1.8):
             for pat in (0, 5, 9):
@@ -410,7 +411,7 @@ def run_gofd(args):
                     "s": round(time.perf_counter() - t1, 5), "inner_iters": info["inner_iters"],
                     "rel_res_fp64": info["rel_res_fp64"], "h_over_a_h": round(h_c / info["a_h"], 3)}
                 pp.close()
-        pcg["L-shape 385^2 (h about a_h): preconditioners"] = ic
+        pcg[f"L-shape {n_c}^2 (h about a_h): preconditioners"] = ic
     if not args.no_pcg and args.workload == "lshape1024":
         # the small unit-disk configuration: FP64 PCG to 1e-10, f = 1, against
         # the closed form u = (2/pi) (1 - |x|^2)^(1/2) (alpha = 1, Section 5)

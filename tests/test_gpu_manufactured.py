@@ -74,3 +74,28 @@ def test_manufactured_solution_converges_at_the_paper_rate(alpha, k):
     assert errs[2] < errs[1] < errs[0], errs
     assert rate >= expect - 0.15, (rate, expect, errs)
     assert errs[2] < 0.04, errs
+
+
+@pytest.mark.parametrize("alpha", [0.5, 1.5])
+def test_1d_rates_of_example_5_1(alpha):
+    # Example 5.1: the 1D problem with k = 0 on uniform meshes, h_FD = a_h (grid
+    # nodes on the mesh vertices), box 1.1 times the domain; the paper reports
+    # O(h^s) in the maximum norm and O(h^{min(1, s+1/2)}) in L2 (the FP64 oracle
+    # reproduces 0.25 / 0.75 at s = 1/4 and 0.75 / 0.98 at s = 3/4)
+    from paper_2307_14437_gb300 import Problem
+    sv = alpha / 2
+    e2, ei = [], []
+    ladder = [80, 160, 320, 640]
+    for cells in ladder:
+        v, s = mg.interval_mesh(cells, jitter=0.0)
+        gp = Problem(v, s, alpha, 2.0 / cells, [-1.1], [1.1])
+        f = torch.tensor(_rhs(0, sv, 1, v), device="cuda")
+        u, info = gp.solve(f, rhs="vertex", mode="fp64", tol=1e-12)
+        gp.close()
+        err = u.cpu().numpy() - _exact(0, sv, 1, v)
+        e2.append(o.lumped_l2(v, s, err))
+        ei.append(np.abs(err).max())
+    r2 = math.log(e2[-2] / e2[-1]) / math.log(2)
+    ri = math.log(ei[-2] / ei[-1]) / math.log(2)
+    assert abs(r2 - min(1.0, sv + 0.5)) <= 0.1, (r2, e2)
+    assert abs(ri - sv) <= 0.1, (ri, ei)

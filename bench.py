@@ -387,6 +387,23 @@ def run_gofd(args):
             row[mode] = {"s": round(time.perf_counter() - t1, 5), "inner_iters": info["inner_iters"],
                          "outer_iters": info["outer_iters"], "rel_res_fp64": info["rel_res_fp64"]}
         row["speedup_mixed_vs_fp64"] = round(row["fp64"]["s"] / row["mixed"]["s"], 3)
+        # the diagonal of S as preconditioner (its set-up timed apart)
+        g_args = (v, s, alpha, h, lo, hi) if pg is prob else (vg_, sg_, ag_, hg_, log_, hig_)
+        t1 = time.perf_counter()
+        pj = Problem(*g_args, precond=1)
+        row["diagonal_precond_build_s"] = round(time.perf_counter() - t1, 3)
+        pj.autotune(nb=1)
+        for mode in ("mixed", "fp64"):
+            pj.solve(ft, rhs="vertex", mode=mode, tol=1e-8)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            _, info = pj.solve(ft, rhs="vertex", mode=mode, tol=1e-8)
+            torch.cuda.synchronize()
+            row[mode + " + diagonal precond"] = {"s": round(time.perf_counter() - t1, 5),
+                                                 "inner_iters": info["inner_iters"],
+                                                 "outer_iters": info["outer_iters"],
+                                                 "rel_res_fp64": info["rel_res_fp64"]}
+        pj.close()
         pcg["graded disk 2048^2 alpha=1.2, f_target vertex data"] = row
         if pg is not prob:
             pg.close()

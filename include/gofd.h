@@ -79,7 +79,9 @@ typedef enum {
 } gofd_rhs;
 
 typedef struct {
-    int precond;               /* 0: none; 5 or 9 (2D), 7 or 27 (3D), 3 (1D): IC(ic_level) of I^T A_FD^(k) I (Ah-4) */
+    int precond;               /* 0: none; 5 or 9 (2D), 7 or 27 (3D), 3 (1D): IC(ic_level) of I^T A_FD^(k) I (Ah-4);
+                                  1: the diagonal of S itself (Jacobi scaling; not in the paper, pays on graded
+                                  meshes where the diagonal spans orders of magnitude)                               */
     int ic_level;              /* level of fill of the incomplete Cholesky factor (paper: 1)                        */
     int64_t filon_M;           /* finest Filon panel count M; 0 = paper default (2^14 in 1D/2D, 2^11 in 3D), raised
                                   so that the coarsest Richardson level keeps M/2^(levels-1) >= n                      */
@@ -320,6 +322,15 @@ gofd_status gofd_export_vertex_data(const gofd_problem* p, int32_t* interior_ind
  */
 gofd_status gofd_export_precond(const gofd_problem* p, int32_t* perm, int32_t* lptr, int32_t* lcol,
                                 double* lval);
+
+/*
+ * gofd_export_diagonal -- the diagonal of S over the interior unknowns
+ * (n_interior doubles, host), S_jj = sum over the grid nodes k, m of the
+ * support of phi_j of phi_j(x_k) T_{|k-m|} phi_j(x_m) (products in FP32, sums
+ * in FP64).  Available when the problem was built with precond = 1
+ * (GOFD_E_ARG otherwise).  Not in the paper.
+ */
+gofd_status gofd_export_diagonal(const gofd_problem* p, double* diag);
 
 /* gofd_get_coefficients -- T_p for p in [0,n)^d (FP64, axis 0 fastest), to host. */
 gofd_status gofd_get_coefficients(const gofd_problem* p, double* T);

@@ -24,6 +24,8 @@ Parity status of each function (what pins it is in ``tests/test_oracle_*.py``):
                                         unit-ball closed form (exam-2), f=1 identity)
   ic1 factor / pcg                     pinned (complete pattern = exact Cholesky,
                                         L L^T = A on the kept pattern)
+  jacobi_diagonal                      pinned (the diagonal of S assembled column by
+                                        column from the stiffness product)
 """
 from __future__ import annotations
 
@@ -912,6 +914,42 @@ def pcg_ic(prob: Problem, b: np.ndarray, pattern: int = 9, tol: float = 1e-10, m
     x, info = solve(prob, b, tol, maxit=maxit, precond=precond)
     info["ic_shift"] = shift
     return x, info
+
+
+def jacobi_diagonal(prob: Problem) -> np.ndarray:
+    """Diagonal of S over the interior vertices (not in the paper; the scaling
+    behind the library's diagonal preconditioner):
+    S_jj = sum_{k,m} phi_j(x_k) T(|k-m|) phi_j(x_m) over the grid nodes of the
+    support of phi_j, T taken at the per-axis distances, written out row by row."""
+    I = prob.I.tocsc()
+    n = prob.n
+    d = prob.d
+    out = np.empty(len(prob.interior))
+    for r, j in enumerate(prob.interior):
+        nodes = I.indices[I.indptr[j]:I.indptr[j + 1]]
+        w = I.data[I.indptr[j]:I.indptr[j + 1]]
+        coords = []
+        rem = nodes.copy()
+        for ax in range(d):
+            coords.append(rem % n[ax])
+            rem = rem // n[ax]
+        # T is indexed (k_{d-1}, ..., k_0)
+        idx = tuple(np.abs(coords[ax][:, None] - coords[ax][None, :]) for ax in reversed(range(d)))
+        out[r] = w @ prob.T[idx] @ w
+    return out
+
+
+def pcg_jacobi(prob: Problem, b: np.ndarray, tol: float = 1e-10, maxit=100000):
+    """PCG on (GoFD-2) scaled by the diagonal of S (jacobi_diagonal)."""
+    ii = prob.interior
+    dinv = 1.0 / jacobi_diagonal(prob)
+
+    def precond(r):
+        out = np.zeros_like(r)
+        out[ii] = r[ii] * dinv
+        return out
+
+    return solve(prob, b, tol, maxit=maxit, precond=precond)
 
 
 # ============================================================================

@@ -68,6 +68,7 @@ EXPORTS = {
     "gofd_export_vertex_data": (C.c_int, [_P, _P, _P]),
     "gofd_get_coefficients": (C.c_int, [_P, _P]),
     "gofd_export_precond": (C.c_int, [_P, _P, _P, _P, _P]),
+    "gofd_export_diagonal": (C.c_int, [_P, _P]),
     "gofd_get_symbol": (C.c_int, [_P, _P]),
     "gofd_afd_apply": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "gofd_afd_apply_noalloc": (C.c_int, [C.c_int, C.c_int, _P, _P, _P, _P]),

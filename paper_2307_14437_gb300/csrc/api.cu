@@ -353,6 +353,11 @@ gofd_status gofd_export_precond(const gofd_problem* p, int32_t* perm, int32_t* l
     GOFD_API_BODY(q, { gofd::precond_export(p, perm, lptr, lcol, lval); })
 }
 
+gofd_status gofd_export_diagonal(const gofd_problem* p, double* diag) {
+    if (!p || !diag) return GOFD_E_ARG;
+    GOFD_API_BODY(const_cast<gofd_problem*>(p), { gofd::precond_diagonal(p, diag); })
+}
+
 gofd_status gofd_get_coefficients(const gofd_problem* p, double* T) {
     if (!p || !T) return GOFD_E_ARG;
     gofd_problem* q = const_cast<gofd_problem*>(p);

@@ -298,6 +298,7 @@ int64_t precond_nnz(const gofd_problem* p);
 double precond_shift(const gofd_problem* p);
 int precond_levels(const gofd_problem* p);
 void precond_export(const gofd_problem* p, int32_t* perm, int32_t* lptr, int32_t* lcol, double* lval);
+void precond_diagonal(const gofd_problem* p, double* diag);
 // z = M^{-1} r on interior vectors (length nint); fp64 selects the precision
 void precond_apply(gofd_problem* p, bool fp64, const void* r, void* z, cudaStream_t st);
 

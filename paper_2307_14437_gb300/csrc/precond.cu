@@ -38,7 +38,11 @@ struct Precond {
     DevBuf level_ptr, level_rows;        // rows grouped by level
     std::vector<int> hlevel_ptr;         // host copy
     DevBuf tmp64a, tmp64b, tmp32a, tmp32b;   // apply work vectors
+    DevBuf diag, dinv64, dinv32;         // pattern 1 (diagonal of S): the diagonal and its inverse
 };
+
+void setup_jacobi(gofd_problem* p, DevBuf& diag, DevBuf& dinv64, DevBuf& dinv32);
+void jacobi_apply(const gofd_problem* p, bool fp64, const void* dinv, const void* r, void* z, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // per-thread open-addressing accumulator (keys = column, values = sum)
@@ -504,10 +508,19 @@ static int64_t sum_counts(DevBuf& cnt, DevBuf& ptr, int64_t n, cudaStream_t st) 
 void setup_precond(gofd_problem* p) {
     const int pattern = p->opt.precond;
     if (pattern == 0) return;
+    if (pattern == 1) {   // the diagonal of S (jacobi.cu)
+        Precond* pc = new Precond();
+        p->pc = pc;
+        pc->pattern = 1;
+        pc->n = p->nint;
+        pc->nnz = p->nint;
+        setup_jacobi(p, pc->diag, pc->dinv64, pc->dinv32);
+        return;
+    }
     const int d = p->d;
     const bool ok = (d == 1 && pattern == 3) || (d == 2 && (pattern == 5 || pattern == 9)) ||
                     (d == 3 && (pattern == 7 || pattern == 27));
-    if (!ok) fail(GOFD_E_ARG, "preconditioner pattern must be 3 (1D), 5 or 9 (2D), 7 or 27 (3D)");
+    if (!ok) fail(GOFD_E_ARG, "preconditioner must be 1 (diagonal), or IC on 3 (1D), 5 or 9 (2D), 7 or 27 (3D)");
     if (p->opt.ic_level != 0 && p->opt.ic_level != 1) fail(GOFD_E_ARG, "only ic_level 1 is supported");
     cudaStream_t st = p->setup_stream;
     const int T = 256;
@@ -777,6 +790,10 @@ static void apply_t(gofd_problem* p, const V* r, V* z, V* t1, V* t2, cudaStream_
 void precond_apply(gofd_problem* p, bool fp64, const void* r, void* z, cudaStream_t st) {
     Precond* pc = p->pc;
     if (!pc) fail(GOFD_E_ARG, "no preconditioner");
+    if (pc->pattern == 1) {
+        jacobi_apply(p, fp64, fp64 ? pc->dinv64.ptr : pc->dinv32.ptr, r, z, st);
+        return;
+    }
     if (fp64) {
         apply_t<double>(p, (const double*)r, (double*)z, pc->tmp64a.as<double>(), pc->tmp64b.as<double>(), st);
     } else {
@@ -788,6 +805,7 @@ void precond_apply(gofd_problem* p, bool fp64, const void* r, void* z, cudaStrea
 void precond_export(const gofd_problem* p, int32_t* perm, int32_t* lptr, int32_t* lcol, double* lval) {
     const Precond* pc = p->pc;
     if (!pc) fail(GOFD_E_ARG, "no preconditioner");
+    if (pc->pattern == 1) fail(GOFD_E_ARG, "the diagonal preconditioner has no factor (gofd_export_diagonal)");
     const int32_t n = (int32_t)pc->n;
     if (perm) {
         if (pc->ordering == 1) GOFD_CUDA_TRY(cudaMemcpy(perm, pc->perm.ptr, 4 * n, cudaMemcpyDeviceToHost));
@@ -797,6 +815,13 @@ void precond_export(const gofd_problem* p, int32_t* perm, int32_t* lptr, int32_t
     if (lptr) GOFD_CUDA_TRY(cudaMemcpy(lptr, pc->lptr.ptr, 4 * (n + 1), cudaMemcpyDeviceToHost));
     if (lcol) GOFD_CUDA_TRY(cudaMemcpy(lcol, pc->lcol.ptr, 4 * pc->nnz, cudaMemcpyDeviceToHost));
     if (lval) GOFD_CUDA_TRY(cudaMemcpy(lval, pc->lval64.ptr, 8 * pc->nnz, cudaMemcpyDeviceToHost));
+}
+
+// the diagonal of S (pattern 1) copied to host, n_interior doubles
+void precond_diagonal(const gofd_problem* p, double* diag) {
+    const Precond* pc = p->pc;
+    if (!pc || pc->pattern != 1) fail(GOFD_E_ARG, "the problem was not built with the diagonal preconditioner");
+    GOFD_CUDA_TRY(cudaMemcpy(diag, pc->diag.ptr, 8 * pc->n, cudaMemcpyDeviceToHost));
 }
 
 }  // namespace gofd

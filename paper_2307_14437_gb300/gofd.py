@@ -115,6 +115,12 @@ class Problem:
         self._check(self._lib.gofd_export_vertex_data(self._h, ii.ctypes.data, cs.ctypes.data))
         return ii, cs
 
+    def export_diagonal(self) -> np.ndarray:
+        """The diagonal of S over the interior unknowns (problems built with precond=1)."""
+        d = np.empty(self.info()["n_interior"], dtype=np.float64)
+        self._check(self._lib.gofd_export_diagonal(self._h, d.ctypes.data))
+        return d
+
     def export_precond(self):
         """(perm, lptr, lcol, lval) of the incomplete Cholesky factor (NumPy)."""
         inf = self.info()

@@ -73,3 +73,31 @@ def test_ic1_preconditioner_reduces_iterations(alpha):
     x, pc = o.pcg_ic(P, b, pattern=9, tol=1e-10)
     assert pc["rel_res"] < 1e-10
     assert pc["iters"] < plain["iters"]
+
+
+def test_jacobi_diagonal_is_the_diagonal_of_s():
+    # S assembled column by column from the stiffness product (an independent
+    # route through A_FD by FFT), against the row-by-row double sum
+    for d, v, s, n, alpha in (
+            (2,) + mg.disk_ring_mesh(rings=4, seed=mg.seed_for(1, 9)) + (13, 1.3),
+            (1,) + mg.interval_mesh(9, seed=mg.seed_for(0, 9)) + (19, 0.7)):
+        lo, hi, h = mg.grid_box(d, n)
+        ref = o.build(d, v, s, alpha, h, lo, hi, M=2 ** 9)
+        ii = ref.interior
+        want = np.empty(len(ii))
+        for r, j in enumerate(ii):
+            e = np.zeros(len(v))
+            e[j] = 1.0
+            want[r] = o.stiffness_apply(ref, e)[j]
+        got = o.jacobi_diagonal(ref)
+        assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+
+
+def test_jacobi_pcg_matches_plain_cg():
+    v, s = mg.disk_ring_mesh(rings=5, seed=mg.seed_for(1, 8))
+    lo, hi, h = mg.grid_box(2, 17)
+    ref = o.build(2, v, s, 1.1, h, lo, hi, M=2 ** 9)
+    b = o.rhs_grid(ref, np.ones(ref.n_grid))
+    x1, _ = o.solve(ref, b, tol=1e-13)
+    x2, _ = o.pcg_jacobi(ref, b, tol=1e-13)
+    assert np.linalg.norm(x1 - x2) <= 1e-10 * np.linalg.norm(x1)

@@ -479,7 +479,8 @@ def run_gofd(args):
                            "launch_shapes": {"lines_per_cta": inf["tune_lines_per_cta"],
                                              "cols_per_cta": inf["tune_cols_per_cta"],
                                              "scatter_lanes": inf["tune_scatter_lanes"],
-                                             "col_elems": inf["tune_col_elems"]}},
+                                             "col_elems": inf["tune_col_elems"],
+                                             "row_elems": inf["tune_row_elems"]}},
                 "roofline": roofline, "roofline_fp64_product": roofline_fp64, "e2e": e2e, "pcg": pcg,
                 "gpu_launches": 4 * args.steps, "clocks": clk}
         if world == 1 and not args.no_cpu and args.workload == "lshape1024":

@@ -131,7 +131,8 @@ typedef struct {
     int tune_cols_per_cta;     /*   grid lines per CTA of the row FFTs, columns per CTA of the column */
     int tune_scatter_lanes;    /*   FFTs, lanes per row of the I^T scatter,                           */
     int tune_col_elems;        /*   elements per thread of the column FFTs,                           */
-    int tune_batch_chunk;      /*   columns per sub-batch of the 2D batched product (0 = all)         */
+    int tune_batch_chunk;      /*   columns per sub-batch of the 2D batched product (0 = all),        */
+    int tune_row_elems;        /*   elements per thread of the 2D row FFTs (FP32)                     */
 } gofd_info;
 
 /*
@@ -277,9 +278,10 @@ gofd_status gofd_solve_batch(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs
 
 /*
  * gofd_autotune -- time the batched FP32 product with nb columns for each
- * launch shape (elements per thread of the column FFTs, grid lines per CTA
- * in the row FFTs, columns per CTA in the column FFTs, lanes per row in the
- * scatter; one choice at a time with the others at their best so far) and
+ * launch shape (elements per thread of the column FFTs and, in 2D, of the
+ * row FFTs, grid lines per CTA in the row FFTs, columns per CTA in the column
+ * FFTs, lanes per row in the scatter; one choice at a time with the others
+ * at their best so far) and
  * keep the fastest in the handle for all later products; with nb > 1 in 2D
  * also the number of columns per sub-batch of the batched product.  *best_ms (may be
  * NULL) receives its time per product of nb columns.  CTA shapes leave every
@@ -290,6 +292,24 @@ gofd_status gofd_solve_batch(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs
  * and drops the solvers' captured CUDA graphs.
  */
 gofd_status gofd_autotune(gofd_problem* p, int nb, void* stream, double* best_ms);
+
+/*
+ * gofd_set_launch_shapes -- set the launch shapes gofd_autotune chooses
+ * from, e.g. to reuse a tuned set on a new handle or to test one shape.
+ * Each argument is 0 (the built-in default) or one of:
+ *   lines_per_cta  1, 2, 4        grid lines per CTA of the 2D row FFTs
+ *   cols_per_cta   1, 2, 4        spectrum columns per CTA of the 2D column FFTs
+ *   scatter_lanes  4, 8, 16, 32   lanes per row of the I^T scatter
+ *   col_elems      8, 16, 32      elements per thread of the column FFTs
+ *   row_elems      8, 16          elements per thread of the 2D row FFTs
+ *   batch_chunk    >= 0           columns per sub-batch of the 2D batched product
+ * A value that does not apply to the problem's sizes or precision is
+ * replaced by the default at launch (as for tuned values).  Any other value:
+ * GOFD_E_ARG and nothing changes.  Drops the solvers' captured CUDA graphs.
+ * gofd_get_info reports the shapes in use.
+ */
+gofd_status gofd_set_launch_shapes(gofd_problem* p, int lines_per_cta, int cols_per_cta, int scatter_lanes,
+                                   int col_elems, int row_elems, int batch_chunk);
 
 /* gofd_get_info -- sizes and set-up results (host struct). */
 gofd_status gofd_get_info(const gofd_problem* p, gofd_info* info);

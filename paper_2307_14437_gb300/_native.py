@@ -44,7 +44,7 @@ class Info(C.Structure):
                 ("min_colsum", C.c_double), ("precond_nnz", C.c_int64), ("precond_levels", C.c_int), ("ic_shift", C.c_double),
                 ("t_setup_ms", C.c_double), ("tune_lines_per_cta", C.c_int), ("tune_cols_per_cta", C.c_int),
                 ("tune_scatter_lanes", C.c_int), ("tune_col_elems", C.c_int),
-                ("tune_batch_chunk", C.c_int)]
+                ("tune_batch_chunk", C.c_int), ("tune_row_elems", C.c_int)]
 
 
 _P = C.c_void_p
@@ -63,6 +63,7 @@ EXPORTS = {
     "gofd_solve_batch": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, C.c_int64, C.c_double, C.c_int, _P,
                                    _P, _P]),
     "gofd_autotune": (C.c_int, [_P, C.c_int, _P, C.POINTER(C.c_double)]),
+    "gofd_set_launch_shapes": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
     "gofd_get_info": (C.c_int, [_P, C.POINTER(Info)]),
     "gofd_export_transfer": (C.c_int, [_P, _P, _P, _P]),
     "gofd_export_vertex_data": (C.c_int, [_P, _P, _P]),

@@ -3,6 +3,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <initializer_list>
 #include <string>
 #include <vector>
 
@@ -287,6 +288,29 @@ gofd_status gofd_autotune(gofd_problem* p, int nb, void* stream, double* best_ms
     })
 }
 
+gofd_status gofd_set_launch_shapes(gofd_problem* p, int lines_per_cta, int cols_per_cta, int scatter_lanes,
+                                   int col_elems, int row_elems, int batch_chunk) {
+    if (!p) return GOFD_E_ARG;
+    GOFD_API_BODY(p, {
+        auto in = [](int v, std::initializer_list<int> ok) {
+            if (v == 0) return true;
+            for (int o : ok)
+                if (v == o) return true;
+            return false;
+        };
+        if (!in(lines_per_cta, {1, 2, 4}) || !in(cols_per_cta, {1, 2, 4}) || !in(scatter_lanes, {4, 8, 16, 32}) ||
+            !in(col_elems, {8, 16, 32}) || !in(row_elems, {8, 16}) || batch_chunk < 0)
+            gofd::fail(GOFD_E_ARG, "launch shape out of range");
+        gofd::invalidate_graphs(p);
+        p->tune_lpc = lines_per_cta;
+        p->tune_cols = cols_per_cta;
+        p->tune_tpr = scatter_lanes;
+        p->tune_cole = col_elems;
+        p->tune_rowe = row_elems;
+        p->tune_bchunk = batch_chunk;
+    })
+}
+
 gofd_status gofd_get_info(const gofd_problem* p, gofd_info* info) {
     if (!p || !info) return GOFD_E_ARG;
     std::memset(info, 0, sizeof(*info));
@@ -316,6 +340,7 @@ gofd_status gofd_get_info(const gofd_problem* p, gofd_info* info) {
     info->tune_scatter_lanes = p->tune_tpr;
     info->tune_col_elems = p->tune_cole;
     info->tune_batch_chunk = p->tune_bchunk;
+    info->tune_row_elems = p->tune_rowe;
     return GOFD_OK;
 }
 

@@ -31,6 +31,14 @@ int col_elems(int N, int tuned) {
     if (fp32 && N >= 2048) return 32;
     return ct_elems_col(N);
 }
+// row transforms: 8 or 16 elements per thread; tuned > 0 selects the other
+// one for FP32 lines of 512 to 2048 complex points
+constexpr bool row_alt(int NR) { return NR >= 512 && NR <= 2048; }
+constexpr int row_alt_elems(int NR) { return ct_elems_row(NR) == 8 ? 16 : 8; }
+int row_elems(int NR, int tuned) {
+    if (sizeof(Real) == 4 && row_alt(NR) && tuned == row_alt_elems(NR)) return tuned;
+    return ct_elems_row(NR);
+}
 int lines_per_cta(int nthr, int tuned) {
     if (tuned > 0 && (tuned & (tuned - 1)) == 0 && tuned * nthr <= 512 && tuned <= 4) return tuned;
     return std::max(1, std::min(4, 512 / nthr));
@@ -48,6 +56,11 @@ void set_attrs(int limit) {
     constexpr int ER = ct_elems_row(N / 2);
     GOFD_CUDA_TRY(cudaFuncSetAttribute(row_fwd_t_kernel<Real, 3, N / 2, ER>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
     GOFD_CUDA_TRY(cudaFuncSetAttribute(row_inv_t_kernel<Real, N / 2, ER>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    if constexpr (sizeof(Real) == 4 && row_alt(N / 2)) {
+        constexpr int EA = row_alt_elems(N / 2);
+        GOFD_CUDA_TRY(cudaFuncSetAttribute(row_fwd_t_kernel<Real, 3, N / 2, EA>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+        GOFD_CUDA_TRY(cudaFuncSetAttribute(row_inv_t_kernel<Real, N / 2, EA>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    }
     GOFD_CUDA_TRY(cudaFuncSetAttribute(col_kernel<N, 8>(), cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
     if constexpr (N >= 512)
         GOFD_CUDA_TRY(cudaFuncSetAttribute(col_kernel<N, 16>(), cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
@@ -57,11 +70,10 @@ void set_attrs(int limit) {
 
 // P = circulant length (column lines), rows use P/2; nb right-hand sides with
 // strides xs (input), ws (output grid) and the batch spectrum buffer
-template <int P, int EC>
+template <int P, int EC, int ER>
 void run_e(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, int nb, int64_t xs, int64_t ws, C* S,
            cudaStream_t st) {
     constexpr int NR = P / 2, NC = P;
-    constexpr int ER = ct_elems_row(NR);
     constexpr int tr = NR / ER, tc = NC / EC;
     const int lpc = lines_per_cta(tr, p->tune_lpc), G = cols_per_cta(tc, p->tune_cols);
     const int n = p->n[0], H = P / 2 + 1, nlines = (int)p->nlines;
@@ -83,15 +95,25 @@ void run_e(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, int n
     mark_stage(st, "row_ifft");
 }
 
+template <int P, int EC>
+void run_r(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, int nb, int64_t xs, int64_t ws, C* S,
+           cudaStream_t st) {
+    constexpr int ER = ct_elems_row(P / 2);
+    if constexpr (sizeof(Real) == 4 && row_alt(P / 2))
+        if (row_elems(P / 2, p->tune_rowe) != ER)
+            return run_e<P, EC, row_alt_elems(P / 2)>(p, x, vgrid, wgrid, nb, xs, ws, S, st);
+    run_e<P, EC, ER>(p, x, vgrid, wgrid, nb, xs, ws, S, st);
+}
+
 template <int P>
 void run(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, int nb, int64_t xs, int64_t ws, C* S,
          cudaStream_t st) {
     const int e = col_elems(P, p->tune_cole);
     if constexpr (P >= 1024 && sizeof(Real) == 4)
-        if (e == 32) return run_e<P, 32>(p, x, vgrid, wgrid, nb, xs, ws, S, st);
+        if (e == 32) return run_r<P, 32>(p, x, vgrid, wgrid, nb, xs, ws, S, st);
     if constexpr (P >= 512)
-        if (e == 16) return run_e<P, 16>(p, x, vgrid, wgrid, nb, xs, ws, S, st);
-    run_e<P, 8>(p, x, vgrid, wgrid, nb, xs, ws, S, st);
+        if (e == 16) return run_r<P, 16>(p, x, vgrid, wgrid, nb, xs, ws, S, st);
+    run_r<P, 8>(p, x, vgrid, wgrid, nb, xs, ws, S, st);
 }
 
 }  // namespace

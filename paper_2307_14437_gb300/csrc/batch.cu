@@ -101,6 +101,7 @@ __device__ __forceinline__ double bdot_local(const V* a, const V* b, int64_t n) 
 template <class V>
 __global__ void bdot_kernel(const V* __restrict__ A, const V* __restrict__ B, int64_t n, int64_t ld, double* red,
                             unsigned* cnt, BScal* s, int mode) {
+    pdl_enter();
     __shared__ double sh[32];
     const V* a = A + blockIdx.y * ld;
     const V* b = B + blockIdx.y * ld;
@@ -129,6 +130,7 @@ template <class V>
 __global__ void bupdate_kernel(V* __restrict__ X, V* __restrict__ R, const V* __restrict__ Pp,
                                const V* __restrict__ Q, int64_t n, int64_t ld, double* red, unsigned* cnt, BScal* s,
                                int has_pc) {
+    pdl_enter();
     __shared__ double sh[32];
     const double a = s[blockIdx.y].alpha;
     V* x = X + blockIdx.y * ld;
@@ -158,6 +160,7 @@ __global__ void bupdate_kernel(V* __restrict__ X, V* __restrict__ R, const V* __
 template <class V>
 __global__ void bupdate_p_kernel(V* __restrict__ Pp, const V* __restrict__ Z, int64_t n, int64_t ld,
                                  const BScal* s) {
+    pdl_enter();
     const double b = s[blockIdx.y].beta;
     V* p = Pp + blockIdx.y * ld;
     const V* z = Z + blockIdx.y * ld;
@@ -318,13 +321,13 @@ static int bpcg(gofd_problem* p, BatchWork* w, int nb, V* D, V* R, V* Pd, V* Q, 
     int it = 0;
     auto iteration = [&]() {
         apply_interior_batch(p, f64, Pd, Q, nb, ld, w->grid.ptr, w->spec.ptr, w->partial.ptr, w->counters.ptr, st);
-        bdot_kernel<V><<<rg, BRED_THREADS, 0, st>>>(Pd, Q, n, ld, red, cnt, s, 2);
-        bupdate_kernel<V><<<rg, BRED_THREADS, 0, st>>>(D, R, Pd, Q, n, ld, red, cnt, s, pc ? 1 : 0);
+        launch_pdl(bdot_kernel<V>, rg, dim3(BRED_THREADS), 0, st, Pd, Q, n, ld, red, cnt, s, 2);
+        launch_pdl(bupdate_kernel<V>, rg, dim3(BRED_THREADS), 0, st, D, R, Pd, Q, n, ld, red, cnt, s, pc ? 1 : 0);
         if (pc) {
             for (int c = 0; c < nb; ++c) precond_apply(p, f64, R + c * ld, Z + c * ld, st);
-            bdot_kernel<V><<<rg, BRED_THREADS, 0, st>>>(R, Z, n, ld, red, cnt, s, 1);
+            launch_pdl(bdot_kernel<V>, rg, dim3(BRED_THREADS), 0, st, R, Z, n, ld, red, cnt, s, 1);
         }
-        bupdate_p_kernel<V><<<vg, 256, 0, st>>>(Pd, ZZ, n, ld, s);
+        launch_pdl(bupdate_p_kernel<V>, vg, dim3(256), 0, st, Pd, ZZ, n, ld, s);
         GOFD_CHECK_LAUNCH();
     };
     const int gi = f64 ? 1 : 0;
@@ -495,9 +498,10 @@ double autotune(gofd_problem* p, int nb, cudaStream_t st) {
     cudaEvent_t a, b;
     GOFD_CUDA_TRY(cudaEventCreate(&a));
     GOFD_CUDA_TRY(cudaEventCreate(&b));
-    // coordinate descent over the four choices (each swept with the others
-    // at their current best): column elements per thread, lines per CTA of
-    // the row transforms, columns per CTA, scatter lanes per row
+    // coordinate descent over the choices (each swept with the others at
+    // their current best): column elements per thread, row elements per
+    // thread (2D), lines per CTA of the row transforms, columns per CTA,
+    // scatter lanes per row, sub-batch size (2D batches)
     auto time_current = [&]() {
         apply_interior_batch(p, false, w->p32.ptr, w->q32.ptr, nb, ld, w->grid.ptr, w->spec.ptr, w->partial.ptr,
                              w->counters.ptr, st);   // warm
@@ -515,9 +519,10 @@ double autotune(gofd_problem* p, int nb, cudaStream_t st) {
     const std::vector<int> shapes = p->d == 2 ? std::vector<int>{1, 2, 4} : std::vector<int>{0};
     const std::vector<int> elems = p->d == 1 ? std::vector<int>{0} : std::vector<int>{8, 16, 32};
     const std::vector<int> lanes = {4, 8, 16, 32};
-    p->tune_cole = p->tune_lpc = p->tune_cols = p->tune_tpr = p->tune_bchunk = 0;
+    const std::vector<int> rowe = p->d == 2 ? std::vector<int>{8, 16} : std::vector<int>{0};
+    p->tune_cole = p->tune_lpc = p->tune_cols = p->tune_tpr = p->tune_bchunk = p->tune_rowe = 0;
     double best = time_current();
-    int be = 0, bl = 0, bc = 0, bt = 0, bk = 0;
+    int be = 0, bl = 0, bc = 0, bt = 0, bk = 0, br = 0;
     auto sweep = [&](int* field, const std::vector<int>& vals, int* keep) {
         for (int v : vals) {
             *field = v;
@@ -530,6 +535,7 @@ double autotune(gofd_problem* p, int nb, cudaStream_t st) {
         *field = *keep;
     };
     sweep(&p->tune_cole, elems, &be);
+    sweep(&p->tune_rowe, rowe, &br);
     sweep(&p->tune_lpc, shapes, &bl);
     sweep(&p->tune_cols, shapes, &bc);
     sweep(&p->tune_tpr, lanes, &bt);
@@ -544,6 +550,7 @@ double autotune(gofd_problem* p, int nb, cudaStream_t st) {
     p->tune_lpc = bl;
     p->tune_cols = bc;
     p->tune_tpr = bt;
+    p->tune_rowe = br;
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     return best;

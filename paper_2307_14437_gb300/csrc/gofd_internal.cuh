@@ -236,6 +236,7 @@ struct gofd_problem {
     int midK = 0;              // 3D: planes k_x0 per chunk of the middle stage
     int tune_lpc = 0, tune_cols = 0, tune_tpr = 0;  // launch shapes picked by the autotuner (0 = default)
     int tune_cole = 0;         // elements per thread of the column transforms (0 = default)
+    int tune_rowe = 0;         // elements per thread of the 2D row transforms (0 = default)
     int tune_bchunk = 0;       // 2D batched product: columns per sub-batch (0 = all)
     gofd::DevBuf lamT64, lamT32;  // 2D/3D: scaled symbol with the axis order reversed
     gofd::DevBuf gridw;        // real [ngrid] (largest precision): A_FD v on the grid

@@ -127,6 +127,7 @@ __device__ __forceinline__ bool finish_reduction(double mine, double* partial, u
 template <class V>
 __global__ void dot_pq_kernel(const V* __restrict__ p, const V* __restrict__ q, int64_t n, double* partial,
                               unsigned* counter, Scal* s) {
+    pdl_enter();
     __shared__ double sh[32];
     double acc = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -145,6 +146,7 @@ template <class V>
 __global__ void update_xr_kernel(V* __restrict__ x, V* __restrict__ r, const V* __restrict__ p,
                                  const V* __restrict__ q, int64_t n, double* partial, unsigned* counter, Scal* s,
                                  int has_precond) {
+    pdl_enter();
     __shared__ double sh[32];
     const double a = s->alpha;
     double acc = 0;
@@ -171,6 +173,7 @@ __global__ void update_xr_kernel(V* __restrict__ x, V* __restrict__ r, const V* 
 template <class V>
 __global__ void dot_rz_kernel(const V* __restrict__ r, const V* __restrict__ z, int64_t n, double* partial,
                               unsigned* counter, Scal* s, int init) {
+    pdl_enter();
     __shared__ double sh[32];
     double acc = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -204,6 +207,7 @@ __global__ void dot_rr_kernel(const V* __restrict__ r, int64_t n, double* partia
 // p = z + beta p
 template <class V>
 __global__ void update_p_kernel(V* __restrict__ p, const V* __restrict__ z, int64_t n, const Scal* s) {
+    pdl_enter();
     const double b = s->beta;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         p[i] = (V)((double)z[i] + b * (double)p[i]);
@@ -324,13 +328,16 @@ static int pcg(gofd_problem* p, Workspace* w, V* d, V* r, V* pv, V* q, V* z, dou
     double rel = 1.0;
     auto iteration = [&]() {
         apply_interior(p, fp64, pv, q, st);
-        dot_pq_kernel<V><<<RED_BLOCKS, RED_THREADS, 0, st>>>(pv, q, n, part, cnt, s);
-        update_xr_kernel<V><<<RED_BLOCKS, RED_THREADS, 0, st>>>(d, r, pv, q, n, part, cnt, s, pc ? 1 : 0);
+        launch_pdl(dot_pq_kernel<V>, dim3(RED_BLOCKS), dim3(RED_THREADS), 0, st, (const V*)pv, (const V*)q, n,
+                   part, cnt, s);
+        launch_pdl(update_xr_kernel<V>, dim3(RED_BLOCKS), dim3(RED_THREADS), 0, st, d, r, (const V*)pv,
+                   (const V*)q, n, part, cnt, s, pc ? 1 : 0);
         if (pc) {
             precond_apply(p, fp64, r, z, st);
-            dot_rz_kernel<V><<<RED_BLOCKS, RED_THREADS, 0, st>>>(r, z, n, part, cnt, s, 0);
+            launch_pdl(dot_rz_kernel<V>, dim3(RED_BLOCKS), dim3(RED_THREADS), 0, st, (const V*)r, (const V*)z, n,
+                       part, cnt, s, 0);
         }
-        update_p_kernel<V><<<nb, 256, 0, st>>>(pv, zz, n, s);
+        launch_pdl(update_p_kernel<V>, dim3(nb), dim3(256), 0, st, pv, (const V*)zz, n, (const Scal*)s);
         GOFD_CHECK_LAUNCH();
     };
     // The iterations run as one CUDA graph: a conditional while node whose

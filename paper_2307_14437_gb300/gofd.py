@@ -236,6 +236,13 @@ class Problem:
         self._check(self._lib.gofd_autotune(self._h, int(nb), _stream_ptr(stream), C.byref(ms)))
         return ms.value
 
+    def set_launch_shapes(self, lines_per_cta: int = 0, cols_per_cta: int = 0, scatter_lanes: int = 0,
+                          col_elems: int = 0, row_elems: int = 0, batch_chunk: int = 0) -> None:
+        """Set the launch shapes the autotuner chooses from (0 = built-in default)."""
+        self._check(self._lib.gofd_set_launch_shapes(self._h, int(lines_per_cta), int(cols_per_cta),
+                                                     int(scatter_lanes), int(col_elems), int(row_elems),
+                                                     int(batch_chunk)))
+
     def adjoint(self, f, u, grad_u, mode: str = "mixed", tol: float = 1e-10, maxit: int = 100000, stream=None):
         """(dL/df, dL/dX) for the vertex-data solve u = S^{-1} h^{2s} D_h f given dL/du."""
         torch = _torch()

@@ -63,6 +63,56 @@ def test_lshape_products(lshape):
     assert _rel(y32, want) < 1e-5
 
 
+_ROWS = [(8, 1), (8, 2), (8, 4), (16, 1), (16, 2), (16, 4)]
+_COLS = [(8, 1), (8, 2), (8, 4), (16, 1), (16, 2), (16, 4), (32, 1), (32, 2), (32, 4)]
+_SHAPES = [dict(row_elems=_ROWS[i * 5 % 6][0], lines_per_cta=_ROWS[i * 5 % 6][1], col_elems=_COLS[i][0],
+                cols_per_cta=_COLS[i][1], scatter_lanes=(4, 8, 16, 32)[i % 4], batch_chunk=i % 3)
+           for i in range(9)]
+
+
+@pytest.mark.parametrize("shape", _SHAPES, ids=lambda d: "r%(row_elems)d.%(lines_per_cta)d-c%(col_elems)d.%(cols_per_cta)d"
+                         "-s%(scatter_lanes)d-b%(batch_chunk)d" % d)
+def test_lshape_products_every_launch_shape(lshape, shape):
+    # every launch shape the autotuner may choose at this size (all row and
+    # column shapes, every scatter width and sub-batch size) against the oracle;
+    # the batched product equals the single-vector products bit for bit
+    gp, ref = lshape
+    gp.set_launch_shapes(**shape)
+    try:
+        info = gp.info()
+        assert info["tune_row_elems"] == shape["row_elems"] and info["tune_col_elems"] == shape["col_elems"]
+        u = mg.random_vector(len(ref.verts), 41)
+        want = o.stiffness_apply(ref, u)
+        y32 = gp.apply(torch.tensor(u, device="cuda", dtype=torch.float32)).cpu().numpy().astype(np.float64)
+        y64 = gp.apply(torch.tensor(u, device="cuda")).cpu().numpy()
+        assert _rel(y32, want) < 1e-5
+        assert _rel(y64, want) < 1e-12
+        ii, _ = gp.export_vertex_data()
+        iv = np.nonzero(ii >= 0)[0]
+        X = np.zeros((3, len(iv) + 1))
+        for c in range(3):
+            X[c, :len(iv)] = mg.random_vector(len(ref.verts), 50 + c)[iv]
+        Xd = torch.tensor(X, device="cuda", dtype=torch.float32)
+        Yd = torch.empty_like(Xd)
+        gp.apply_interior_batch(Xd, Yd)
+        for c in range(3):
+            y1 = torch.empty(len(iv), device="cuda", dtype=torch.float32)
+            gp.apply_interior(Xd[c].contiguous(), y1)
+            assert torch.equal(Yd[c, :len(iv)], y1), c
+    finally:
+        gp.set_launch_shapes()
+
+
+def test_launch_shape_arguments_are_checked(lshape):
+    from paper_2307_14437_gb300 import GofdError
+    gp, _ = lshape
+    for bad in (dict(lines_per_cta=3), dict(cols_per_cta=8), dict(scatter_lanes=2), dict(col_elems=4),
+                dict(row_elems=32), dict(batch_chunk=-1)):
+        with pytest.raises(GofdError):
+            gp.set_launch_shapes(**bad)
+    assert gp.info()["tune_row_elems"] == 0
+
+
 @pytest.mark.parametrize("alpha", [0.5, 1.0, 1.5])
 def test_lshape_solves_reach_1e8(lshape, alpha):
     from paper_2307_14437_gb300 import Problem

@@ -132,7 +132,7 @@ typedef struct {
     int tune_scatter_lanes;    /*   FFTs, lanes per row of the I^T scatter,                           */
     int tune_col_elems;        /*   elements per thread of the column FFTs,                           */
     int tune_batch_chunk;      /*   columns per sub-batch of the 2D batched product (0 = all),        */
-    int tune_row_elems;        /*   elements per thread of the 2D row FFTs (FP32)                     */
+    int tune_row_elems;        /*   elements per thread of the 2D row / 3D axis-1 FFTs (FP32)         */
 } gofd_info;
 
 /*
@@ -278,8 +278,8 @@ gofd_status gofd_solve_batch(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs
 
 /*
  * gofd_autotune -- time the batched FP32 product with nb columns for each
- * launch shape (elements per thread of the column FFTs and, in 2D, of the
- * row FFTs, grid lines per CTA in the row FFTs, columns per CTA in the column
+ * launch shape (elements per thread of the column FFTs and of the 2D row /
+ * 3D axis-1 FFTs, grid lines per CTA in the row FFTs, columns per CTA in the column
  * FFTs, lanes per row in the scatter; one choice at a time with the others
  * at their best so far) and
  * keep the fastest in the handle for all later products; with nb > 1 in 2D
@@ -300,8 +300,8 @@ gofd_status gofd_autotune(gofd_problem* p, int nb, void* stream, double* best_ms
  *   lines_per_cta  1, 2, 4        grid lines per CTA of the 2D row FFTs
  *   cols_per_cta   1, 2, 4        spectrum columns per CTA of the 2D column FFTs
  *   scatter_lanes  4, 8, 16, 32   lanes per row of the I^T scatter
- *   col_elems      8, 16, 32      elements per thread of the column FFTs
- *   row_elems      8, 16          elements per thread of the 2D row FFTs
+ *   col_elems      8, 16, 32      elements per thread of the column (2D) / axis-2 (3D) FFTs
+ *   row_elems      8, 16          elements per thread of the 2D row / 3D axis-1 FFTs
  *   batch_chunk    >= 0           columns per sub-batch of the 2D batched product
  * A value that does not apply to the problem's sizes or precision is
  * replaced by the default at launch (as for tuned values).  Any other value:

@@ -13,9 +13,22 @@ using Real = REAL;
 using C = Cplx<Real>::T;
 
 constexpr int ct3_elems(int N) { return N >= 4096 ? 16 : 8; }
-// elements per thread of the axis-2 column transform: 8 or 16 (tuned > 0
-// selects, 0 the default 8)
-int col3_elems(int N, int tuned) { return (tuned == 16 && N >= 512) ? 16 : 8; }
+// elements per thread of the axis-2 column transform: 8, 16 or 32 (32 in FP32
+// only; tuned > 0 selects, 0 the default 8); the 32-element kernel caps its
+// registers for two CTAs of 256 threads per SM, as in 2D
+constexpr bool col3_alt(int N) { return N >= 512 && N <= 1024; }
+int col3_elems(int N, int tuned) {
+    if (!col3_alt(N)) return ct3_elems(N);
+    if (tuned == 16 || (tuned == 32 && sizeof(Real) == 4)) return tuned;
+    return 8;
+}
+template <int N, int E>
+constexpr auto col3_kernel() { return col_conv_t_kernel<Real, N, E, (N / E > 256 ? N / E : 256), E == 32 ? 2 : 1>; }
+// elements per thread of the axis-1 (plane) transforms: 8 or 16 for FP32
+// lines of 512 and 1024 (tuned row elements select)
+int plane3_elems(int N, int tuned) {
+    return (sizeof(Real) == 4 && col3_alt(N) && tuned == 16) ? 16 : ct3_elems(N);
+}
 int rows_per_cta(int nthr) { return std::max(1, std::min(4, 512 / nthr)); }
 int groups_per_cta(int nthr) { return std::max(1, std::min(4, 256 / nthr)); }
 size_t row_smem3(int N, int lpc) {
@@ -30,14 +43,20 @@ void set_attrs3(int limit) {
     GOFD_CUDA_TRY(cudaFuncSetAttribute(row_inv_t_kernel<Real, NR, ER>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
     GOFD_CUDA_TRY(cudaFuncSetAttribute(plane_fwd_t_kernel<Real, NC, EC>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
     GOFD_CUDA_TRY(cudaFuncSetAttribute(plane_inv_t_kernel<Real, NC, EC>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
-    GOFD_CUDA_TRY(cudaFuncSetAttribute(col_conv_t_kernel<Real, NC, EC>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
-    if constexpr (NC >= 512)
-        GOFD_CUDA_TRY(cudaFuncSetAttribute(col_conv_t_kernel<Real, NC, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    GOFD_CUDA_TRY(cudaFuncSetAttribute(col3_kernel<NC, EC>(), cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+    if constexpr (col3_alt(NC)) {
+        GOFD_CUDA_TRY(cudaFuncSetAttribute(col3_kernel<NC, 16>(), cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+        if constexpr (sizeof(Real) == 4) {
+            GOFD_CUDA_TRY(cudaFuncSetAttribute(col3_kernel<NC, 32>(), cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+            GOFD_CUDA_TRY(cudaFuncSetAttribute(plane_fwd_t_kernel<Real, NC, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+            GOFD_CUDA_TRY(cudaFuncSetAttribute(plane_inv_t_kernel<Real, NC, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, limit));
+        }
+    }
 }
 
-template <int P, int ECC>
+template <int P, int ECC, int EC>
 void run3_e(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, cudaStream_t st) {
-    constexpr int NR = P / 2, NC = P, ER = ct3_elems(NR), EC = ct3_elems(NC);
+    constexpr int NR = P / 2, NC = P, ER = ct3_elems(NR);
     constexpr int tr = NR / ER, tc = NC / EC, tcc = NC / ECC;
     const int lpc = rows_per_cta(tr), G = groups_per_cta(tc), GC = groups_per_cta(tcc);
     const int n = p->n[0], H = P / 2 + 1, nlines = (int)p->nlines;
@@ -60,7 +79,7 @@ void run3_e(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, cuda
         const int kc = std::min(p->midK, H - k0);
         launch_pdl(plane_fwd_t_kernel<Real, NC, EC>, dim3((unsigned)(kc * ngroups)), dim3(G * tc), mid_smem3(NC, G),
                    st, (const C*)S, ld, M, n, ngroups, k0, tw);
-        launch_pdl(col_conv_t_kernel<Real, NC, ECC>, dim3((unsigned)(((int64_t)kc * P + GC - 1) / GC)),
+        launch_pdl(col3_kernel<NC, ECC>(), dim3((unsigned)(((int64_t)kc * P + GC - 1) / GC)),
                    dim3(GC * tcc), mid_smem3(NC, GC), st, M, n, n, (int)((int64_t)kc * P), H, tw, lamT, (int64_t)0,
                    P, (int64_t)k0 * P);
         launch_pdl(plane_inv_t_kernel<Real, NC, EC>, dim3((unsigned)(kc * ngroups)), dim3(G * tc), mid_smem3(NC, G),
@@ -72,11 +91,22 @@ void run3_e(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, cuda
     mark_stage(st, "row_ifft");
 }
 
+template <int P, int ECC>
+void run3_p(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, cudaStream_t st) {
+    if constexpr (sizeof(Real) == 4 && col3_alt(P))
+        if (plane3_elems(P, p->tune_rowe) == 16) return run3_e<P, ECC, 16>(p, x, vgrid, wgrid, st);
+    run3_e<P, ECC, ct3_elems(P)>(p, x, vgrid, wgrid, st);
+}
+
 template <int P>
 void run3(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, cudaStream_t st) {
-    if constexpr (P >= 512)
-        if (col3_elems(P, p->tune_cole) == 16) return run3_e<P, 16>(p, x, vgrid, wgrid, st);
-    run3_e<P, ct3_elems(P)>(p, x, vgrid, wgrid, st);
+    if constexpr (col3_alt(P)) {
+        const int e = col3_elems(P, p->tune_cole);
+        if constexpr (sizeof(Real) == 4)
+            if (e == 32) return run3_p<P, 32>(p, x, vgrid, wgrid, st);
+        if (e == 16) return run3_p<P, 16>(p, x, vgrid, wgrid, st);
+    }
+    run3_p<P, ct3_elems(P)>(p, x, vgrid, wgrid, st);
 }
 
 }  // namespace
@@ -100,8 +130,11 @@ void AFD3D_ATTR_FN(int limit, int P, size_t* need) {
 #undef ATTR
         default: fail(GOFD_E_GRID, "3D circulant length beyond 1024 (n > 513) is not supported");
     }
-    const int tr = P / 2 / ct3_elems(P / 2), tc = P / ct3_elems(P);
-    *need = std::max(row_smem3(P / 2, rows_per_cta(tr)), mid_smem3(P, groups_per_cta(tc)));
+    const int tr = P / 2 / ct3_elems(P / 2);
+    size_t nd = row_smem3(P / 2, rows_per_cta(tr));
+    for (int e : {8, 16, 32})   // every middle-stage shape the tuner may pick
+        if (P / e >= 1) nd = std::max(nd, mid_smem3(P, groups_per_cta(P / e)));
+    *need = nd;
 }
 
 }  // namespace gofd

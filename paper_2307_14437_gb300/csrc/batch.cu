@@ -519,7 +519,7 @@ double autotune(gofd_problem* p, int nb, cudaStream_t st) {
     const std::vector<int> shapes = p->d == 2 ? std::vector<int>{1, 2, 4} : std::vector<int>{0};
     const std::vector<int> elems = p->d == 1 ? std::vector<int>{0} : std::vector<int>{8, 16, 32};
     const std::vector<int> lanes = {4, 8, 16, 32};
-    const std::vector<int> rowe = p->d == 2 ? std::vector<int>{8, 16} : std::vector<int>{0};
+    const std::vector<int> rowe = p->d >= 2 ? std::vector<int>{8, 16} : std::vector<int>{0};
     p->tune_cole = p->tune_lpc = p->tune_cols = p->tune_tpr = p->tune_bchunk = p->tune_rowe = 0;
     double best = time_current();
     int be = 0, bl = 0, bc = 0, bt = 0, bk = 0, br = 0;

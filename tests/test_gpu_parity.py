@@ -318,6 +318,38 @@ def test_3d_afd_ragged_129():
     gp.close()
 
 
+@pytest.fixture(scope="module")
+def afd256():
+    # n = 256 (P = 512): the size at which the axis-1/axis-2 kernels have
+    # alternative launch shapes; one oracle product serves every shape
+    import os
+    v, s = mg.ball_shell_mesh(shells=6, seed=mg.seed_for(3, 4))
+    lo, hi, h = mg.grid_box(3, 256)
+    gp = _gpu(v, s, 1.5, h, lo, hi)
+    T = gp.coefficients().reshape((256,) * 3)
+    lam = o.symbol(T, 512)
+    x = mg.random_vector(256 ** 3, 53)
+    want = o.afd_apply_fft(lam, x.reshape((256,) * 3), 512, workers=os.cpu_count()).ravel()
+    yield gp, x, want
+    gp.close()
+
+
+@pytest.mark.parametrize("col_elems,row_elems", [(8, 8), (16, 8), (32, 8), (8, 16), (16, 16), (32, 16)])
+def test_3d_afd_every_middle_shape(afd256, col_elems, row_elems):
+    # axis-2 columns with 8/16/32 elements per thread (32 in FP32 only) and
+    # axis-1 planes with 8/16, against the oracle's FFT convolution
+    gp, x, want = afd256
+    gp.set_launch_shapes(col_elems=col_elems, row_elems=row_elems)
+    try:
+        xd = torch.tensor(x, device="cuda")
+        got64 = gp.afd_apply(xd).cpu().numpy()
+        got32 = gp.afd_apply(xd.float()).cpu().numpy().astype(np.float64)
+        assert _rel(got64, want) < 1e-12
+        assert _rel(got32, want) < 1e-5
+    finally:
+        gp.set_launch_shapes()
+
+
 def test_3d_products_do_not_depend_on_plane_chunks(built):
     # the axis-1/axis-2 stage over chunks of 5 planes (13 chunks at P = 128)
     # gives the same products, bit for bit, as over all planes at once

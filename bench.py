@@ -70,17 +70,19 @@ BATCH_METRIC = "batched block-PCG: right-hand sides solved to rel-res 1e-8 per s
 BATCH_RHS = 8
 
 
-def workload(name="lshape1024", alpha=None):
+def workload(name="lshape1024", alpha=None, grid=0):
+    """Mesh, alpha and overlay grid of a workload; grid > 0 replaces its grid
+    size (a smaller case of the same kernels, for profiling captures)."""
     if name == "graded2048":
-        lo, hi, h = mg.grid_box(2, 2048)
-        v, s = mg.graded_disk_mesh(h, seed=mg.seed_for(4))
+        lo, hi, h = mg.grid_box(2, grid or 2048)
+        v, s = mg.graded_disk_mesh(mg.grid_box(2, 2048)[2], seed=mg.seed_for(4))
         return v, s, 1.2 if alpha is None else alpha, h, lo, hi
     if name == "ball256":
         v, s = mg.ball_shell_mesh(seed=mg.seed_for(3))
-        lo, hi, h = mg.grid_box(3, 256)
+        lo, hi, h = mg.grid_box(3, grid or 256)
         return v, s, 1.5 if alpha is None else alpha, h, lo, hi
     v, s = mg.lshape_mesh(seed=mg.seed_for(2))
-    lo, hi, h = mg.grid_box(2, N_GRID)
+    lo, hi, h = mg.grid_box(2, grid or N_GRID)
     return v, s, 1.0 if alpha is None else alpha, h, lo, hi
 
 
@@ -212,12 +214,15 @@ def run_gofd(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    v, s, alpha, h, lo, hi = workload(args.workload)
+    v, s, alpha, h, lo, hi = workload(args.workload, grid=args.grid)
     t0 = time.perf_counter()
     prob = Problem(v, s, alpha, h, lo, hi)
     t_setup = time.perf_counter() - t0
     t0 = time.perf_counter()
-    prob.autotune(nb=1)                      # launch shapes of the product (part of the set-up)
+    if args.shapes:                          # launch shapes given: no tuning (profiling captures)
+        prob.set_launch_shapes(*[int(a) for a in args.shapes.split(",")])
+    else:
+        prob.autotune(nb=1)                  # launch shapes of the product (part of the set-up)
     t_tune = time.perf_counter() - t0
     inf = prob.info()
     d, n_loc, n_v, nint, P = inf["d"], inf["n_loc"], inf["n_v"], inf["n_interior"], inf["P"]
@@ -473,7 +478,7 @@ def run_gofd(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic (seeded jittered L-shape Delaunay mesh, uniform random x)",
                 "config": {"workload": WORKLOADS[args.workload] + ", FP32 stiffness product (%d vertices, %d interior)"
-                                       % (n_v, nint),
+                                       % (n_v, nint) + (", grid replaced by %d^%d" % (args.grid, d) if args.grid else ""),
                            "l2": "flushed (256 MB write) before every timed step",
                            "n_loc": n_loc, "setup_s": round(t_setup, 3), "autotune_s": round(t_tune, 3),
                            "launch_shapes": {"lines_per_cta": inf["tune_lines_per_cta"],
@@ -660,6 +665,10 @@ def main():
     ap.add_argument("--no-pcg", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="lshape1024", choices=sorted(WORKLOADS))
+    ap.add_argument("--grid", type=int, default=0,
+                    help="replace the workload's grid size (a smaller case for profiling; not a bench line)")
+    ap.add_argument("--shapes", default="",
+                    help="launch shapes lines,cols,lanes,col_elems,row_elems,batch_chunk instead of autotuning")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

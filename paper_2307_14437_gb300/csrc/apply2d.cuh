@@ -290,19 +290,20 @@ __global__ void __launch_bounds__(MAXT, MINB) row_fwd_t_kernel(
         }
     }
     __syncthreads();
-    // transposed tile: element (k, line g) at k*lpc + (g ^ (k & (lpc-1)))
+    // transposed tile: element (k, line g) at g*LS + k, LS = tile_ld(N+1, lpc)
     const int msk = lpc - 1, lsh = __ffs(lpc) - 1;   // lpc is a power of two
+    const int LS = tile_ld(N + 1, lpc);
 #pragma unroll
     for (int j = 0; j < JMAX; ++j) {
         const int k = t + j * nthr;
-        if (k <= N) sm[k * lpc + (g ^ (k & msk))] = X[j];
+        if (k <= N) sm[g * LS + k] = X[j];
     }
     __syncthreads();
     const int total = (N + 1) * lpc;
     for (int i = threadIdx.x; i < total; i += blockDim.x) {
         const int k = i >> lsh, l = i & msk;
         const int ln = blockIdx.x * lpc + l;
-        if (ln < nlines) specT[(int64_t)k * ld + ln] = sm[k * lpc + (l ^ (k & msk))];
+        if (ln < nlines) specT[(int64_t)k * ld + ln] = sm[l * LS + k];
     }
 }
 
@@ -374,11 +375,12 @@ __global__ void __launch_bounds__(MAXT, MINB) row_inv_t_kernel(const typename Cp
     C* sm = reinterpret_cast<C*>(smem_raw);
     constexpr int nthr = N / E;
     const int msk = lpc - 1, lsh = __ffs(lpc) - 1;   // lpc is a power of two
+    const int LS = tile_ld(N + 1, lpc);                // tile: (k, line l) at l*LS + k
     const int total = (N + 1) * lpc;
     for (int i = threadIdx.x; i < total; i += blockDim.x) {
         const int k = i >> lsh, l = i & msk;
         const int ln = blockIdx.x * lpc + l;
-        sm[k * lpc + (l ^ (k & msk))] = (ln < nlines) ? specT[(int64_t)k * ld + ln] : cmk<C>(0.0, 0.0);
+        sm[l * LS + k] = (ln < nlines) ? specT[(int64_t)k * ld + ln] : cmk<C>(0.0, 0.0);
     }
     __syncthreads();
     const int g = threadIdx.x / nthr, t = threadIdx.x % nthr;
@@ -388,8 +390,8 @@ __global__ void __launch_bounds__(MAXT, MINB) row_inv_t_kernel(const typename Cp
     // Z'_k = (X_k + conj X_{N-k}) + i W_P^{-k} (X_k - conj X_{N-k})
     each_elem_r<ct_radix_o(N, E, false, 0), E>(t, nthr, N, [&](int i, int k) {
         const int kc = N - k;
-        const C xk = sm[k * lpc + (g ^ (k & msk))];
-        const C xc = cconj(sm[kc * lpc + (g ^ (kc & msk))]);
+        const C xk = sm[g * LS + k];
+        const C xc = cconj(sm[g * LS + kc]);
         const C e = cadd(xk, xc);
         const C o = cmulc(csub(xk, xc), __ldg(&tw[k]));
         C z;

@@ -48,7 +48,9 @@ int cols_per_cta(int nthr, int tuned) {
     if (tuned > 0 && (tuned & (tuned - 1)) == 0 && tuned * nthr <= std::max(nthr, 256) && tuned <= 4) return tuned;
     return std::max(1, std::min(4, 256 / nthr));
 }
-size_t row_smem(int N, int lpc) { return sizeof(C) * std::max<size_t>((size_t)spad_len(N) * lpc, (size_t)(N + 1) * lpc); }
+size_t row_smem(int N, int lpc) {
+    return sizeof(C) * std::max<size_t>((size_t)spad_len(N) * lpc, (size_t)tile_ld(N + 1, lpc) * lpc);
+}
 size_t col_smem(int N, int G) { return sizeof(C) * (size_t)spad_len(N) * G; }
 
 template <int N>

@@ -44,12 +44,13 @@ __global__ void __launch_bounds__(N / E > 256 ? N / E : 256) plane_fwd_t_kernel(
     });
     fft_ct<false, N, E, false>(v, sm + g * spad_len(N), t, g, tw, 1);
     __syncthreads();   // the tile reuses the line buffers
-    each_elem_r<ct_last<N, E, false>(), E>(t, nthr, N, [&](int i, int pos) { sm[pos * G + (g ^ (pos & msk))] = v[i]; });
+    const int LS = tile_ld(N, G);   // tile: (pos, line l) at l*LS + pos
+    each_elem_r<ct_last<N, E, false>(), E>(t, nthr, N, [&](int i, int pos) { sm[g * LS + pos] = v[i]; });
     __syncthreads();
     C* out = M + (int64_t)kl * N * n;   // plane kl of the chunk
     for (int i = threadIdx.x; i < N * G; i += blockDim.x) {
         const int pos = i >> gsh, l = i & msk;
-        if (k20 + l < n) out[(int64_t)pos * n + k20 + l] = sm[pos * G + (l ^ (pos & msk))];
+        if (k20 + l < n) out[(int64_t)pos * n + k20 + l] = sm[l * LS + pos];
     }
 }
 
@@ -65,15 +66,16 @@ __global__ void __launch_bounds__(N / E > 256 ? N / E : 256) plane_inv_t_kernel(
     const int G = blockDim.x / nthr, msk = G - 1, gsh = __ffs(G) - 1;   // G is a power of two
     const int kl = blockIdx.x / ngroups, kx = kx0 + kl, k20 = (blockIdx.x % ngroups) * G;
     const C* in = M + (int64_t)kl * N * n;
+    const int LS = tile_ld(N, G);   // tile: (pos, line l) at l*LS + pos
     for (int i = threadIdx.x; i < N * G; i += blockDim.x) {
         const int pos = i >> gsh, l = i & msk;
-        sm[pos * G + (l ^ (pos & msk))] = (k20 + l < n) ? in[(int64_t)pos * n + k20 + l] : cmk<C>(0.0, 0.0);
+        sm[l * LS + pos] = (k20 + l < n) ? in[(int64_t)pos * n + k20 + l] : cmk<C>(0.0, 0.0);
     }
     __syncthreads();
     const int g = threadIdx.x / nthr, t = threadIdx.x % nthr;
     const int k2 = k20 + g;
     C v[E];
-    each_elem_r<ct_radix_o(N, E, false, 0), E>(t, nthr, N, [&](int i, int pos) { v[i] = sm[pos * G + (g ^ (pos & msk))]; });
+    each_elem_r<ct_radix_o(N, E, false, 0), E>(t, nthr, N, [&](int i, int pos) { v[i] = sm[g * LS + pos]; });
     __syncthreads();   // the line buffers reuse the tile
     fft_ct<true, N, E, false>(v, sm + g * spad_len(N), t, g, tw, 1);
     if (k2 >= n) return;

@@ -32,9 +32,9 @@ int plane3_elems(int N, int tuned) {
 int rows_per_cta(int nthr) { return std::max(1, std::min(4, 512 / nthr)); }
 int groups_per_cta(int nthr) { return std::max(1, std::min(4, 256 / nthr)); }
 size_t row_smem3(int N, int lpc) {
-    return sizeof(C) * std::max<size_t>((size_t)spad_len(N) * lpc, (size_t)(N + 1) * lpc);
+    return sizeof(C) * std::max<size_t>((size_t)spad_len(N) * lpc, (size_t)tile_ld(N + 1, lpc) * lpc);
 }
-size_t mid_smem3(int N, int G) { return sizeof(C) * std::max<size_t>((size_t)spad_len(N) * G, (size_t)N * G); }
+size_t mid_smem3(int N, int G) { return sizeof(C) * std::max<size_t>((size_t)spad_len(N) * G, (size_t)tile_ld(N, G) * G); }
 
 template <int P>
 void set_attrs3(int limit) {

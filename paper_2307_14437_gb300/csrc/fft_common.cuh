@@ -38,6 +38,14 @@ template <class C> __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return 
 __device__ __forceinline__ int spad(int i) { return i + (i >> 4); }
 __host__ __device__ constexpr int spad_len(int n) { return n + (n >> 4) + 1; }
 
+// Row stride of a shared-memory tile holding G lines (G = 1, 2, 4) of len
+// complex entries, line after line: len rounded up to 16/G modulo 16.  Then
+// both ways the tile is accessed are free of bank conflicts for 8-byte
+// entries: one line's consecutive entries, and the tile order in which
+// consecutive threads take the G lines' entries of consecutive positions
+// (16 threads cover 16/G positions x G lines = 16 distinct slots mod 16).
+__host__ __device__ constexpr int tile_ld(int len, int G) { return len + ((((16 / G) & 15) - (len & 15)) & 15); }
+
 // cos / sin of 2 pi k / 16
 __host__ __device__ constexpr double cos16(int k) {
     switch (k & 15) {

@@ -43,10 +43,14 @@ int lines_per_cta(int nthr, int tuned) {
     if (tuned > 0 && (tuned & (tuned - 1)) == 0 && tuned * nthr <= 512 && tuned <= 4) return tuned;
     return std::max(1, std::min(4, 512 / nthr));
 }
-// the column kernel is compiled for at most max(N/E, 256) threads per CTA
+// the column kernel is compiled for at most max(N/E, 256) threads per CTA;
+// by default a CTA takes one column (two or four when a column has fewer
+// than 64 threads): with about a thousand columns this spreads them evenly
+// over the SMs (at 2048 x 1025, four columns per CTA leave 257 CTAs for 152
+// SMs and cost 5 us of a 61 us product)
 int cols_per_cta(int nthr, int tuned) {
     if (tuned > 0 && (tuned & (tuned - 1)) == 0 && tuned * nthr <= std::max(nthr, 256) && tuned <= 4) return tuned;
-    return std::max(1, std::min(4, 256 / nthr));
+    return std::max(1, std::min(4, 64 / nthr));
 }
 size_t row_smem(int N, int lpc) {
     return sizeof(C) * std::max<size_t>((size_t)spad_len(N) * lpc, (size_t)tile_ld(N + 1, lpc) * lpc);

@@ -64,7 +64,7 @@ WORKLOADS = {
 # dram__bytes_write.sum) from one `ncu --set full` capture of the current
 # kernels; profiles/product_kernels_lshape1024_fp32.md gives the command.
 NCU_DRAM_BYTES = {
-    "lshape1024": {"gather_row_fft": 19201024, "col_fft_conv": 12678400, "row_ifft": 8425984, "scatter": 22080000},
+    "lshape1024": {"gather_row_fft": 19200256, "col_fft_conv": 12679936, "row_ifft": 8424192, "scatter": 22079744},
 }
 BATCH_METRIC = "batched block-PCG: right-hand sides solved to rel-res 1e-8 per second (mixed), 1 GB300"
 BATCH_RHS = 8

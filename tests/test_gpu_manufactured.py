@@ -18,13 +18,13 @@ import math
 import numpy as np
 import pytest
 
+import manufactured
 import meshgen as mg
 from oracle import gofd as o
 
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
-special = pytest.importorskip("scipy.special")
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -35,19 +35,8 @@ def _lib():
     build_native.build()
 
 
-def _jacobi(k, s, d, r2):
-    return special.eval_jacobi(k, s, d / 2.0 - 1.0, 2.0 * r2 - 1.0)
-
-
-def _rhs(k, s, d, x):
-    r2 = np.sum(x * x, axis=1)
-    c = 2.0 ** (2 * s) * math.gamma(1 + s + k) * math.gamma(d / 2 + s + k) / (math.factorial(k) * math.gamma(d / 2 + k))
-    return c * _jacobi(k, s, d, r2)
-
-
-def _exact(k, s, d, x):
-    r2 = np.sum(x * x, axis=1)
-    return np.maximum(0.0, 1.0 - r2) ** s * _jacobi(k, s, d, r2)
+_rhs = manufactured.rhs
+_exact = manufactured.exact
 
 
 def _error(rings, alpha, k):

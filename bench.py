@@ -191,7 +191,8 @@ def run_reference(args):
         return 0
     steps = args.steps
     _, cb = cpu_baseline(steps_cap=steps + args.warmup, budget_s=120.0)
-    line = {"impl": "reference", "metric": METRIC, "value": round(cb["value"], 4), "unit": "GB/s",
+    cb["value"] = round(cb["value"], 4)   # the line's value
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "GB/s",
             "n_gpus": args.gpus, "steps": steps, "warmup": args.warmup,
             "ms_per_step": round(cb["ms_per_step"], 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded jittered L-shape Delaunay mesh)",

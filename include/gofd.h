@@ -285,8 +285,8 @@ gofd_status gofd_solve_batch(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs
  * keep the fastest in the handle for all later products; with nb > 1 in 2D
  * also the number of columns per sub-batch of the batched product.  *best_ms (may be
  * NULL) receives its time per product of nb columns.  CTA shapes leave every
- * result bit unchanged; the column elements per thread (the FFT's radix
- * plan) and the scatter's lanes per row change the rounding order, so
+ * result bit unchanged; the elements per thread of the FFTs (their radix
+ * plans) and the scatter's lanes per row change the rounding order, so
  * products may differ in the last bits between choices (each choice is
  * reproducible run to run).  Uses the batch workspace of gofd_solve_batch
  * and drops the solvers' captured CUDA graphs.

@@ -396,7 +396,10 @@ void solve_batch(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs, int nb, co
     GOFD_CUDA_TRY(cudaMemsetAsync(X, 0, 8 * ld * nb, st));
     std::vector<double> bn, rn;
     bnorms(p, w, B, nb, bn, st);
-    for (double& v : bn) v = std::sqrt(v);
+    for (double& v : bn) {
+        v = std::sqrt(v);
+        if (!std::isfinite(v)) fail(GOFD_E_ARG, "a right-hand side has a non-finite entry");
+    }
     std::vector<int> outer(nb, 0), inner(nb, 0);
     std::vector<double> rel(nb, 0.0);
     int total_inner = 0, rounds = 0;
@@ -414,6 +417,7 @@ void solve_batch(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs, int nb, co
         std::vector<double> inv(nb), scale(nb);
         for (int c = 0; c < nb; ++c) {
             const double r = std::sqrt(rn[c]);
+            if (!std::isfinite(r)) fail(GOFD_E_NOT_CONVERGED, "a residual became non-finite");
             rel[c] = bn[c] > 0 ? r / bn[c] : 0.0;
             const bool act = rel[c] > tol;
             all_done &= !act;

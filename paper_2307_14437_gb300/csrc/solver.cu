@@ -409,6 +409,7 @@ void solve_core(gofd_problem* p, gofd_solve_mode mode, const double* b, double t
     if (init_zero) GOFD_CUDA_TRY(cudaMemsetAsync(x, 0, 8 * (n + 1), st));
     else GOFD_CUDA_TRY(cudaMemsetAsync(x + n, 0, 8, st));
     const double bn = norm64(p, w, b, st);
+    if (!std::isfinite(bn)) fail(GOFD_E_ARG, "the right-hand side has a non-finite entry");
     int outer = 0, inner = 0;
     double rel = 0.0;
     bool converged = false;
@@ -427,6 +428,10 @@ void solve_core(gofd_problem* p, gofd_solve_mode mode, const double* b, double t
         }
         GOFD_CHECK_LAUNCH();
         const double rn = norm64(p, w, r, st);
+        if (!std::isfinite(rn)) {
+            if (outer == 0) fail(GOFD_E_ARG, "the initial guess has a non-finite entry");
+            fail(GOFD_E_NOT_CONVERGED, "the residual became non-finite");
+        }
         rel = rn / bn;
         if (rel <= tol) {
             converged = true;

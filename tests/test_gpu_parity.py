@@ -218,6 +218,27 @@ def test_solve_vertex_rhs_equals_grid_rhs_for_constant_f(built):
 # ---------------------------------------------------------------------------
 # edge cases
 # ---------------------------------------------------------------------------
+def test_non_finite_data_is_rejected(built):
+    # a NaN or Inf in f reaching the right-hand side is an argument error, for
+    # both solvers and the batched one; the handle stays usable afterwards
+    from paper_2307_14437_gb300 import GofdError
+    gp, ref = built("disk37_ragged")
+    ii, _ = gp.export_vertex_data()
+    k = int(np.nonzero(ii >= 0)[0][0])
+    f = torch.ones(len(ref.verts), dtype=torch.float64, device="cuda")
+    f[k] = float("nan")
+    for mode in ("mixed", "fp64"):
+        with pytest.raises(GofdError):
+            gp.solve(f, rhs="vertex", mode=mode, tol=1e-8)
+    F = torch.ones((2, len(ref.verts)), dtype=torch.float64, device="cuda")
+    F[1, k] = float("inf")
+    with pytest.raises(GofdError):
+        gp.solve_batch(F, rhs="vertex", mode="mixed", tol=1e-8)
+    f[k] = 1.0
+    u, info = gp.solve(f, rhs="vertex", mode="mixed", tol=1e-8)
+    assert info["rel_res_fp64"] <= 1e-8 and bool(torch.isfinite(u).all())
+
+
 def test_degenerate_simplex_is_rejected():
     from paper_2307_14437_gb300 import GofdError
     v = np.array([[0.0, 0.0], [0.5, 0.5], [0.25, 0.25], [0.5, 0.0]])

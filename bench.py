@@ -53,6 +53,18 @@ def b_alg(d, n_loc, n_v, n_grid, P, b):
             + b * (P // 2 + 1) ** d)                   # symbol
 
 
+def launches_per_product(d, n, P):
+    """Kernels of one FP32 product: 2D row FFT (with the gather), column
+    convolution, inverse row FFT, scatter; 3D the same around the middle stage
+    of three kernels per chunk of spectrum planes (chunks bound the middle
+    buffer, P n complex doubles per plane, to 1 GiB)."""
+    if d == 3:
+        H = P // 2 + 1
+        per_chunk = max(1, min(H, (1 << 30) // (16 * P * n)))
+        return 3 + 3 * (-(-H // per_chunk))
+    return 4
+
+
 WORKLOADS = {
     "lshape1024": "2D L-shape [-1,1]^2\\[0,1]^2, 6.05e4 vertices, 1024^2 grid in a 2048^2 circulant, alpha=1",
     "graded2048": "2D graded unit disk, 2.1e5 vertices, 2048^2 grid in a 4096^2 circulant, alpha=1.2",
@@ -488,7 +500,7 @@ def run_gofd(args):
                                              "col_elems": inf["tune_col_elems"],
                                              "row_elems": inf["tune_row_elems"]}},
                 "roofline": roofline, "roofline_fp64_product": roofline_fp64, "e2e": e2e, "pcg": pcg,
-                "gpu_launches": 4 * args.steps, "clocks": clk}
+                "gpu_launches": launches_per_product(d, inf["n"][0], P) * args.steps, "clocks": clk}
         if world == 1 and not args.no_cpu and args.workload == "lshape1024":
             try:
                 line["cpu_baseline"] = cpu_baseline()[1]

@@ -372,9 +372,10 @@ gofd_status gofd_afd_apply(gofd_problem* p, gofd_precision prec,
  * gofd_afd_apply_noalloc -- w = A_FD v in FP32 on an n^d grid (d = 1..3)
  * without allocating any memory.  The paper has no counterpart: this entry
  * point exists for callers that cannot call cudaMalloc at the moment they
- * need the product -- code running while a CUDA graph is being captured,
- * plug-ins inside a framework that owns all device memory through its own
- * allocator, real-time loops that must not risk an allocation failure.
+ * need the product: plug-ins inside a framework that owns all device memory
+ * through its own allocator (a cudaMalloc behind its back can fail or break
+ * its accounting), real-time loops that must not risk an allocation failure
+ * or its latency, and code whose device memory is fixed up front.
  *   d, n        grid dimension and nodes per axis (no handle is needed)
  *   lambda_dev  device, (P/2+1)^d floats, axis 0 fastest: the real circulant
  *               symbol divided by P^d, lambda_k / P^d for k in [0, P/2]^d, with
@@ -383,14 +384,16 @@ gofd_status gofd_afd_apply(gofd_problem* p, gofd_precision prec,
  *   v_dev       device, n^d floats (input grid vector)
  *   w_dev       device, n^d floats (output), must not overlap v_dev
  * The spectrum scratch is a file-scope device array of 1,064,960 complex
- * floats (8.1 MiB, plus a 16 KiB twiddle table) that every GPU loading the
- * library holds until the process exits.  A grid whose spectrum does not fit
+ * floats (8.1 MiB, plus 32 KiB of twiddle tables, one per circulant length
+ * from 32 to 2048) that every GPU loading the library holds until the process
+ * exits.  A grid whose spectrum does not fit
  * (a 2D grid needs n*pitch, a 3D grid n^2*pitch + n*P*pitch complex values,
  * pitch = P/2+1 rounded up to a multiple of 16; so 2D n <= 1024) is rejected
  * with GOFD_E_ARG before any device work.  The first call on each device
- * looks up the array's device address (cudaGetSymbolAddress) and raises the
- * kernels' shared-memory limit, so make that first call before any stream
- * capture.  Every call uses the same array and it keeps the last call's
+ * looks up the arrays' device addresses (cudaGetSymbolAddress), raises the
+ * kernels' shared-memory limit and fills the twiddle tables (one launch on
+ * `stream`, then a wait for that stream), so make that first call before any
+ * stream capture.  Every call uses the same array and it keeps the last call's
  * contents; calls that overlap on the GPU (several streams or threads) race
  * and give wrong results.  No cudaMalloc, cudaFree or allocating library
  * routine is called.  Messages go to gofd_last_error(NULL).

@@ -8,7 +8,8 @@ CUDA path and the FP64 oracle can consume the same inputs without sharing code.
 
 Every generator is deterministic for a given seed (``numpy.random.default_rng``)
 and returns ``(vertices[N_v, d] float64, simplices[N_e, d+1] int32)`` with every
-simplex positively oriented.
+simplex positively oriented (``flip_orientations`` makes mixed-orientation
+copies).
 """
 from __future__ import annotations
 
@@ -54,6 +55,17 @@ def _drop_unused(verts: np.ndarray, simp: np.ndarray):
     remap = -np.ones(len(verts), dtype=np.int64)
     remap[used] = np.arange(used.sum())
     return verts[used], remap[simp]
+
+
+def flip_orientations(simp: np.ndarray, frac: float = 0.5, seed: int = SEED_BASE) -> np.ndarray:
+    """A copy of ``simp`` in which a seeded random ``frac`` of the simplices
+    have their first two local vertices swapped (negative orientation): the
+    same mesh with mixed orientations and a different local vertex order."""
+    simp = np.array(simp, dtype=np.int32, copy=True)
+    rng = np.random.default_rng(seed)
+    flip = rng.random(len(simp)) < frac
+    simp[flip, 0], simp[flip, 1] = simp[flip, 1].copy(), simp[flip, 0].copy()
+    return simp
 
 
 def mesh_volume(verts: np.ndarray, simp: np.ndarray) -> float:

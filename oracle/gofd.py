@@ -17,7 +17,8 @@ Parity status of each function (what pins it is in ``tests/test_oracle_*.py``):
   grid / locate / weights / transfer   pinned (exact rationals, grid-aligned mesh,
                                         Lemma 3.1 invariants, linear precision)
   coefficients (Filon + Richardson)    pinned (1D Gamma formula (T-1D-0), s=1 5-point,
-                                        Gauss-Legendre quadrature of (T-1), tail law)
+                                        Gauss-Legendre quadrature of (T-1) in 2D and 3D,
+                                        tail law); coefficients_at equals it entry by entry
   symbol, A_FD apply                   pinned (direct DFT, direct Toeplitz sum,
                                         s=1 Laplacian, symmetry, positivity)
   stiffness apply, rhs, cg             pinned (grid-aligned special case = (FD-1),
@@ -465,6 +466,56 @@ def coefficients(d: int, s: float, n: int, M: int | None = None, levels: int = 4
     exps = richardson_exponents(d, s, levels)
     R = [filon_coefficients(d, s, n, M // 2 ** l) for l in range(levels)]
     for e in exps:
+        r = 2.0 ** e
+        R = [(r * R[l] - R[l + 1]) / (r - 1.0) for l in range(len(R) - 1)]
+    return R[0]
+
+
+def filon_coefficients_at(d: int, s: float, ps: np.ndarray, M: int) -> np.ndarray:
+    """filon_coefficients() at a list of multi-indices ps (K x d), for grids
+    whose full coefficient array is too large to form.
+
+    The same formula written out as a sum instead of a DCT-I: with weight 1 at
+    j_i in {0, M/2} and 2 inside, the trapezoid sum (T-3) over one period is
+    sum_{j in [0,M/2]^d} wt_j psi~_j prod_i cos(2 pi p_i j_i / M), taken one
+    axis at a time (3D: one j_2 plane at a time); then the Filon factor
+    prod_i (-1)^{p_i} sinc^2(p_i/M) / M (reading R4).
+    """
+    ps = np.atleast_2d(np.asarray(ps, dtype=np.int64))
+    if ps.shape[1] != d:
+        raise OracleError("ps must have d columns")
+    H = M // 2 + 1
+    j = np.arange(H, dtype=np.int64)
+    c = 4.0 * np.cos(np.pi * j.astype(np.float64) / M) ** 2
+    wt = np.where((j == 0) | (j == M // 2), 1.0, 2.0)
+    # cos(2 pi p j / M) from the exact residue (p j) mod M
+    A = [wt[:, None] * np.cos(2.0 * np.pi * ((j[:, None] * ps[None, :, ax]) % M) / M) for ax in range(d)]
+    if d == 1:
+        S = (c ** s) @ A[0]
+    elif d == 2:
+        F = (c[:, None] + c[None, :]) ** s                   # F[j0, j1]
+        S = np.sum((F.T @ A[0]) * A[1], axis=0)
+    else:
+        S = np.zeros(len(ps))
+        base = c[:, None] + c[None, :]
+        for j2 in range(H):
+            F = (base + c[j2]) ** s
+            S += np.sum((F.T @ A[0]) * A[1], axis=0) * A[2][j2]
+    fac = np.prod((-1.0) ** ps * np.sinc(ps / M) ** 2, axis=1)
+    return fac * S / float(M) ** d
+
+
+def coefficients_at(d: int, s: float, ps, M: int, levels: int = 4) -> np.ndarray:
+    """coefficients() at a list of multi-indices ps (K x d): the Filon sums of
+    filon_coefficients_at() at M, M/2, ..., combined by the same Richardson
+    tableau (Section 2.3, reading R5)."""
+    ps = np.atleast_2d(np.asarray(ps, dtype=np.int64))
+    if M // (2 ** (levels - 1)) <= int(ps.max(initial=0)):
+        raise OracleError("coarsest Filon level must have M_l > max p")
+    R = [filon_coefficients_at(d, s, ps, M // 2 ** l) for l in range(levels)]
+    if levels == 1:
+        return R[0]
+    for e in richardson_exponents(d, s, levels):
         r = 2.0 ** e
         R = [(r * R[l] - R[l + 1]) / (r - 1.0) for l in range(len(R) - 1)]
     return R[0]

@@ -108,8 +108,11 @@ struct ColDesc {
     int P;
 };
 
+// in and out may be the same array (in-place columns): every column is read
+// into shared memory before any of it is stored, and neither pointer is
+// declared __restrict__.
 template <class Real, int MODE>
-__global__ void __launch_bounds__(512) col_fft_kernel(const typename Cplx<Real>::T* __restrict__ in, typename Cplx<Real>::T* __restrict__ out,
+__global__ void __launch_bounds__(512) col_fft_kernel(const typename Cplx<Real>::T* in, typename Cplx<Real>::T* out,
                                ColDesc cd, LinePlan plan, const typename Cplx<Real>::T* __restrict__ tw,
                                const Real* __restrict__ lam) {
     using C = typename Cplx<Real>::T;
@@ -690,23 +693,26 @@ void scatter_grid_f64(gofd_problem* p, const double* f, double* y, double scale,
 // ===========================================================================
 // Allocation-free grid convolution w = A_FD v (FP32).
 //
-// Some callers cannot call cudaMalloc when they need this product: code that
-// runs while a CUDA graph is being captured (allocation is not allowed then),
-// plug-ins living inside a host framework whose device memory is entirely
-// owned by that framework's own allocator, and real-time loops that must not
-// risk an allocation failure or its latency.  This variant takes the symbol,
+// Some callers cannot call cudaMalloc when they need this product: plug-ins
+// living inside a host framework whose device memory is entirely owned by
+// that framework's own allocator (an allocation behind its back can fail or
+// break its accounting), real-time loops that must not risk an allocation
+// failure or its latency, and code whose device memory is fixed up front.  This variant takes the symbol,
 // the input and the output from the caller and keeps its spectrum scratch in
 // a fixed file-scope device array instead of any allocation.  Every GPU that
-// loads the library holds that array (8.1 MiB plus a 16 KiB twiddle table)
+// loads the library holds that array (8.1 MiB plus 32 KiB of twiddle tables)
 // until the process exits.  It launches the generic line-FFT kernels of this
 // file (gather-free row FFTs, column FFTs, inverse row FFTs).
 // ===========================================================================
 namespace gofd {
 
 constexpr int64_t NOALLOC_MAX_COMPLEX = 1064960;  // 1024 rows x 1040: a 2D grid with n <= 1024
-constexpr int NOALLOC_MAX_P = 2048;
+constexpr int NOALLOC_MIN_P = 32, NOALLOC_MAX_P = 2048;
+// twiddle tables e^{-2 pi i m / P}, m < P, one per power of two P from 32 to
+// 2048, stored one after another: the table of P starts at entry P - 32
+constexpr int NOALLOC_TW_ENTRIES = 2 * NOALLOC_MAX_P - NOALLOC_MIN_P;
 static __device__ __align__(256) float2 g_noalloc_spec[NOALLOC_MAX_COMPLEX];
-static __device__ __align__(256) float2 g_noalloc_tw[NOALLOC_MAX_P];
+static __device__ __align__(256) float2 g_noalloc_tw[NOALLOC_TW_ENTRIES];
 
 struct NoallocDevice {
     bool ready = false;
@@ -716,18 +722,25 @@ struct NoallocDevice {
 static std::mutex g_noalloc_mu;
 static NoallocDevice g_noalloc_devices[128];
 
-__global__ void noalloc_twiddle_kernel(float2* __restrict__ tw, int P) {
-    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < P; m += gridDim.x * blockDim.x) {
+// every table at once: entry i belongs to the table of P = the largest power
+// of two <= i + 32, at position m = i - (P - 32)
+__global__ void noalloc_twiddle_kernel(float2* __restrict__ tw) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < NOALLOC_TW_ENTRIES; i += gridDim.x * blockDim.x) {
+        int P = NOALLOC_MIN_P;
+        while (2 * P <= i + NOALLOC_MIN_P) P *= 2;
+        const int m = i - (P - NOALLOC_MIN_P);
         double sn, cs;
         sincospi(2.0 * (double)m / (double)P, &sn, &cs);
-        tw[m] = make_float2((float)cs, (float)-sn);
+        tw[i] = make_float2((float)cs, (float)-sn);
     }
 }
 
 // Set-up once per device, with that device current: look up the arrays'
-// device addresses (a host-side symbol is not a device address) and raise the
-// kernels' dynamic shared-memory limit.
-static NoallocDevice noalloc_device() {
+// device addresses (a host-side symbol is not a device address), raise the
+// kernels' dynamic shared-memory limit and fill the twiddle tables (one
+// launch on the caller's stream, waited for, so that later calls on any
+// stream see the tables).
+static NoallocDevice noalloc_device(cudaStream_t st) {
     int dev = 0;
     GOFD_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 128) fail(GOFD_E_CUDA, "device ordinal out of range");
@@ -741,6 +754,9 @@ static NoallocDevice noalloc_device() {
         int limit = 0;
         GOFD_CUDA_TRY(cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
         set_smem_attrs<float>(limit);
+        noalloc_twiddle_kernel<<<grid_blocks(NOALLOC_TW_ENTRIES, 256), 256, 0, st>>>(static_cast<float2*>(tw));
+        GOFD_CHECK_LAUNCH();
+        GOFD_CUDA_TRY(cudaStreamSynchronize(st));
         d.spec = static_cast<float2*>(spec);
         d.tw = static_cast<float2*>(tw);
         d.ready = true;
@@ -764,11 +780,10 @@ void afd_apply_noalloc(int d, int n, const float* lam, const float* v, float* w,
     if (P > NOALLOC_MAX_P || needA + needB > NOALLOC_MAX_COMPLEX)
         fail(GOFD_E_ARG, "grid too large for the static scratch of 1064960 complex values "
                          "(a 2D grid needs n*pitch, a 3D grid n^2*pitch + n*P*pitch, pitch = P/2+1 rounded up to 16)");
-    const NoallocDevice dv = noalloc_device();
+    const NoallocDevice dv = noalloc_device(st);
     float2* A = dv.spec;
     float2* B = dv.spec + needA;
-    noalloc_twiddle_kernel<<<grid_blocks(P, 256), 256, 0, st>>>(dv.tw, P);
-    GOFD_CHECK_LAUNCH();
+    const float2* tw = dv.tw + (P - NOALLOC_MIN_P);
     const LinePlan row = make_line_plan(P / 2), col = make_line_plan(P);
     const int lpc = std::max(1, 256 / row.nthr);
     const int tc = std::max(1, std::min(16, 8192 / P));
@@ -778,13 +793,13 @@ void afd_apply_noalloc(int d, int n, const float* lam, const float* v, float* w,
     // forward real FFT along axis 0 of the caller's grid vector
     if (d == 1)
         row_forward_kernel<float, 2><<<rblocks, lpc * row.nthr, rsm, st>>>(
-            nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, nlines, row, dv.tw, A, pitch, 1, v, n);
+            nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, nlines, row, tw, A, pitch, 1, v, n);
     else if (d == 2)
         row_forward_kernel<float, 3><<<rblocks, lpc * row.nthr, rsm, st>>>(
-            nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, nlines, row, dv.tw, A, pitch, 1, v, n);
+            nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, nlines, row, tw, A, pitch, 1, v, n);
     else
         row_forward_kernel<float, 4><<<rblocks, lpc * row.nthr, rsm, st>>>(
-            nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, nlines, row, dv.tw, A, pitch, 1, v, n);
+            nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr, nullptr, nlines, row, tw, A, pitch, 1, v, n);
     GOFD_CHECK_LAUNCH();
     const unsigned cblocks = (unsigned)((H + tc - 1) / tc);
     const int threads_c = tc * col.nthr;
@@ -792,20 +807,20 @@ void afd_apply_noalloc(int d, int n, const float* lam, const float* v, float* w,
         spec_scale_kernel<float><<<grid_blocks(H, 256), 256, 0, st>>>(A, lam, H);
     } else if (d == 2) {
         ColDesc cd{0, pitch, 0, pitch, n, n, H, tc, 0, H, P};
-        col_fft_kernel<float, 1><<<dim3(cblocks, 1), threads_c, csm, st>>>(A, A, cd, col, dv.tw, lam);
+        col_fft_kernel<float, 1><<<dim3(cblocks, 1), threads_c, csm, st>>>(A, A, cd, col, tw, lam);
     } else {
         const int64_t pt = pitch;
         ColDesc f{(int64_t)n * pt, pt, (int64_t)P * pt, pt, n, P, H, tc, 0, 0, P};
-        col_fft_kernel<float, 0><<<dim3(cblocks, (unsigned)n), threads_c, csm, st>>>(A, B, f, col, dv.tw, lam);
+        col_fft_kernel<float, 0><<<dim3(cblocks, (unsigned)n), threads_c, csm, st>>>(A, B, f, col, tw, lam);
         GOFD_CHECK_LAUNCH();
         ColDesc m{pt, (int64_t)P * pt, pt, (int64_t)P * pt, n, n, H, tc, (int64_t)H, (int64_t)H * H, P};
-        col_fft_kernel<float, 1><<<dim3(cblocks, (unsigned)P), threads_c, csm, st>>>(B, B, m, col, dv.tw, lam);
+        col_fft_kernel<float, 1><<<dim3(cblocks, (unsigned)P), threads_c, csm, st>>>(B, B, m, col, tw, lam);
         GOFD_CHECK_LAUNCH();
         ColDesc iv{(int64_t)P * pt, pt, (int64_t)n * pt, pt, P, n, H, tc, 0, 0, P};
-        col_fft_kernel<float, 2><<<dim3(cblocks, (unsigned)n), threads_c, csm, st>>>(B, A, iv, col, dv.tw, lam);
+        col_fft_kernel<float, 2><<<dim3(cblocks, (unsigned)n), threads_c, csm, st>>>(B, A, iv, col, tw, lam);
     }
     GOFD_CHECK_LAUNCH();
-    row_inverse_kernel<float><<<rblocks, lpc * row.nthr, rsm, st>>>(A, pitch, nlines, row, dv.tw, w, n);
+    row_inverse_kernel<float><<<rblocks, lpc * row.nthr, rsm, st>>>(A, pitch, nlines, row, tw, w, n);
     GOFD_CHECK_LAUNCH();
 }
 

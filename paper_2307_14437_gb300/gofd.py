@@ -307,8 +307,9 @@ def afd_apply_noalloc(d: int, n: int, lam_scaled, v, out=None, stream=None):
     """w = A_FD v (FP32) through the entry point that allocates nothing.
 
     For callers that cannot allocate device memory when they need the product
-    (inside CUDA graph capture, under a framework-owned allocator, in
-    real-time loops): the library keeps its scratch in a fixed device array.
+    (under a framework that owns all device memory, in real-time loops that
+    must not risk an allocation failure or its latency): the library keeps its
+    scratch in a fixed device array.
     lam_scaled is the float32 symbol lambda_k / P^d on [0, P/2]^d; v and out
     are float32 grid vectors of n^d entries.  Calls that overlap on the GPU
     race on the shared scratch.

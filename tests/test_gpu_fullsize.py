@@ -5,9 +5,10 @@ L-shape 6.05e4 vertices / 1024^2 grid and graded disk 2.1e5 vertices / 2048^2
 grid: every grid node's owner and ELL row against the exact oracle, the
 coefficients and symbol, FP32 and FP64 products against the oracle's FFT
 product, solves checked with the oracle's operator.  Unit ball 1.3e5 vertices
-/ 256^3 grid: owners of sampled nodes against the exact oracle, properties
-that hold at any size (symmetry, positivity, FP32/FP64 agreement) and the
-closed-form solution (exam-2).
+/ 256^3 grid: every owner and ELL row against the exact oracle, D_h, a seeded
+sample of T against the oracle's coefficients, properties that hold at any
+size (symmetry, positivity, FP32/FP64 agreement) and the closed-form solution
+(exam-2).
 """
 import numpy as np
 import pytest
@@ -165,19 +166,50 @@ def test_graded_disk_2048(request):
     gp.close()
 
 
-def test_ball_256_properties_and_closed_form():
+@pytest.fixture(scope="module")
+def ball():
     from paper_2307_14437_gb300 import Problem
     v, s = mg.ball_shell_mesh(seed=mg.seed_for(3))
     lo, hi, h = mg.grid_box(3, 256)
     gp = Problem(v, s, 1.5, h, lo, hi)
-    owner, idx, w = gp.export_transfer()
+    yield gp, v, s, lo, hi, h
+    gp.close()
+
+
+def test_ball_256_transfer_and_coefficients(ball):
+    # every grid node's owner and every ELL row against the oracle's exact
+    # location (bounding-box pruned, same predicate and tie rule), weights
+    # within their FP64 evaluation error, D_h over every interior vertex; and
+    # a seeded sample of T (M = 2^11, the paper's 3D default) against the
+    # oracle's Filon + Richardson evaluated entry by entry
+    gp, v, s, lo, hi, h = ball
     n = o.grid_shape(lo, hi, h)
-    rng = np.random.default_rng(5)
-    located = np.nonzero(owner >= 0)[0]
-    sample = np.concatenate([rng.choice(located, 48, replace=False),
-                             rng.choice(np.nonzero(owner < 0)[0], 16, replace=False)])
-    want = o.locate(v, s, lo, h, n, nodes=sample, chunk=4)
-    assert np.array_equal(owner[sample], want.astype(np.int32))
+    owner, idx, w = gp.export_transfer()
+    want = o.locate_pruned(v, s, lo, h, n)
+    assert np.array_equal(owner, want.astype(np.int32))
+    nodes, ridx, rw = o.ell_layout(v, s, lo, h, n, want, exact=False)
+    assert np.array_equal(idx, ridx.astype(np.int32))
+    assert np.abs(w - rw).max() < 1e-12
+    I = o.transfer_matrix(nodes, ridx, rw, int(np.prod(n)), len(v))
+    Dh = o.column_sums(I)
+    interior = np.nonzero(~o.boundary_vertices(s, len(v)))[0]
+    ii, cs = gp.export_vertex_data()
+    assert np.array_equal(np.nonzero(ii >= 0)[0], interior)
+    assert np.abs(cs[interior] - Dh[interior]).max() < 1e-13 * Dh.max()
+    info = gp.info()
+    M = info["filon_M"]
+    assert M == 2 ** 11
+    rng = np.random.default_rng(mg.seed_for(3, 9))
+    ps = np.vstack([[0, 0, 0], [1, 0, 0], [1, 1, 1], [255, 0, 0], [255, 255, 255], [0, 254, 3],
+                    rng.integers(0, 256, size=(26, 3))])
+    Tw = o.coefficients_at(3, 0.75, ps, M)
+    T = gp.coefficients().reshape((256,) * 3)
+    got = np.array([T[p[2], p[1], p[0]] for p in ps])
+    assert np.abs(got - Tw).max() < 1e-13, np.abs(got - Tw).max()
+
+
+def test_ball_256_properties_and_closed_form(ball):
+    gp, v, s, lo, hi, h = ball
     # symmetry and positivity of S (Theorem 3.1), FP32 vs FP64 agreement
     a = torch.tensor(mg.random_vector(len(v), 44), device="cuda")
     b = torch.tensor(mg.random_vector(len(v), 45), device="cuda")
@@ -195,4 +227,3 @@ def test_ball_256_properties_and_closed_form():
     err = o.lumped_l2(v, s, u.cpu().numpy() - o.ball_exact(v, 0.75))
     norm = o.lumped_l2(v, s, o.ball_exact(v, 0.75))
     assert err / norm < 0.05, err / norm
-    gp.close()

@@ -90,6 +90,60 @@ def test_2d_matches_gauss_legendre_quadrature_of_definition(s):
         assert abs(T[q, p] - ref) < 1e-10, (p, q, T[q, p], ref)
 
 
+def _gl_coefficient_3d(s, p, levels=40, order=16):
+    """Independent route in 3D: tensor Gauss-Legendre quadrature of (T-1),
+    T_p = pi^{-3} int_{[0,pi]^3} psi prod_i cos(p_i xi_i), on cubic shells
+    [0, pi 2^-l]^3 minus [0, pi 2^-l-1]^3 (seven boxes each) graded toward the
+    singular corner, the outer shells further subdivided."""
+    x, w = np.polynomial.legendre.leggauss(order)
+    W = w[:, None, None] * w[None, :, None] * w[None, None, :]
+
+    def box(lo, hi):
+        pts = [0.5 * (hi[a] - lo[a]) * x + 0.5 * (hi[a] + lo[a]) for a in range(3)]
+        X, Y, Z = np.meshgrid(*pts, indexing="ij")
+        f = ((4 * np.sin(X / 2) ** 2 + 4 * np.sin(Y / 2) ** 2 + 4 * np.sin(Z / 2) ** 2) ** s
+             * np.cos(p[0] * X) * np.cos(p[1] * Y) * np.cos(p[2] * Z))
+        return np.prod([(hi[a] - lo[a]) / 2 for a in range(3)]) * (W * f).sum()
+
+    tot = 0.0
+    for l in range(levels):
+        big = np.pi * 2.0 ** (-l)
+        mid = big / 2
+        sub = 4 if l == 0 else (2 if l < 3 else 1)
+        for corner in range(1, 8):
+            lo = [mid if (corner >> a) & 1 else 0.0 for a in range(3)]
+            hi = [big if (corner >> a) & 1 else mid for a in range(3)]
+            e = [np.linspace(lo[a], hi[a], sub + 1) for a in range(3)]
+            for i in range(sub):
+                for j in range(sub):
+                    for k in range(sub):
+                        tot += box([e[0][i], e[1][j], e[2][k]], [e[0][i + 1], e[1][j + 1], e[2][k + 1]])
+    return tot / np.pi ** 3
+
+
+@pytest.mark.parametrize("s", [0.25, 0.75])
+def test_3d_matches_gauss_legendre_quadrature_of_definition(s):
+    T = o.coefficients(3, s, 4, M=2 ** 9)
+    for p in [(0, 0, 0), (1, 0, 0), (1, 1, 0), (1, 1, 1), (2, 1, 0), (3, 2, 1)]:
+        ref = _gl_coefficient_3d(s, p)
+        assert abs(T[p[2], p[1], p[0]] - ref) < 1e-10, (p, T[p[2], p[1], p[0]], ref)
+
+
+@pytest.mark.parametrize("d,n,M,s", [(1, 40, 2 ** 10, 0.3), (2, 20, 2 ** 9, 0.6), (3, 9, 2 ** 8, 0.75),
+                                     (3, 5, 2 ** 6, 0.25)])
+def test_coefficients_at_equals_full_array(d, n, M, s):
+    # the sampled evaluation (a direct trapezoid sum) equals the DCT-I route
+    # entry by entry, including the last index n-1 on the coarsest level
+    T = o.coefficients(d, s, n, M=M)
+    rng = np.random.default_rng(d)
+    ps = np.vstack([np.zeros((1, d), dtype=np.int64), np.full((1, d), n - 1), rng.integers(0, n, size=(20, d))])
+    got = o.coefficients_at(d, s, ps, M)
+    want = np.array([T[tuple(p[::-1])] for p in ps])
+    assert np.abs(got - want).max() < 1e-14 * max(1.0, np.abs(want).max())
+    with pytest.raises(o.OracleError):
+        o.coefficients_at(d, s, np.full((1, d), M // 8), M)
+
+
 @pytest.mark.parametrize("d,s", [(2, 0.5), (2, 0.75), (3, 0.75)])
 def test_tail_follows_hypersingular_kernel(d, s):
     # T_p ~ -C_{d,s} |p|^{-(d+2s)} with C_{d,s} = 2^{2s} s Gamma(s+d/2) /

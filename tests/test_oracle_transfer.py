@@ -241,3 +241,46 @@ def test_pruned_locate_equals_brute_force(case):
         lo, hi, h = mg.grid_box(3, 9)
     n = o.grid_shape(lo, hi, h)
     assert np.array_equal(o.locate_pruned(v, s, lo, h, n), o.locate(v, s, lo, h, n))
+
+
+@pytest.mark.parametrize("case", ["disk", "aligned2", "aligned3", "ball"])
+def test_mixed_orientations_permute_slots_only(case):
+    # containment in a closed simplex does not depend on its orientation: with
+    # half of the simplices flipped (first two local vertices swapped) every
+    # owner is the same, the ELL row lists the same vertices in the new local
+    # order, the exact weights follow their vertices, and the pure-rational
+    # brute force agrees
+    if case == "disk":
+        v, s = mg.disk_ring_mesh(rings=4, seed=5)
+        lo, hi, h = mg.grid_box(2, 13)
+    elif case == "aligned2":
+        lo, hi, h = mg.grid_box(2, 9)
+        v, s = mg.grid_aligned_mesh(2, -1.0, h, 4, origin_cells=2)
+    elif case == "aligned3":
+        lo, hi, h = mg.grid_box(3, 5)
+        v, s = mg.grid_aligned_mesh(3, -1.0, h, 2, origin_cells=1)
+    else:
+        v, s = mg.ball_shell_mesh(shells=2, seed=6)
+        lo, hi, h = mg.grid_box(3, 5)
+    f = mg.flip_orientations(s, seed=11)
+    flipped = np.any(f != s, axis=1)
+    assert 0.3 < flipped.mean() < 0.7
+    assert np.all(o.element_orientations(v, f)[flipped] == -1)
+    n = o.grid_shape(lo, hi, h)
+    own_s = o.locate(v, s, lo, h, n)
+    own_f = o.locate(v, f, lo, h, n)
+    assert np.array_equal(own_s, own_f)
+    assert np.array_equal(own_f, _pure_fraction_locate(v, f, lo, h, n))
+    assert np.array_equal(own_f, o.locate_pruned(v, f, lo, h, n))
+    _, idx_s, w_s = o.ell_layout(v, s, lo, h, n, own_s)
+    _, idx_f, w_f = o.ell_layout(v, f, lo, h, n, own_f)
+    swap = flipped[own_f[own_f >= 0]]
+    perm = np.arange(len(idx_s))
+    perm[:2] = [1, 0]
+    assert np.array_equal(idx_f[:, swap], idx_s[perm][:, swap])
+    assert np.array_equal(idx_f[:, ~swap], idx_s[:, ~swap])
+    assert np.array_equal(w_f[:, swap], w_s[perm][:, swap])
+    assert np.array_equal(w_f[:, ~swap], w_s[:, ~swap])
+    # float weights (the large-case route) follow their vertices too
+    _, _, wf_f = o.ell_layout(v, f, lo, h, n, own_f, exact=False)
+    assert np.abs(wf_f - w_f).max() < 1e-14

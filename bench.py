@@ -285,6 +285,8 @@ def run_gofd(args):
     nl = n ** (d - 1)
     kbytes = {
         "gather_row_fft": (d + 1) * 8 * n_loc + 4 * nint + 8 * nl * H,
+        "gather": (d + 1) * 8 * n_loc + 4 * nint + 4 * n ** d,
+        "row_fft": 4 * n ** d + 8 * nl * H,
         "col_fft_conv": 8 * n * H * 2 + 4 * H * H,
         "row_ifft": 8 * nl * H + 4 * n ** d,
         "scatter": inf["nnz_t"] * 8 + 4 * (nint + 1) + 4 * inf["nnz_t"] + 4 * nint,

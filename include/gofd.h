@@ -133,6 +133,8 @@ typedef struct {
     int tune_col_elems;        /*   elements per thread of the column FFTs,                           */
     int tune_batch_chunk;      /*   columns per sub-batch of the 2D batched product (0 = all),        */
     int tune_row_elems;        /*   elements per thread of the 2D row / 3D axis-1 FFTs (FP32)         */
+    int warp_fft_path;         /* 1: the 2D FP32 product runs the one-warp-per-1024-point-FFT kernels
+                                  (circulant 2048, default launch shapes); 0: the general kernels      */
 } gofd_info;
 
 /*

@@ -44,7 +44,7 @@ class Info(C.Structure):
                 ("min_colsum", C.c_double), ("precond_nnz", C.c_int64), ("precond_levels", C.c_int), ("ic_shift", C.c_double),
                 ("t_setup_ms", C.c_double), ("tune_lines_per_cta", C.c_int), ("tune_cols_per_cta", C.c_int),
                 ("tune_scatter_lanes", C.c_int), ("tune_col_elems", C.c_int),
-                ("tune_batch_chunk", C.c_int), ("tune_row_elems", C.c_int)]
+                ("tune_batch_chunk", C.c_int), ("tune_row_elems", C.c_int), ("warp_fft_path", C.c_int)]
 
 
 _P = C.c_void_p

@@ -43,6 +43,10 @@ int circulant_length(int n) {
     return P < 32 ? 32 : P;
 }
 
+}  // namespace
+
+namespace {
+
 void release_all(gofd_problem* p) {
     gofd::free_batch(p);
     gofd::free_adjoint(p);
@@ -341,6 +345,7 @@ gofd_status gofd_get_info(const gofd_problem* p, gofd_info* info) {
     info->tune_col_elems = p->tune_cole;
     info->tune_batch_chunk = p->tune_bchunk;
     info->tune_row_elems = p->tune_rowe;
+    info->warp_fft_path = gofd::afd_2d_warp_eligible(p) ? 1 : 0;
     return GOFD_OK;
 }
 

@@ -79,6 +79,7 @@ void setup_apply_2d(gofd_problem* p) {
     afd_2d_attrs_f32(limit, p->P, &n32);
     afd_2d_attrs_f64(limit, p->P, &n64);
     if (std::max(n32, n64) > (size_t)limit) fail(GOFD_E_GRID, "FFT line does not fit in shared memory");
+    setup_apply_2d_warp(p);
 }
 
 }  // namespace gofd

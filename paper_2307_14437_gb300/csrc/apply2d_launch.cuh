@@ -126,6 +126,12 @@ void run(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, int nb,
 
 void AFD2D_FN(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, int nb, int64_t xs, int64_t ws,
               void* spec, cudaStream_t st) {
+    if constexpr (sizeof(Real) == 4)
+        if (!vgrid && afd_2d_warp_eligible(p)) {
+            afd_2d_warp_f32(p, reinterpret_cast<const float*>(x), reinterpret_cast<float*>(wgrid), nb, xs, ws, spec,
+                            st);
+            return;
+        }
     C* S = spec ? static_cast<C*>(spec) : p->specT.as<C>();
     switch (p->P) {
         case 32: run<32>(p, x, vgrid, wgrid, nb, xs, ws, S, st); break;

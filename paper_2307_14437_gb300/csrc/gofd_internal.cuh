@@ -197,6 +197,7 @@ struct gofd_problem {
     gofd::DevBuf ell_w64;      // double[(d+1)*nloc]
     gofd::DevBuf ell_w32;      // float [(d+1)*nloc]
     gofd::DevBuf ell_iidx;     // int32 [(d+1)*nloc] interior numbering, boundary -> nint (zero slot)
+    gofd::DevBuf wdesc_line;   // 2D warp-FFT path: per-line run descriptors (2 int4 per line)
     int64_t nruns = 0;
     gofd::DevBuf line_run_ptr; // int32 [nlines+1]
     gofd::DevBuf run_k0;       // int32 [nruns]   first k0 of the run
@@ -225,6 +226,7 @@ struct gofd_problem {
     gofd::DevBuf lam64;        // double[(P/2+1)^d], scaled by 1/P^d
     gofd::DevBuf lam32;        // float [(P/2+1)^d], scaled by 1/P^d
     gofd::DevBuf tw64, tw32;   // twiddle tables e^{-2 pi i m / L} for L = P and P/2 (concatenated)
+    gofd::DevBuf twp32;        // 2D warp-FFT path: W_1024^{i j} at [i*32 + j] (float2)
 
     // FFT convolution work buffers
     int pitch0 = 0;            // complex entries per spectrum row along axis 0 (>= P/2+1)
@@ -274,6 +276,13 @@ void afd_2d_f32(gofd_problem* p, const float* x, const float* vgrid, float* wgri
                 void* spec, cudaStream_t st);
 void afd_2d_f64(gofd_problem* p, const double* x, const double* vgrid, double* wgrid, int nb, int64_t xs,
                 int64_t ws, void* spec, cudaStream_t st);
+// 2D FP32 product for a 2048-point circulant, one warp per 1024-point FFT
+// (apply2d_warp.cu); used by afd_2d_f32 when eligible (default launch shapes)
+void setup_apply_2d_warp(gofd_problem* p);
+bool afd_2d_warp_eligible(const gofd_problem* p);
+void afd_2d_warp_f32(gofd_problem* p, const float* x, float* wgrid, int nb, int64_t xs, int64_t ws, void* spec,
+                     cudaStream_t st);
+
 void apply_interior(gofd_problem* p, bool fp64, const void* x, void* y, cudaStream_t st);
 void afd_apply_grid(gofd_problem* p, bool fp64, const void* v, void* w, cudaStream_t st);
 void afd_apply_noalloc(int d, int n, const float* lam, const float* v, float* w, cudaStream_t st);

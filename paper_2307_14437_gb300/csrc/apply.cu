@@ -357,6 +357,76 @@ __global__ void __launch_bounds__(256) scatter_kernel(const int32_t* __restrict_
     }
 }
 
+// Packed scatter (the default): block c < npack takes a run of consecutive
+// rows of at most SCATTER_LONG entries each, at most SCATTER_PACK entries in
+// all (descriptor {first row, end row, first entry, end entry} from set-up).
+// Every thread loads its entries' columns and weights (set-up data) before
+// the launch dependency is resolved, then multiplies by w into shared
+// memory; one thread per row adds its products in ascending entry order.
+// Blocks from npack on take the chunks of the long rows exactly as
+// scatter_kernel does (fixed-order tree per chunk, chunks added in order).
+constexpr int SCATTER_PACK = 2048;
+constexpr int PACK_THREADS = 256;
+template <class Real>
+__global__ void __launch_bounds__(PACK_THREADS) scatter_packed_kernel(
+    const int32_t* __restrict__ ptr, const int32_t* __restrict__ col, const Real* __restrict__ val,
+    const Real* __restrict__ w, Real* __restrict__ y, Real scale, int64_t ws, int64_t ys,
+    const int4* __restrict__ pdesc, unsigned npack, LongRows lr, Real* partial, unsigned* counters) {
+    w += blockIdx.y * ws;
+    y += blockIdx.y * ys;
+    if (blockIdx.x >= npack) {
+        pdl_trigger();
+        pdl_wait();
+        __shared__ Real part[256];
+        __shared__ bool last;
+        const int64_t c = blockIdx.x - npack;
+        Real* pp = partial + (int64_t)blockIdx.y * lr.nchunks;
+        unsigned* cnt = counters + (int64_t)blockIdx.y * lr.nrows;
+        const Real sum = chunk_sum<Real>(col, val, w, __ldg(&lr.cbeg[c]), __ldg(&lr.cend[c]), part);
+        const int r = __ldg(&lr.crow[c]);
+        const int c0 = __ldg(&lr.cptr[r]), c1 = __ldg(&lr.cptr[r + 1]);
+        if (threadIdx.x == 0) {
+            pp[c] = sum;
+            __threadfence();
+            last = atomicAdd(&cnt[r], 1u) == (unsigned)(c1 - c0 - 1);
+        }
+        __syncthreads();
+        if (last && threadIdx.x == 0) {
+            __threadfence();
+            Real acc = 0;
+            for (int k = c0; k < c1; ++k) acc += ((volatile Real*)pp)[k];
+            y[__ldg(&lr.rows[r])] = acc * scale;
+            cnt[r] = 0;   // ready for the next product
+        }
+        return;
+    }
+    __shared__ Real pr[SCATTER_PACK];
+    __shared__ int rp[SCATTER_PACK + 1];
+    constexpr int PER = SCATTER_PACK / PACK_THREADS;
+    const int4 d = __ldg(&pdesc[blockIdx.x]);   // r0, r1, e0, e1
+    const int nr = d.y - d.x;
+    for (int r = threadIdx.x; r <= nr; r += PACK_THREADS) rp[r] = __ldg(&ptr[d.x + r]) - d.z;
+    int cc[PER];
+    Real vv[PER];
+#pragma unroll
+    for (int j = 0; j < PER; ++j) {
+        const int e = d.z + threadIdx.x + PACK_THREADS * j;
+        cc[j] = e < d.w ? __ldg(&col[e]) : -1;
+        vv[j] = e < d.w ? __ldg(&val[e]) : (Real)0;
+    }
+    pdl_trigger();
+    pdl_wait();
+#pragma unroll
+    for (int j = 0; j < PER; ++j)
+        if (cc[j] >= 0) pr[threadIdx.x + PACK_THREADS * j] = vv[j] * __ldg(&w[cc[j]]);
+    __syncthreads();
+    for (int r = threadIdx.x; r < nr; r += PACK_THREADS) {
+        Real s = 0;
+        for (int k = rp[r]; k < rp[r + 1]; ++k) s += pr[k];
+        y[d.x + r] = s * scale;
+    }
+}
+
 template <class Real>
 __global__ void compact_kernel(const Real* __restrict__ u, const int32_t* __restrict__ i2v, int64_t nint,
                                Real* __restrict__ x) {
@@ -445,6 +515,20 @@ void setup_apply(gofd_problem* p) {
                 }
                 cptr.push_back((int32_t)cb.size());
             }
+        // packed runs of short rows for scatter_packed_kernel: {r0, r1, e0, e1}
+        std::vector<int4> pd;
+        for (int64_t i = 0; i < p->nint;) {
+            if (ptr[i + 1] - ptr[i] > SCATTER_LONG) { ++i; continue; }
+            const int64_t r0 = i;
+            while (i < p->nint && i - r0 < SCATTER_PACK && ptr[i + 1] - ptr[i] <= SCATTER_LONG &&
+                   ptr[i + 1] - ptr[r0] <= SCATTER_PACK)
+                ++i;
+            pd.push_back(make_int4((int)r0, (int)i, ptr[r0], ptr[i]));
+        }
+        p->n_pack = (int64_t)pd.size();
+        p->pack_desc.alloc(sizeof(int4) * (pd.size() + 1));
+        if (!pd.empty())
+            GOFD_CUDA_TRY(cudaMemcpy(p->pack_desc.ptr, pd.data(), sizeof(int4) * pd.size(), cudaMemcpyHostToDevice));
         p->n_long_rows = (int64_t)rows.size();
         p->n_long_chunks = (int64_t)cb.size();
         p->long_rows.alloc(4 * (rows.size() + 1));
@@ -556,6 +640,16 @@ static void scatter_b(gofd_problem* p, const Real* wgrid, Real* y, Real scale, i
                 p->long_rows.as<int32_t>(), p->long_chunk_ptr.as<int32_t>(), p->n_long_chunks, p->n_long_rows};
     Real* part = partial ? partial : reinterpret_cast<Real*>(p->long_partial.ptr);
     unsigned* cnt = counters ? counters : p->long_cnt.as<unsigned>();
+    if (p->tune_tpr == 0) {   // default: the packed kernel
+        const dim3 grid((unsigned)(p->n_pack + p->n_long_chunks), nb);
+        if (grid.x == 0) return;
+        launch_pdl(scatter_packed_kernel<Real>, grid, dim3(PACK_THREADS), 0, st, p->csr_ptr.as<int32_t>(),
+                   p->csr_col.as<int32_t>(), val, wgrid, y, scale, ws, ys, p->pack_desc.as<int4>(),
+                   (unsigned)p->n_pack, lr, part, cnt);
+        GOFD_CHECK_LAUNCH();
+        mark_stage(st, "scatter");
+        return;
+    }
     const unsigned nshort = (unsigned)grid_blocks(p->nint * tpr, threads, 1 << 20);
     const dim3 grid(nshort + (unsigned)p->n_long_chunks, nb);
 #define SCAT(TPR)                                                                                              \

@@ -219,6 +219,8 @@ struct gofd_problem {
     gofd::DevBuf long_cnt;     // unsigned [n_long_rows] chunk counters (zero between products)
     gofd::DevBuf long_partial; // chunk partial sums (largest precision)
     int64_t n_long_rows = 0, n_long_chunks = 0;
+    gofd::DevBuf pack_desc;    // int4 [n_pack] packed runs of short rows {r0, r1, e0, e1} (default scatter)
+    int64_t n_pack = 0;
     double a_h = 0, min_colsum = 0;
 
     // coefficients and symbol

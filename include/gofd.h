@@ -282,6 +282,41 @@ gofd_status gofd_solve_batch(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs
                              double* u_dev, gofd_solve_info* infos, void* stream);
 
 /*
+ * Groups -- several 2D problems (meshes, alpha) on ONE overlay grid (same box
+ * and h, hence the same n and circulant), each with nb right-hand sides,
+ * solved together: the np*nb columns advance in lock step through one block
+ * PCG (per-column scalars and convergence, as gofd_solve_batch), whose
+ * iterations run as one CUDA graph launch with a device-side loop; every
+ * product kernel covers the columns of all problems in one launch, each
+ * column taking its problem's ELL, runs, symbol and I^T from a device table.
+ * Problems with equal alpha, Filon M and Richardson levels share one symbol.
+ * The paper has no counterpart: this is the batching of many instances.
+ *
+ * gofd_group_create -- np >= 1 problems (each 2D, all on one grid and one
+ *   device; they must outlive the group), nb >= 1 columns each.  Allocates the
+ *   group's workspace: 12 vectors of the largest N_int + 1 per column, one
+ *   grid vector and one half spectrum per column (FP64 size).  GOFD_E_ARG if
+ *   the problems do not share a grid.  The launch shapes are those of the
+ *   first problem (gofd_group_autotune tunes them on the whole group).
+ * gofd_group_autotune -- gofd_autotune for the group's product of np*nb
+ *   columns; sets the first problem's launch shapes.  *best_ms may be NULL.
+ * gofd_group_solve -- f_dev[i] (device, np pointers in a host array): the nb
+ *   columns of problem i at f_dev[i] + c*ldf[i] (n_grid doubles each for grid
+ *   data, N_v of problem i for vertex data); u_dev[i] receives nb x N_v(i)
+ *   doubles, row-major.  infos: np*nb entries, column c of problem i at
+ *   i*nb + c (may be NULL).  Modes, tolerance and errors as gofd_solve_batch.
+ *   Synchronises `stream`.  Messages go to gofd_last_error(NULL).
+ * gofd_group_destroy -- free the group (NULL is a no-op); the problems stay.
+ */
+typedef struct gofd_group gofd_group;
+gofd_status gofd_group_create(int np, gofd_problem* const* problems, int nb, gofd_group** out);
+gofd_status gofd_group_autotune(gofd_group* g, void* stream, double* best_ms);
+gofd_status gofd_group_solve(gofd_group* g, gofd_solve_mode mode, gofd_rhs rhs, const double* const* f_dev,
+                             const int64_t* ldf, double tol, int maxit, double* const* u_dev,
+                             gofd_solve_info* infos, void* stream);
+void gofd_group_destroy(gofd_group* g);
+
+/*
  * gofd_autotune -- time the batched FP32 product with nb columns for each
  * launch shape (elements per thread of the column FFTs and of the 2D row /
  * 3D axis-1 FFTs, grid lines per CTA in the row FFTs, columns per CTA in the column

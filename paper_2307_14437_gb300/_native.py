@@ -63,6 +63,10 @@ EXPORTS = {
     "gofd_solve_batch": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, C.c_int64, C.c_double, C.c_int, _P,
                                    _P, _P]),
     "gofd_autotune": (C.c_int, [_P, C.c_int, _P, C.POINTER(C.c_double)]),
+    "gofd_group_create": (C.c_int, [C.c_int, _P, C.c_int, C.POINTER(_P)]),
+    "gofd_group_autotune": (C.c_int, [_P, _P, C.POINTER(C.c_double)]),
+    "gofd_group_solve": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, C.c_double, C.c_int, _P, _P, _P]),
+    "gofd_group_destroy": (None, [_P]),
     "gofd_set_launch_shapes": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
     "gofd_get_info": (C.c_int, [_P, C.POINTER(Info)]),
     "gofd_export_transfer": (C.c_int, [_P, _P, _P, _P]),

@@ -283,6 +283,54 @@ gofd_status gofd_solve_batch(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs
     })
 }
 
+struct gofd_group {
+    gofd::Group* impl = nullptr;
+};
+
+gofd_status gofd_group_create(int np, gofd_problem* const* problems, int nb, gofd_group** out) {
+    if (out) *out = nullptr;
+    GOFD_API_BODY(nullptr, {
+        if (!out || !problems || np < 1 || nb < 1 || (int64_t)np * nb > 65535)
+            gofd::fail(GOFD_E_ARG, "need problems, 1 <= np, 1 <= nb and np*nb <= 65535");
+        auto* g = new gofd_group();
+        try {
+            g->impl = gofd::group_create(np, problems, nb);
+        } catch (...) {
+            delete g;
+            throw;
+        }
+        *out = g;
+    })
+}
+
+gofd_status gofd_group_autotune(gofd_group* g, void* stream, double* best_ms) {
+    if (!g) return GOFD_E_ARG;
+    GOFD_API_BODY(nullptr, {
+        const double ms = gofd::group_autotune(g->impl, (cudaStream_t)stream);
+        if (best_ms) *best_ms = ms;
+    })
+}
+
+gofd_status gofd_group_solve(gofd_group* g, gofd_solve_mode mode, gofd_rhs rhs, const double* const* f_dev,
+                             const int64_t* ldf, double tol, int maxit, double* const* u_dev,
+                             gofd_solve_info* infos, void* stream) {
+    if (!g) return GOFD_E_ARG;
+    GOFD_API_BODY(nullptr, {
+        if (!f_dev || !ldf || !u_dev) gofd::fail(GOFD_E_ARG, "NULL argument");
+        if (mode != GOFD_SOLVE_FP64 && mode != GOFD_SOLVE_MIXED) gofd::fail(GOFD_E_ARG, "bad mode");
+        if (rhs != GOFD_RHS_GRID && rhs != GOFD_RHS_VERTEX) gofd::fail(GOFD_E_ARG, "bad rhs kind");
+        if (!(tol > 0.0) || maxit < 1) gofd::fail(GOFD_E_ARG, "tol must be > 0 and maxit >= 1");
+        gofd::group_solve(g->impl, mode, rhs, f_dev, ldf, tol, maxit, u_dev, infos, (cudaStream_t)stream);
+    })
+}
+
+void gofd_group_destroy(gofd_group* g) {
+    if (!g) return;
+    cudaDeviceSynchronize();
+    gofd::group_destroy(g->impl);
+    delete g;
+}
+
 gofd_status gofd_autotune(gofd_problem* p, int nb, void* stream, double* best_ms) {
     if (!p) return GOFD_E_ARG;
     GOFD_API_BODY(p, {

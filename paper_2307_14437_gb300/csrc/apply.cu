@@ -371,17 +371,34 @@ template <class Real>
 __global__ void __launch_bounds__(PACK_THREADS) scatter_packed_kernel(
     const int32_t* __restrict__ ptr, const int32_t* __restrict__ col, const Real* __restrict__ val,
     const Real* __restrict__ w, Real* __restrict__ y, Real scale, int64_t ws, int64_t ys,
-    const int4* __restrict__ pdesc, unsigned npack, LongRows lr, Real* partial, unsigned* counters) {
+    const int4* __restrict__ pdesc, unsigned npack, LongRows lr, Real* partial, unsigned* counters, GroupArg ga) {
     w += blockIdx.y * ws;
     y += blockIdx.y * ys;
+    int64_t part_off = (int64_t)blockIdx.y * lr.nchunks, cnt_off = (int64_t)blockIdx.y * lr.nrows;
+    if (ga.iv) {   // a group: this column's instance (the grid covers the largest one)
+        const InstView& I = ga.iv[blockIdx.y / ga.nbper];
+        ptr = I.csr_ptr;
+        col = I.csr_col;
+        val = sizeof(Real) == 4 ? reinterpret_cast<const Real*>(I.csr_val32) : reinterpret_cast<const Real*>(I.csr_val64);
+        pdesc = I.pack_desc;
+        npack = (unsigned)I.n_pack;
+        lr = LongRows{I.cbeg, I.cend, I.crow, I.lrows, I.cptr, I.nchunks, I.nrows};
+        const int64_t c = blockIdx.y % ga.nbper;
+        part_off = I.part_off + c * I.nchunks;
+        cnt_off = I.cnt_off + c * I.nrows;
+        if (blockIdx.x >= npack + lr.nchunks) {
+            pdl_trigger();
+            return;
+        }
+    }
     if (blockIdx.x >= npack) {
         pdl_trigger();
         pdl_wait();
         __shared__ Real part[256];
         __shared__ bool last;
         const int64_t c = blockIdx.x - npack;
-        Real* pp = partial + (int64_t)blockIdx.y * lr.nchunks;
-        unsigned* cnt = counters + (int64_t)blockIdx.y * lr.nrows;
+        Real* pp = partial + part_off;
+        unsigned* cnt = counters + cnt_off;
         const Real sum = chunk_sum<Real>(col, val, w, __ldg(&lr.cbeg[c]), __ldg(&lr.cend[c]), part);
         const int r = __ldg(&lr.crow[c]);
         const int c0 = __ldg(&lr.cptr[r]), c1 = __ldg(&lr.cptr[r + 1]);
@@ -630,7 +647,7 @@ static void afd_core(gofd_problem* p, const ApplyCfg& c, const Real* x, const Re
 // counters for the long rows (NULL: the handle's, nb = 1).  One launch.
 template <class Real>
 static void scatter_b(gofd_problem* p, const Real* wgrid, Real* y, Real scale, int nb, int64_t ws, int64_t ys,
-                      Real* partial, unsigned* counters, cudaStream_t st) {
+                      Real* partial, unsigned* counters, cudaStream_t st, GroupArg ga = GroupArg{}) {
     const Real* val = reinterpret_cast<const Real*>(sizeof(Real) == 4 ? p->csr_val32.ptr : p->csr_val64.ptr);
     const double avg = p->nint ? (double)p->nnz_t / p->nint : 0;
     const int threads = 256;
@@ -640,12 +657,12 @@ static void scatter_b(gofd_problem* p, const Real* wgrid, Real* y, Real scale, i
                 p->long_rows.as<int32_t>(), p->long_chunk_ptr.as<int32_t>(), p->n_long_chunks, p->n_long_rows};
     Real* part = partial ? partial : reinterpret_cast<Real*>(p->long_partial.ptr);
     unsigned* cnt = counters ? counters : p->long_cnt.as<unsigned>();
-    if (p->tune_tpr == 0) {   // default: the packed kernel
-        const dim3 grid((unsigned)(p->n_pack + p->n_long_chunks), nb);
+    if (p->tune_tpr == 0 || ga.iv) {   // default, and every group: the packed kernel
+        const dim3 grid((unsigned)(ga.iv ? ga.max_scatter : p->n_pack + p->n_long_chunks), nb);
         if (grid.x == 0) return;
         launch_pdl(scatter_packed_kernel<Real>, grid, dim3(PACK_THREADS), 0, st, p->csr_ptr.as<int32_t>(),
                    p->csr_col.as<int32_t>(), val, wgrid, y, scale, ws, ys, p->pack_desc.as<int4>(),
-                   (unsigned)p->n_pack, lr, part, cnt);
+                   (unsigned)p->n_pack, lr, part, cnt, ga);
         GOFD_CHECK_LAUNCH();
         mark_stage(st, "scatter");
         return;
@@ -741,6 +758,55 @@ void apply_interior_batch(gofd_problem* p, bool fp64, const void* x, void* y, in
     const size_t b = fp64 ? 8 : 4;
     for (int k = 0; k < nb; ++k)
         apply_interior(p, fp64, (const char*)x + k * ld * b, (char*)y + k * ld * b, st);
+}
+
+// Y[c] = S_i X[c] for the columns of a group of 2D problems on one grid
+// (instance i = c / ga.nbper, views in ga.iv): one launch sequence for all
+// columns.  Columns have length ld; entries past an instance's n_int are zero
+// and stay zero.  rp supplies the grid, the twiddles and the launch shapes.
+void apply_interior_group(gofd_problem* rp, bool fp64, const void* x, void* y, int nbtot, int64_t ld, void* grid_ws,
+                          void* spec_ws, void* partial_ws, void* counter_ws, GroupArg ga, cudaStream_t st) {
+    const int64_t ws = rp->ngrid;
+    if (fp64) {
+        afd_2d_f64(rp, (const double*)x, nullptr, (double*)grid_ws, nbtot, ld, ws, spec_ws, st, ga);
+        scatter_b<double>(rp, (const double*)grid_ws, (double*)y, 1.0, nbtot, ws, ld, (double*)partial_ws,
+                          (unsigned*)counter_ws, st, ga);
+    } else {
+        afd_2d_f32(rp, (const float*)x, nullptr, (float*)grid_ws, nbtot, ld, ws, spec_ws, st, ga);
+        scatter_b<float>(rp, (const float*)grid_ws, (float*)y, 1.0f, nbtot, ws, ld, (float*)partial_ws,
+                         (unsigned*)counter_ws, st, ga);
+    }
+}
+
+InstView inst_view(const gofd_problem* p) {
+    InstView v;
+    v.ell_iidx = p->ell_iidx.as<int32_t>();
+    v.ell_w32 = p->ell_w32.as<float>();
+    v.ell_w64 = p->ell_w64.as<double>();
+    v.ell_node = p->ell_node.as<int32_t>();
+    v.nloc = p->nloc;
+    v.run_ptr = p->line_run_ptr.as<int32_t>();
+    v.run_k0 = p->run_k0.as<int32_t>();
+    v.run_len = p->run_len.as<int32_t>();
+    v.run_e0 = p->run_e0.as<int32_t>();
+    v.wdesc_line = p->wdesc_line.as<int4>();
+    v.lamT32 = p->lamT32.as<float>();
+    v.lamT64 = p->lamT64.as<double>();
+    v.csr_ptr = p->csr_ptr.as<int32_t>();
+    v.csr_col = p->csr_col.as<int32_t>();
+    v.csr_val32 = p->csr_val32.as<float>();
+    v.csr_val64 = p->csr_val64.as<double>();
+    v.pack_desc = p->pack_desc.as<int4>();
+    v.n_pack = p->n_pack;
+    v.cbeg = p->chunk_beg.as<int32_t>();
+    v.cend = p->chunk_end.as<int32_t>();
+    v.crow = p->chunk_row.as<int32_t>();
+    v.lrows = p->long_rows.as<int32_t>();
+    v.cptr = p->long_chunk_ptr.as<int32_t>();
+    v.nchunks = p->n_long_chunks;
+    v.nrows = p->n_long_rows;
+    v.part_off = v.cnt_off = 0;
+    return v;
 }
 
 void afd_of_interior(gofd_problem* p, bool fp64, const void* x, void* wgrid, cudaStream_t st) {

@@ -184,8 +184,18 @@ __global__ void __launch_bounds__(MAXT, MINB) row_fwd_t_kernel(
     const int32_t* __restrict__ run_ptr, const int32_t* __restrict__ run_k0, const int32_t* __restrict__ run_len,
     const int32_t* __restrict__ run_e0, const Real* __restrict__ vgrid, int nlines, int n,
     const typename Cplx<Real>::T* __restrict__ tw, typename Cplx<Real>::T* __restrict__ specT, int ld, int lpc,
-    int64_t xstride, int64_t sstride) {
+    int64_t xstride, int64_t sstride, GroupArg ga) {
     pdl_trigger();
+    if (ga.iv) {   // a group: this column's instance
+        const InstView& I = ga.iv[blockIdx.y / ga.nbper];
+        iidx = I.ell_iidx;
+        w = sizeof(Real) == 4 ? reinterpret_cast<const Real*>(I.ell_w32) : reinterpret_cast<const Real*>(I.ell_w64);
+        nloc = I.nloc;
+        run_ptr = I.run_ptr;
+        run_k0 = I.run_k0;
+        run_len = I.run_len;
+        run_e0 = I.run_e0;
+    }
     using C = typename Cplx<Real>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* sm = reinterpret_cast<C*>(smem_raw);
@@ -315,8 +325,12 @@ template <class Real, int N, int E, int MAXT = (N / E > 256 ? N / E : 256), int 
 __global__ void __launch_bounds__(MAXT, MINB) col_conv_t_kernel(typename Cplx<Real>::T* __restrict__ specT, int ld, int n,
                                                        int ncols, int H, const typename Cplx<Real>::T* __restrict__ tw,
                                                        const Real* __restrict__ lamT, int64_t sstride, int pm,
-                                                       int64_t col0) {
+                                                       int64_t col0, GroupArg ga) {
     pdl_enter();
+    if (ga.iv) {
+        const InstView& I = ga.iv[blockIdx.y / ga.nbper];
+        lamT = sizeof(Real) == 4 ? reinterpret_cast<const Real*>(I.lamT32) : reinterpret_cast<const Real*>(I.lamT64);
+    }
     using C = typename Cplx<Real>::T;
     specT += blockIdx.y * sstride;
     extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -193,7 +193,14 @@ __global__ void __launch_bounds__(GTH, 12) gather_w_kernel(const float* __restri
                                                           const float* __restrict__ w,
                                                           const int32_t* __restrict__ node, int64_t nloc,
                                                           float* __restrict__ vgrid, int64_t xstride,
-                                                          int64_t vstride) {
+                                                          int64_t vstride, GroupArg ga) {
+    if (ga.iv) {   // a group: this column's instance
+        const InstView& I = ga.iv[blockIdx.y / ga.nbper];
+        iidx = I.ell_iidx;
+        w = I.ell_w32;
+        node = I.ell_node;
+        nloc = I.nloc;
+    }
     x += blockIdx.y * xstride;
     vgrid += blockIdx.y * vstride;
     const int64_t e0 = ((int64_t)blockIdx.x * GTH) * GRW + threadIdx.x;
@@ -249,10 +256,16 @@ __global__ void __launch_bounds__(128, 3) row_fwd_w_kernel(
     const int32_t* __restrict__ run_len, int nlines, int n, const float2* __restrict__ tw,
     const float2* __restrict__ twp, const void* pf0, int64_t pb0, const void* pf1, int64_t pb1, const void* pf2,
     int64_t pb2, const void* pf3, int64_t pb3, float2* __restrict__ specT, int ld, int64_t vstride,
-    int64_t sstride) {
+    int64_t sstride, GroupArg ga) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
     const int l0 = blockIdx.x * LINES, line = l0 + g;
+    if (ga.iv) {
+        const InstView& I = ga.iv[blockIdx.y / ga.nbper];
+        ldesc = I.wdesc_line;
+        run_k0 = I.run_k0;
+        run_len = I.run_len;
+    }
     vgrid += blockIdx.y * vstride;
     specT += blockIdx.y * sstride;
     const LaneTw t = lane_twiddles(twp, tw, lane);
@@ -262,7 +275,7 @@ __global__ void __launch_bounds__(128, 3) row_fwd_w_kernel(
         d1 = __ldg(&ldesc[2 * line + 1]);
     }
     pdl_wait();
-    if (blockIdx.y == 0) {
+    if (blockIdx.y == 0 && !ga.iv) {
         prefetch_share(pf0, pb0, blockIdx.x, gridDim.x);
         prefetch_share(pf1, pb1, blockIdx.x, gridDim.x);
         prefetch_share(pf2, pb2, blockIdx.x, gridDim.x);
@@ -322,7 +335,9 @@ __global__ void __launch_bounds__(128, 3) row_fwd_w_kernel(
 __global__ void __launch_bounds__(64, 7) col_conv_w_kernel(float2* __restrict__ specT, int ld, int n,
                                                         const float2* __restrict__ tw,
                                                         const float2* __restrict__ twp,
-                                                        const float* __restrict__ lamT, int64_t sstride) {
+                                                        const float* __restrict__ lamT, int64_t sstride,
+                                                        GroupArg ga) {
+    if (ga.iv) lamT = ga.iv[blockIdx.y / ga.nbper].lamT32;
     __shared__ __align__(16) float2 xb[2][XBUF];
     __shared__ __align__(16) float2 cb[WN];
     __shared__ __align__(16) float lb[WH + 3];
@@ -482,7 +497,7 @@ void setup_apply_2d_warp(gofd_problem* p) {
 // (outputs wgrid + b ws), spectra in spec (nb x (P/2+1) x ldT complex) or the
 // handle's buffer for nb = 1.  v = I x_b is formed in wgrid + b ws first.
 void afd_2d_warp_f32(gofd_problem* p, const float* x, float* wgrid, int nb, int64_t xs, int64_t ws, void* spec,
-                     cudaStream_t st) {
+                     cudaStream_t st, GroupArg ga) {
     float2* S = spec ? static_cast<float2*>(spec) : p->specT.as<float2>();
     const int n = p->n[0], nlines = (int)p->nlines;
     const int64_t ss = (int64_t)WH * p->ldT;
@@ -491,17 +506,18 @@ void afd_2d_warp_f32(gofd_problem* p, const float* x, float* wgrid, int nb, int6
     const float2* twp = p->twp32.as<float2>();
     const unsigned rblocks = (unsigned)((nlines + LINES - 1) / LINES);
     const float* lam = p->lamT32.as<float>();
-    const unsigned gblocks = (unsigned)std::max<int64_t>(1, (p->nloc + GTH * GRW - 1) / (GTH * GRW));
+    const int64_t nloc_max = ga.iv ? ga.max_nloc : p->nloc;
+    const unsigned gblocks = (unsigned)std::max<int64_t>(1, (nloc_max + GTH * GRW - 1) / (GTH * GRW));
     launch_pdl(gather_w_kernel, dim3(gblocks, nb), dim3(GTH), 0, st, x, p->ell_iidx.as<int32_t>(),
-               p->ell_w32.as<float>(), p->ell_node.as<int32_t>(), p->nloc, wgrid, xs, ws);
+               p->ell_w32.as<float>(), p->ell_node.as<int32_t>(), p->nloc, wgrid, xs, ws, ga);
     mark_stage(st, "gather");
     launch_pdl(row_fwd_w_kernel, dim3(rblocks, nb), dim3(128), ROW_SMEM, st, (const float*)wgrid,
                p->wdesc_line.as<int4>(), p->run_k0.as<int32_t>(), p->run_len.as<int32_t>(), nlines, n, tw, twp,
                (const void*)lam, (int64_t)4 * WH * WH, (const void*)p->csr_col.ptr, (int64_t)4 * p->nnz_t,
                (const void*)p->csr_val32.ptr, (int64_t)4 * p->nnz_t, (const void*)p->csr_ptr.ptr,
-               (int64_t)4 * (p->nint + 1), S, p->ldT, ws, sb);
+               (int64_t)4 * (p->nint + 1), S, p->ldT, ws, sb, ga);
     mark_stage(st, "row_fft");
-    launch_pdl(col_conv_w_kernel, dim3(WH, nb), dim3(64), 0, st, S, p->ldT, n, tw, twp, lam, sb);
+    launch_pdl(col_conv_w_kernel, dim3(WH, nb), dim3(64), 0, st, S, p->ldT, n, tw, twp, lam, sb, ga);
     mark_stage(st, "col_fft_conv");
     launch_pdl(row_inv_w_kernel, dim3(rblocks, nb), dim3(128), ROW_SMEM, st, (const float2*)S, p->ldT, nlines, n,
                tw, twp, wgrid, sb, ws);

@@ -70,7 +70,7 @@ void run3_e(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, cuda
     launch_pdl(row_fwd_t_kernel<Real, 4, NR, ER>, dim3(rblocks), dim3(lpc * tr), row_smem3(NR, lpc), st, x,
                p->ell_iidx.as<int32_t>(), w, p->nloc, p->line_run_ptr.as<int32_t>(), p->run_k0.as<int32_t>(),
                p->run_len.as<int32_t>(), p->run_e0.as<int32_t>(), vgrid, nlines, n, tw, S, (int)ld, lpc,
-               (int64_t)0, (int64_t)0);
+               (int64_t)0, (int64_t)0, GroupArg{});
     mark_stage(st, "gather_row_fft");
     const int ngroups = (n + G - 1) / G;
     // planes k_x0 in chunks of p->midK so that the chunk's middle buffer
@@ -81,7 +81,7 @@ void run3_e(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, cuda
                    st, (const C*)S, ld, M, n, ngroups, k0, tw);
         launch_pdl(col3_kernel<NC, ECC>(), dim3((unsigned)(((int64_t)kc * P + GC - 1) / GC)),
                    dim3(GC * tcc), mid_smem3(NC, GC), st, M, n, n, (int)((int64_t)kc * P), H, tw, lamT, (int64_t)0,
-                   P, (int64_t)k0 * P);
+                   P, (int64_t)k0 * P, GroupArg{});
         launch_pdl(plane_inv_t_kernel<Real, NC, EC>, dim3((unsigned)(kc * ngroups)), dim3(G * tc), mid_smem3(NC, G),
                    st, (const C*)M, n, ngroups, k0, S, ld, tw);
     }

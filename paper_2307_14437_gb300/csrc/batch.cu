@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <memory>
 #include <vector>
 
 #include "gofd_internal.cuh"
@@ -238,25 +239,29 @@ __global__ void baccumulate_kernel(double* __restrict__ X, const float* __restri
 }
 
 // ---------------------------------------------------------------------------
-static BatchWork* ensure_batch(gofd_problem* p, int nb) {
-    BatchWork* w = p->batch;
-    if (w && w->cap >= nb) return w;
-    delete w;
-    w = new BatchWork();
-    p->batch = w;
+// workspace of nb columns of length ld on problem p's grid; long-row partial
+// sums and counters: nchunks / nrows per column (for a group: the totals)
+static void alloc_batch(BatchWork* w, const gofd_problem* p, int nb, int64_t ld, int64_t part_total,
+                        int64_t cnt_total) {
     w->cap = nb;
-    w->ld = p->nint + 1;
+    w->ld = ld;
     const int64_t m = w->ld * nb;
-    for (DevBuf* b : {&w->b64, &w->x64, &w->r64, &w->p64, &w->q64, &w->z64, &w->d64}) b->alloc(8 * m);
-    for (DevBuf* b : {&w->r32, &w->p32, &w->q32, &w->z32, &w->d32}) b->alloc(4 * m);
-    GOFD_CUDA_TRY(cudaMemset(w->p64.ptr, 0, 8 * m));
-    GOFD_CUDA_TRY(cudaMemset(w->p32.ptr, 0, 4 * m));
-    GOFD_CUDA_TRY(cudaMemset(w->x64.ptr, 0, 8 * m));
+    // every vector starts at zero: in a group, entries past a column's n_int
+    // are never written and must stay zero (the products write only the
+    // interior rows of their instance)
+    for (DevBuf* b : {&w->b64, &w->x64, &w->r64, &w->p64, &w->q64, &w->z64, &w->d64}) {
+        b->alloc(8 * m);
+        GOFD_CUDA_TRY(cudaMemset(b->ptr, 0, 8 * m));
+    }
+    for (DevBuf* b : {&w->r32, &w->p32, &w->q32, &w->z32, &w->d32}) {
+        b->alloc(4 * m);
+        GOFD_CUDA_TRY(cudaMemset(b->ptr, 0, 4 * m));
+    }
     w->grid.alloc(8 * p->ngrid * nb);
     if (p->d == 2) w->spec.alloc(sizeof(double2) * (size_t)(p->P / 2 + 1) * p->ldT * nb);
-    w->partial.alloc(8 * (p->n_long_chunks + 1) * nb);
-    w->counters.alloc(4 * (p->n_long_rows + 1) * nb);
-    GOFD_CUDA_TRY(cudaMemset(w->counters.ptr, 0, 4 * (p->n_long_rows + 1) * nb));
+    w->partial.alloc(8 * (part_total + 1));
+    w->counters.alloc(4 * (cnt_total + 1));
+    GOFD_CUDA_TRY(cudaMemset(w->counters.ptr, 0, 4 * (cnt_total + 1)));
     w->red.alloc(8 * BRED_BLOCKS * nb);
     w->cnt.alloc(sizeof(unsigned) * nb);
     GOFD_CUDA_TRY(cudaMemset(w->cnt.ptr, 0, sizeof(unsigned) * nb));
@@ -267,8 +272,37 @@ static BatchWork* ensure_batch(gofd_problem* p, int nb) {
     GOFD_CUDA_TRY(cudaEventCreateWithFlags(&w->ev_in, cudaEventDisableTiming));
     GOFD_CUDA_TRY(cudaEventCreateWithFlags(&w->ev_out, cudaEventDisableTiming));
     w->host.resize(nb);
+}
+
+static BatchWork* ensure_batch(gofd_problem* p, int nb) {
+    BatchWork* w = p->batch;
+    if (w && w->cap >= nb) return w;
+    delete w;
+    w = new BatchWork();
+    p->batch = w;
+    alloc_batch(w, p, nb, p->nint + 1, (p->n_long_chunks + 1) * nb, (p->n_long_rows + 1) * nb);
     return w;
 }
+
+// The operator of a block solve: one problem's S on every column, or a group
+// (column c belongs to instance c / nbper, all on rp's grid).  n is the
+// vector length (a group: the largest n_int; shorter columns are zero past
+// their n_int and every block-PCG step keeps them so).
+struct BOp {
+    gofd_problem* p = nullptr;
+    const std::vector<gofd_problem*>* members = nullptr;
+    int nbper = 1;
+    GroupArg ga;
+    int64_t n = 0;
+    gofd_problem* member(int c) const { return members ? (*members)[c / nbper] : p; }
+    void apply(bool f64, const void* X, void* Y, int nb, int64_t ld, BatchWork* w, cudaStream_t st) const {
+        if (members)
+            apply_interior_group(p, f64, X, Y, nb, ld, w->grid.ptr, w->spec.ptr, w->partial.ptr, w->counters.ptr, ga,
+                                 st);
+        else
+            apply_interior_batch(p, f64, X, Y, nb, ld, w->grid.ptr, w->spec.ptr, w->partial.ptr, w->counters.ptr, st);
+    }
+};
 
 void free_batch(gofd_problem* p) {
     delete p->batch;
@@ -281,8 +315,8 @@ static void read_bscal(BatchWork* w, int nb, cudaStream_t st) {
 }
 
 // column norms^2 of A (FP64) into host vector
-static void bnorms(gofd_problem* p, BatchWork* w, const double* A, int nb, std::vector<double>& out, cudaStream_t st) {
-    bdot_kernel<double><<<dim3(BRED_BLOCKS, nb), BRED_THREADS, 0, st>>>(A, A, p->nint, w->ld, w->red.as<double>(),
+static void bnorms(const BOp& op, BatchWork* w, const double* A, int nb, std::vector<double>& out, cudaStream_t st) {
+    bdot_kernel<double><<<dim3(BRED_BLOCKS, nb), BRED_THREADS, 0, st>>>(A, A, op.n, w->ld, w->red.as<double>(),
                                                                        w->cnt.as<unsigned>(), w->scal.as<BScal>(), 3);
     GOFD_CHECK_LAUNCH();
     read_bscal(w, nb, st);
@@ -293,21 +327,22 @@ static void bnorms(gofd_problem* p, BatchWork* w, const double* A, int nb, std::
 // block PCG on S D = R (all columns, precision V) from D = 0; column c stops at
 // ||r_c|| <= rtol[c] ||r_c(0)|| (rtol: device, nb entries)
 template <class V>
-static int bpcg(gofd_problem* p, BatchWork* w, int nb, V* D, V* R, V* Pd, V* Q, V* Z, const double* rtol, int maxit,
+static int bpcg(const BOp& op, BatchWork* w, int nb, V* D, V* R, V* Pd, V* Q, V* Z, const double* rtol, int maxit,
                 cudaStream_t st) {
+    gofd_problem* p = op.p;
     const bool f64 = sizeof(V) == 8;
-    const int64_t n = p->nint, ld = w->ld;
+    const int64_t n = op.n, ld = w->ld;
     BScal* s = w->scal.as<BScal>();
     double* red = w->red.as<double>();
     unsigned* cnt = w->cnt.as<unsigned>();
     const dim3 vg(grid_blocks(n, 256, 512), nb);
     const dim3 rg(BRED_BLOCKS, nb);
-    const bool pc = p->pc != nullptr;
+    const bool pc = op.member(0)->pc != nullptr;
     const int check = p->opt.check_every > 0 ? p->opt.check_every : 8;
     GOFD_CUDA_TRY(cudaMemsetAsync(D, 0, sizeof(V) * ld * nb, st));
     V* ZZ = R;
     if (pc) {
-        for (int c = 0; c < nb; ++c) precond_apply(p, f64, R + c * ld, Z + c * ld, st);
+        for (int c = 0; c < nb; ++c) precond_apply(op.member(c), f64, R + c * ld, Z + c * ld, st);
         ZZ = Z;
     }
     // r0 and tolerances
@@ -320,11 +355,11 @@ static int bpcg(gofd_problem* p, BatchWork* w, int nb, V* D, V* R, V* Pd, V* Q, 
     }
     int it = 0;
     auto iteration = [&]() {
-        apply_interior_batch(p, f64, Pd, Q, nb, ld, w->grid.ptr, w->spec.ptr, w->partial.ptr, w->counters.ptr, st);
+        op.apply(f64, Pd, Q, nb, ld, w, st);
         launch_pdl(bdot_kernel<V>, rg, dim3(BRED_THREADS), 0, st, Pd, Q, n, ld, red, cnt, s, 2);
         launch_pdl(bupdate_kernel<V>, rg, dim3(BRED_THREADS), 0, st, D, R, Pd, Q, n, ld, red, cnt, s, pc ? 1 : 0);
         if (pc) {
-            for (int c = 0; c < nb; ++c) precond_apply(p, f64, R + c * ld, Z + c * ld, st);
+            for (int c = 0; c < nb; ++c) precond_apply(op.member(c), f64, R + c * ld, Z + c * ld, st);
             launch_pdl(bdot_kernel<V>, rg, dim3(BRED_THREADS), 0, st, R, Z, n, ld, red, cnt, s, 1);
         }
         launch_pdl(bupdate_p_kernel<V>, vg, dim3(256), 0, st, Pd, ZZ, n, ld, s);
@@ -372,10 +407,20 @@ static int bpcg(gofd_problem* p, BatchWork* w, int nb, V* D, V* R, V* Pd, V* Q, 
     return it;
 }
 
-void solve_batch(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs, int nb, const double* F, int64_t ldf,
-                 double tol, int maxit, double* U, gofd_solve_info* infos, cudaStream_t caller) {
+// Columns of a block solve: column c reads its right-hand side at Fc(c) and
+// writes its solution (N_v of its problem) at Uc(c).
+struct Cols {
+    const double* const* F;   // per instance
+    const int64_t* ldf;       // per instance
+    double* const* U;         // per instance
+    int nbper;
+    const double* fcol(int c) const { return F[c / nbper] + (c % nbper) * ldf[c / nbper]; }
+};
+
+static void solve_cols(const BOp& op, BatchWork* w, const Cols& cols, gofd_solve_mode mode, gofd_rhs rhs, int nb,
+                       double tol, int maxit, gofd_solve_info* infos, cudaStream_t caller) {
     auto t0 = std::chrono::steady_clock::now();
-    BatchWork* w = ensure_batch(p, nb);
+    gofd_problem* p = op.p;
     const cudaStream_t st = w->gs;
     GOFD_CUDA_TRY(cudaEventRecord(w->ev_in, caller));
     GOFD_CUDA_TRY(cudaStreamWaitEvent(st, w->ev_in, 0));
@@ -387,15 +432,16 @@ void solve_batch(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs, int nb, co
             cudaStreamWaitEvent(caller, w->ev_out, 0);
         }
     } join{w, caller};
-    const int64_t n = p->nint, ld = w->ld;
+    const int64_t n = op.n, ld = w->ld;
     double* B = w->b64.as<double>();
     double* X = w->x64.as<double>();
     double* R = w->r64.as<double>();
     const dim3 vg(grid_blocks(n, 256, 512), nb);
-    for (int c = 0; c < nb; ++c) assemble_rhs(p, rhs, F + c * ldf, B + c * ld, st);
+    if (op.members) GOFD_CUDA_TRY(cudaMemsetAsync(B, 0, 8 * ld * nb, st));   // zero past each n_int
+    for (int c = 0; c < nb; ++c) assemble_rhs(op.member(c), rhs, cols.fcol(c), B + c * ld, st);
     GOFD_CUDA_TRY(cudaMemsetAsync(X, 0, 8 * ld * nb, st));
     std::vector<double> bn, rn;
-    bnorms(p, w, B, nb, bn, st);
+    bnorms(op, w, B, nb, bn, st);
     for (double& v : bn) {
         v = std::sqrt(v);
         if (!std::isfinite(v)) fail(GOFD_E_ARG, "a right-hand side has a non-finite entry");
@@ -408,11 +454,11 @@ void solve_batch(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs, int nb, co
         if (rounds == 0) {
             bcopy_kernel<double><<<vg, 256, 0, st>>>(B, R, n, ld);
         } else {
-            apply_interior_batch(p, true, X, w->q64.ptr, nb, ld, w->grid.ptr, w->spec.ptr, w->partial.ptr, w->counters.ptr, st);
+            op.apply(true, X, w->q64.ptr, nb, ld, w, st);
             bresidual_kernel<<<vg, 256, 0, st>>>(B, w->q64.as<double>(), R, n, ld);
         }
         GOFD_CHECK_LAUNCH();
-        bnorms(p, w, R, nb, rn, st);
+        bnorms(op, w, R, nb, rn, st);
         all_done = true;
         std::vector<double> inv(nb), scale(nb);
         for (int c = 0; c < nb; ++c) {
@@ -443,12 +489,12 @@ void solve_batch(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs, int nb, co
         if (mode == GOFD_SOLVE_FP64) {
             // columns normalised to unit residual; converged columns are all zero and stay put
             bscale_kernel<<<vg, 256, 0, st>>>(R, dinv, n, ld);
-            its = bpcg<double>(p, w, nb, w->d64.as<double>(), R, w->p64.as<double>(), w->q64.as<double>(),
+            its = bpcg<double>(op, w, nb, w->d64.as<double>(), R, w->p64.as<double>(), w->q64.as<double>(),
                                w->z64.as<double>(), drtol, maxit - total_inner, st);
             baccumulate64_kernel<<<vg, 256, 0, st>>>(X, w->d64.as<double>(), dscale, n, ld);
         } else {
             bscale_to_f32_kernel<<<vg, 256, 0, st>>>(R, w->r32.as<float>(), dinv, n, ld);
-            its = bpcg<float>(p, w, nb, w->d32.as<float>(), w->r32.as<float>(), w->p32.as<float>(),
+            its = bpcg<float>(op, w, nb, w->d32.as<float>(), w->r32.as<float>(), w->p32.as<float>(),
                               w->q32.as<float>(), w->z32.as<float>(), drtol, maxit - total_inner, st);
             baccumulate_kernel<<<vg, 256, 0, st>>>(X, w->d32.as<float>(), dscale, n, ld);
         }
@@ -459,26 +505,39 @@ void solve_batch(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs, int nb, co
             if (scale[c] > 0) inner[c] += its;
         if (its == 0) break;
     }
-    for (int c = 0; c < nb; ++c) expand_interior(p, true, X + c * ld, U + c * p->nv, 0.0, st);
+    for (int c = 0; c < nb; ++c)
+        expand_interior(op.member(c), true, X + c * ld, cols.U[c / cols.nbper] + (int64_t)(c % cols.nbper) * op.member(c)->nv,
+                        0.0, st);
     GOFD_CUDA_TRY(cudaStreamSynchronize(st));
     auto t1 = std::chrono::steady_clock::now();
     if (infos)
         for (int c = 0; c < nb; ++c) {
             gofd_solve_info& info = infos[c];
+            const gofd_problem* q = op.member(c);
             info.outer_iters = outer[c];
             info.inner_iters = inner[c];
             info.rel_res_fp64 = rel[c];
-            info.a_h = p->a_h;
-            info.min_colsum = p->min_colsum;
-            info.ic_shift = precond_shift(p);
-            const double dd = p->d;
-            info.h_within_strict_bound = p->h <= p->a_h / ((dd + 1) * std::sqrt(dd));
-            info.h_within_practical_bound = p->h <= p->a_h;
-            info.t_setup_ms = p->t_setup_ms;
+            info.a_h = q->a_h;
+            info.min_colsum = q->min_colsum;
+            info.ic_shift = precond_shift(q);
+            const double dd = q->d;
+            info.h_within_strict_bound = q->h <= q->a_h / ((dd + 1) * std::sqrt(dd));
+            info.h_within_practical_bound = q->h <= q->a_h;
+            info.t_setup_ms = q->t_setup_ms;
             info.t_solve_ms = std::chrono::duration<double, std::milli>(t1 - t0).count();
             info.device_loop = !w->no_graph && (w->graph[0] || w->graph[1]);
         }
     if (!all_done) fail(GOFD_E_NOT_CONVERGED, "batched solver reached maxit before tol");
+}
+
+void solve_batch(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs, int nb, const double* F, int64_t ldf,
+                 double tol, int maxit, double* U, gofd_solve_info* infos, cudaStream_t caller) {
+    BatchWork* w = ensure_batch(p, nb);
+    BOp op;
+    op.p = p;
+    op.n = p->nint;
+    Cols cols{&F, &ldf, &U, nb};
+    solve_cols(op, w, cols, mode, rhs, nb, tol, maxit, infos, caller);
 }
 
 void apply_batch(gofd_problem* p, bool fp64, const void* x, void* y, int nb, int64_t ld, cudaStream_t st) {
@@ -489,9 +548,19 @@ void apply_batch(gofd_problem* p, bool fp64, const void* x, void* y, int nb, int
 // ---------------------------------------------------------------------------
 // autotuner: time the batched FP32 product for each launch shape
 // ---------------------------------------------------------------------------
+static double tune_op(const BOp& op, BatchWork* w, int nb, cudaStream_t st);
+
 double autotune(gofd_problem* p, int nb, cudaStream_t st) {
     BatchWork* w = ensure_batch(p, nb);
     invalidate_graphs(p);
+    BOp op;
+    op.p = p;
+    op.n = p->nint;
+    return tune_op(op, w, nb, st);
+}
+
+static double tune_op(const BOp& op, BatchWork* w, int nb, cudaStream_t st) {
+    gofd_problem* p = op.p;
     for (auto& g : w->graph)
         if (g) {
             cudaGraphExecDestroy(g);
@@ -507,13 +576,10 @@ double autotune(gofd_problem* p, int nb, cudaStream_t st) {
     // thread (2D), lines per CTA of the row transforms, columns per CTA,
     // scatter lanes per row, sub-batch size (2D batches)
     auto time_current = [&]() {
-        apply_interior_batch(p, false, w->p32.ptr, w->q32.ptr, nb, ld, w->grid.ptr, w->spec.ptr, w->partial.ptr,
-                             w->counters.ptr, st);   // warm
+        op.apply(false, w->p32.ptr, w->q32.ptr, nb, ld, w, st);   // warm
         constexpr int reps = 10;
         GOFD_CUDA_TRY(cudaEventRecord(a, st));
-        for (int r = 0; r < reps; ++r)
-            apply_interior_batch(p, false, w->p32.ptr, w->q32.ptr, nb, ld, w->grid.ptr, w->spec.ptr,
-                                 w->partial.ptr, w->counters.ptr, st);
+        for (int r = 0; r < reps; ++r) op.apply(false, w->p32.ptr, w->q32.ptr, nb, ld, w, st);
         GOFD_CUDA_TRY(cudaEventRecord(b, st));
         GOFD_CUDA_TRY(cudaEventSynchronize(b));
         float ms = 0;
@@ -522,7 +588,8 @@ double autotune(gofd_problem* p, int nb, cudaStream_t st) {
     };
     const std::vector<int> shapes = p->d == 2 ? std::vector<int>{1, 2, 4} : std::vector<int>{0};
     const std::vector<int> elems = p->d == 1 ? std::vector<int>{0} : std::vector<int>{8, 16, 32};
-    const std::vector<int> lanes = {4, 8, 16, 32};
+    // a group always takes the packed scatter: no lane widths to sweep
+    const std::vector<int> lanes = op.members ? std::vector<int>{} : std::vector<int>{4, 8, 16, 32};
     const std::vector<int> rowe = p->d >= 2 ? std::vector<int>{8, 16} : std::vector<int>{0};
     p->tune_cole = p->tune_lpc = p->tune_cols = p->tune_tpr = p->tune_bchunk = p->tune_rowe = 0;
     double best = time_current();
@@ -543,7 +610,7 @@ double autotune(gofd_problem* p, int nb, cudaStream_t st) {
     sweep(&p->tune_lpc, shapes, &bl);
     sweep(&p->tune_cols, shapes, &bc);
     sweep(&p->tune_tpr, lanes, &bt);
-    if (p->d == 2 && nb > 1) {
+    if (p->d == 2 && nb > 1 && !op.members) {
         std::vector<int> chunks;
         for (int k : {1, 2, 4})
             if (k < nb) chunks.push_back(k);
@@ -558,6 +625,97 @@ double autotune(gofd_problem* p, int nb, cudaStream_t st) {
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     return best;
+}
+
+// ---------------------------------------------------------------------------
+// groups: problems on one grid solved together (the batched workload)
+// ---------------------------------------------------------------------------
+struct Group {
+    std::vector<gofd_problem*> members;
+    int nbper = 0;
+    int64_t n = 0;
+    BatchWork work;
+    DevBuf views;
+    GroupArg ga;
+    BOp op() {
+        BOp o;
+        o.p = members[0];
+        o.members = &members;
+        o.nbper = nbper;
+        o.ga = ga;
+        o.n = n;
+        return o;
+    }
+};
+
+Group* group_create(int np, gofd_problem* const* probs, int nb) {
+    const gofd_problem* r = probs[0];
+    for (int i = 0; i < np; ++i) {
+        const gofd_problem* q = probs[i];
+        if (!q) fail(GOFD_E_ARG, "NULL problem in the group");
+        if (q->d != 2) fail(GOFD_E_ARG, "groups are 2D");
+        if (q->n[0] != r->n[0] || q->n[1] != r->n[1] || q->P != r->P || q->h != r->h || q->lo[0] != r->lo[0] ||
+            q->lo[1] != r->lo[1] || q->device != r->device)
+            fail(GOFD_E_ARG, "the problems of a group must share one grid (box, h) and one device");
+    }
+    auto g = std::make_unique<Group>();
+    g->members.assign(probs, probs + np);
+    g->nbper = nb;
+    std::vector<InstView> v(np);
+    int64_t part = 0, cnt = 0;
+    for (int i = 0; i < np; ++i) {
+        const gofd_problem* q = probs[i];
+        v[i] = inst_view(q);
+        v[i].part_off = part;
+        v[i].cnt_off = cnt;
+        part += (int64_t)nb * q->n_long_chunks;
+        cnt += (int64_t)nb * q->n_long_rows;
+        g->n = std::max<int64_t>(g->n, q->nint);
+        g->ga.max_nloc = std::max<int64_t>(g->ga.max_nloc, q->nloc);
+        g->ga.max_scatter = std::max<int64_t>(g->ga.max_scatter, q->n_pack + q->n_long_chunks);
+        // one symbol per (alpha, Filon M, Richardson levels) on this grid
+        for (int j = 0; j < i; ++j) {
+            const gofd_problem* o = probs[j];
+            if (o->alpha == q->alpha && o->filon_M == q->filon_M && o->rich_levels == q->rich_levels) {
+                v[i].lamT32 = v[j].lamT32;
+                v[i].lamT64 = v[j].lamT64;
+                break;
+            }
+        }
+    }
+    g->views.alloc(sizeof(InstView) * np);
+    GOFD_CUDA_TRY(cudaMemcpy(g->views.ptr, v.data(), sizeof(InstView) * np, cudaMemcpyHostToDevice));
+    g->ga.iv = g->views.as<InstView>();
+    g->ga.nbper = nb;
+    alloc_batch(&g->work, r, np * nb, g->n + 1, part, cnt);
+    return g.release();
+}
+
+void group_destroy(Group* g) { delete g; }
+
+double group_autotune(Group* g, cudaStream_t st) {
+    BatchWork* w = &g->work;
+    for (auto& gr : w->graph)
+        if (gr) {
+            cudaGraphExecDestroy(gr);
+            gr = nullptr;
+        }
+    invalidate_graphs(g->members[0]);
+    const int nb = (int)g->members.size() * g->nbper;
+    GOFD_CUDA_TRY(cudaMemsetAsync(w->p32.ptr, 0, 4 * w->ld * nb, st));
+    return tune_op(g->op(), w, nb, st);
+}
+
+void group_solve(Group* g, gofd_solve_mode mode, gofd_rhs rhs, const double* const* F, const int64_t* ldf, double tol,
+                 int maxit, double* const* U, gofd_solve_info* infos, cudaStream_t st) {
+    const int np = (int)g->members.size();
+    for (int i = 0; i < np; ++i) {
+        if (!F[i] || !U[i]) fail(GOFD_E_ARG, "NULL vector");
+        if (ldf[i] < (rhs == GOFD_RHS_GRID ? g->members[i]->ngrid : g->members[i]->nv))
+            fail(GOFD_E_ARG, "ldf smaller than a column");
+    }
+    Cols cols{F, ldf, U, g->nbper};
+    solve_cols(g->op(), &g->work, cols, mode, rhs, np * g->nbper, tol, maxit, infos, st);
 }
 
 }  // namespace gofd

@@ -161,6 +161,35 @@ LinePlan make_line_plan(int N);
 // ---------------------------------------------------------------------------
 // the problem handle
 // ---------------------------------------------------------------------------
+// A group of 2D problems on the same grid, solved together: the batched
+// product kernels take the instance of column blockIdx.y (instance
+// blockIdx.y / nbper) from a device table of these views.
+struct InstView {
+    const int32_t* ell_iidx;
+    const float* ell_w32;
+    const double* ell_w64;
+    const int32_t* ell_node;
+    int64_t nloc;
+    const int32_t *run_ptr, *run_k0, *run_len, *run_e0;
+    const int4* wdesc_line;
+    const float* lamT32;
+    const double* lamT64;
+    const int32_t *csr_ptr, *csr_col;
+    const float* csr_val32;
+    const double* csr_val64;
+    const int4* pack_desc;
+    int64_t n_pack;
+    const int32_t *cbeg, *cend, *crow, *lrows, *cptr;   // long rows of I^T and their chunks
+    int64_t nchunks, nrows;
+    int64_t part_off, cnt_off;   // this instance's long-row partial sums / counters in the group workspace
+};
+struct GroupArg {
+    const InstView* iv = nullptr;   // nullptr: one problem (the kernel's own arguments)
+    int nbper = 1;                  // columns per instance
+    int64_t max_nloc = 0;           // host side: largest n_loc / scatter grid over the instances
+    int64_t max_scatter = 0;
+};
+
 struct Precond;   // defined in precond.cu
 
 struct Workspace;  // solver vectors, defined in solver.cu
@@ -275,15 +304,15 @@ void afd_3d_f64(gofd_problem* p, const double* x, const double* vgrid, double* w
 // nb right-hand sides: inputs at x + b*xs (or vgrid + b*xs), outputs at wgrid + b*ws;
 // spec = batch spectrum buffer (nb x (P/2+1) x ldT complex) or NULL for one vector
 void afd_2d_f32(gofd_problem* p, const float* x, const float* vgrid, float* wgrid, int nb, int64_t xs, int64_t ws,
-                void* spec, cudaStream_t st);
+                void* spec, cudaStream_t st, GroupArg ga = GroupArg{});
 void afd_2d_f64(gofd_problem* p, const double* x, const double* vgrid, double* wgrid, int nb, int64_t xs,
-                int64_t ws, void* spec, cudaStream_t st);
+                int64_t ws, void* spec, cudaStream_t st, GroupArg ga = GroupArg{});
 // 2D FP32 product for a 2048-point circulant, one warp per 1024-point FFT
 // (apply2d_warp.cu); used by afd_2d_f32 when eligible (default launch shapes)
 void setup_apply_2d_warp(gofd_problem* p);
 bool afd_2d_warp_eligible(const gofd_problem* p);
 void afd_2d_warp_f32(gofd_problem* p, const float* x, float* wgrid, int nb, int64_t xs, int64_t ws, void* spec,
-                     cudaStream_t st);
+                     cudaStream_t st, GroupArg ga = GroupArg{});
 
 void apply_interior(gofd_problem* p, bool fp64, const void* x, void* y, cudaStream_t st);
 void afd_apply_grid(gofd_problem* p, bool fp64, const void* v, void* w, cudaStream_t st);
@@ -322,6 +351,11 @@ void sort_packed_rows(const int32_t* ptr, int64_t nrows, int64_t* packed, int64_
 // unsigned, zero on entry and on exit
 void apply_interior_batch(gofd_problem* p, bool fp64, const void* x, void* y, int nb, int64_t ld, void* grid_ws,
                           void* spec_ws, void* partial_ws, void* counter_ws, cudaStream_t st);
+// a group of 2D problems on one grid (apply.cu): the view of one problem, and
+// Y[c] = S_{c / nbper} X[c] for all columns of the group in one launch sequence
+InstView inst_view(const gofd_problem* p);
+void apply_interior_group(gofd_problem* rp, bool fp64, const void* x, void* y, int nbtot, int64_t ld, void* grid_ws,
+                          void* spec_ws, void* partial_ws, void* counter_ws, GroupArg ga, cudaStream_t st);
 // w = A_FD I x on the grid for an interior-compacted x (n_int + 1 entries)
 void afd_of_interior(gofd_problem* p, bool fp64, const void* x, void* wgrid, cudaStream_t st);
 // adjoint (adjoint.cu)
@@ -334,5 +368,12 @@ void solve_batch(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs, int nb, co
 double autotune(gofd_problem* p, int nb, cudaStream_t st);
 void apply_batch(gofd_problem* p, bool fp64, const void* x, void* y, int nb, int64_t ld, cudaStream_t st);
 void free_batch(gofd_problem* p);
+// groups of 2D problems on one grid (batch.cu)
+struct Group;
+Group* group_create(int np, gofd_problem* const* probs, int nb);
+void group_destroy(Group* g);
+double group_autotune(Group* g, cudaStream_t st);
+void group_solve(Group* g, gofd_solve_mode mode, gofd_rhs rhs, const double* const* F, const int64_t* ldf, double tol,
+                 int maxit, double* const* U, gofd_solve_info* infos, cudaStream_t st);
 
 }  // namespace gofd

@@ -256,31 +256,123 @@ class Problem:
         return gf, gx, {k: getattr(info, k) for k, _ in N.SolveInfo._fields_}
 
 
+class Group:
+    """Several 2D problems on one overlay grid, nb right-hand sides each,
+    solved together in lock step (gofd_group_*): one block PCG over all
+    columns, one CUDA graph launch per inner solve, every product kernel
+    covering all problems' columns.  The problems must outlive the group."""
+
+    def __init__(self, problems, nb: int):
+        self._lib = N.load()
+        self.problems = list(problems)
+        self.nb = int(nb)
+        arr = (C.c_void_p * len(self.problems))(*[q._h.value for q in self.problems])
+        h = C.c_void_p()
+        st = self._lib.gofd_group_create(len(self.problems), C.cast(arr, C.c_void_p), self.nb, C.byref(h))
+        if st != 0:
+            raise GofdError(st, self._lib.gofd_last_error(None).decode())
+        self._g = h
+
+    def _check(self, st: int):
+        if st != 0:
+            raise GofdError(st, self._lib.gofd_last_error(None).decode())
+
+    def autotune(self, stream=None) -> float:
+        """Tune the launch shapes of the group's product; returns ms per product."""
+        ms = C.c_double(0)
+        self._check(self._lib.gofd_group_autotune(self._g, _stream_ptr(stream), C.byref(ms)))
+        return ms.value
+
+    def solve(self, batches, rhs: str = "grid", mode: str = "mixed", tol: float = 1e-8, maxit: int = 100000,
+              stream=None):
+        """batches[i]: (nb, len) float64 CUDA tensor of problem i (rows contiguous).
+        Returns [(U_i: nb x N_v(i), infos_i)] in the problems' order."""
+        torch = _torch()
+        np_ = len(self.problems)
+        if len(batches) != np_:
+            raise ValueError("one batch per problem")
+        Us = []
+        for q, F in zip(self.problems, batches):
+            if F.dtype != torch.float64 or F.dim() != 2 or F.shape[0] != self.nb or F.stride(1) != 1:
+                raise TypeError("each batch must be a float64 (nb, len) tensor with contiguous rows")
+            Us.append(torch.empty((self.nb, q.n_v), dtype=torch.float64, device=F.device))
+        fp = (C.c_void_p * np_)(*[F.data_ptr() for F in batches])
+        up = (C.c_void_p * np_)(*[U.data_ptr() for U in Us])
+        ld = (C.c_int64 * np_)(*[int(F.stride(0)) for F in batches])
+        infos = (N.SolveInfo * (np_ * self.nb))()
+        self._check(self._lib.gofd_group_solve(self._g, _MODES[mode], _RHS[rhs], C.cast(fp, C.c_void_p),
+                                               C.cast(ld, C.c_void_p), float(tol), int(maxit),
+                                               C.cast(up, C.c_void_p), C.cast(infos, C.c_void_p),
+                                               _stream_ptr(stream)))
+        rows = [{k: getattr(i, k) for k, _ in N.SolveInfo._fields_} for i in infos]
+        return [(Us[i], rows[i * self.nb:(i + 1) * self.nb]) for i in range(np_)]
+
+    def close(self):
+        if getattr(self, "_g", None):
+            self._lib.gofd_group_destroy(self._g)
+            self._g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def grid_key(problem):
+    """Problems with equal keys share an overlay grid (and can form a Group)."""
+    inf = problem.info()
+    return (inf["d"], tuple(inf["n"]), inf["P"], float(problem.h))
+
+
 def solve_many(problems, batches, rhs: str = "grid", mode: str = "mixed", tol: float = 1e-8,
-               maxit: int = 100000):
-    """Independent problems (meshes, grids) solved concurrently: problem i
-    solves the columns of batches[i] with solve_batch on a stream of its own,
-    from one host thread per problem (the C calls release the interpreter
-    lock).  Returns the list of (U, infos) in order."""
+               maxit: int = 100000, groups=None):
+    """Independent problems solved together.  2D problems are grouped by grid
+    (grid_key): each group is solved as one Group (all its columns in one
+    block PCG); groups, and problems of other dimensions (solve_batch), run
+    concurrently, one host thread and stream each (the C calls release the
+    interpreter lock).  groups: optional dict key -> Group built earlier for
+    these problems (reused; keeps its tuned launch shapes).  Returns the list
+    of (U, infos) in the problems' order."""
     import threading
     torch = _torch()
     dev = torch.cuda.current_device()
-    streams = [torch.cuda.Stream() for _ in problems]
+    units = {}
+    for i, q in enumerate(problems):
+        key = grid_key(q) if q.d == 2 else ("single", i)
+        units.setdefault(key, []).append(i)
+    keys = list(units)
+    streams = [torch.cuda.Stream() for _ in keys]
     for s in streams:
         s.wait_stream(torch.cuda.current_stream())
     out = [None] * len(problems)
-    errs = [None] * len(problems)
+    errs = [None] * len(keys)
+    nb = {i: batches[i].shape[0] for i in range(len(problems))}
 
-    def work(i):
+    def work(u):
         try:
             torch.cuda.set_device(dev)
-            with torch.cuda.stream(streams[i]):
-                out[i] = problems[i].solve_batch(batches[i], rhs=rhs, mode=mode, tol=tol, maxit=maxit,
-                                                 stream=streams[i])
+            idx = units[keys[u]]
+            with torch.cuda.stream(streams[u]):
+                if keys[u][0] == "single" or len(set(nb[i] for i in idx)) != 1:
+                    for i in idx:
+                        out[i] = problems[i].solve_batch(batches[i], rhs=rhs, mode=mode, tol=tol, maxit=maxit,
+                                                         stream=streams[u])
+                    return
+                g = groups.get(keys[u]) if groups else None
+                own = g is None
+                if own:
+                    g = Group([problems[i] for i in idx], nb[idx[0]])
+                res = g.solve([batches[i] for i in idx], rhs=rhs, mode=mode, tol=tol, maxit=maxit,
+                              stream=streams[u])
+                for i, r in zip(idx, res):
+                    out[i] = r
+                if own:
+                    g.close()
         except Exception as e:  # re-raised on the caller's thread
-            errs[i] = e
+            errs[u] = e
 
-    threads = [threading.Thread(target=work, args=(i,)) for i in range(len(problems))]
+    threads = [threading.Thread(target=work, args=(u,)) for u in range(len(keys))]
     for t in threads:
         t.start()
     for t in threads:

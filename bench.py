@@ -6,12 +6,18 @@ Delaunay mesh of ~6.0e4 vertices, overlay grid 1024^2 on [-1,1]^2 embedded in a
 2048^2 circulant.  A step is one FP32 stiffness product y = I^T A_FD I x
 (gather, FFT convolution, scatter) on device-resident interior vectors; L2 is
 flushed (256 MB write) before every timed step.  The headline value is the
-algorithmic bytes of one product divided by its time (GB/s).  Beside it:
-per-kernel times and the roofline of the dominant kernel, the same product
-end to end through the host-buffer C-ABI call, time to relative residual 1e-8
-for mixed-precision refinement vs plain FP64 PCG at alpha in {0.5, 1, 1.5}
-and on the 2048^2 graded-disk configuration (alpha = 1.2, vertex data), and
-the FP64 CPU oracle timed on the host cores.
+algorithmic bytes of one product divided by its time (GB/s), and the roofline
+is that product against the measured HBM copy bandwidth.  Beside it: per-kernel
+times (the slowest stage in its own key), the same product end to end through
+the host-buffer C-ABI call, and these extras:
+  * time to relative residual 1e-8, mixed-precision refinement vs plain FP64
+    PCG, on the L-shape at alpha in {0.5, 1, 1.5}, on the 2048^2 graded disk
+    (alpha = 1.2, vertex data) and on the 256^3 ball (alpha = 1.5, with the
+    error against the closed form);
+  * the graded-disk gradient: forward solve and adjoint (dL/df, dL/dX) times;
+  * the 48-instance x 8 right-hand-side batch through grid groups, with one
+    right-hand side at a time in FP64 beside it (sampled, scaled);
+  * the FP64 CPU oracle's product timed on the host cores.
 
 Multi-GPU runs (torchrun) execute independent replicas (the product does not
 shard): no data-path collective; the aggregate value sums all ranks' bytes
@@ -53,18 +59,6 @@ def b_alg(d, n_loc, n_v, n_grid, P, b):
             + b * (P // 2 + 1) ** d)                   # symbol
 
 
-def launches_per_product(d, n, P):
-    """Kernels of one FP32 product: 2D row FFT (with the gather), column
-    convolution, inverse row FFT, scatter; 3D the same around the middle stage
-    of three kernels per chunk of spectrum planes (chunks bound the middle
-    buffer, P n complex doubles per plane, to 1 GiB)."""
-    if d == 3:
-        H = P // 2 + 1
-        per_chunk = max(1, min(H, (1 << 30) // (16 * P * n)))
-        return 3 + 3 * (-(-H // per_chunk))
-    return 4
-
-
 WORKLOADS = {
     "lshape1024": "2D L-shape [-1,1]^2\\[0,1]^2, 6.05e4 vertices, 1024^2 grid in a 2048^2 circulant, alpha=1",
     "graded2048": "2D graded unit disk, 2.1e5 vertices, 2048^2 grid in a 4096^2 circulant, alpha=1.2",
@@ -72,12 +66,11 @@ WORKLOADS = {
     "batch48": "48 instances (16 ring disks + 16 L-shapes, 5e3-1.5e5 vertices log-uniform, alpha cycling "
                "0.5/1/1.5, grids 256^2-2048^2) x 8 right-hand sides (f=1 + 7 Gaussian bumps, width 0.1)",
 }
-# DRAM bytes per launch of each product kernel (dram__bytes_read.sum +
-# dram__bytes_write.sum) from one `ncu --set full` capture of the current
-# kernels; profiles/product_kernels_lshape1024_fp32.md gives the command.
-NCU_DRAM_BYTES = {
-    "lshape1024": {"gather_row_fft": 19200256, "col_fft_conv": 12679936, "row_ifft": 8424192, "scatter": 22079744},
-}
+# DRAM bytes of one FP32 L-shape product (dram__bytes_read.sum +
+# dram__bytes_write.sum summed over its kernels), from an ncu capture of this
+# build that keeps L2 between kernels (--cache-control none) after the same
+# 256 MB L2 flush the timed loop does; None until captured for these kernels.
+NCU_PRODUCT_DRAM_BYTES = {"lshape1024": None}
 BATCH_METRIC = "batched block-PCG: right-hand sides solved to rel-res 1e-8 per second (mixed), 1 GB300"
 BATCH_RHS = 8
 
@@ -217,6 +210,61 @@ def run_reference(args):
     return 0
 
 
+def ball_solves(dev, prob=None):
+    """The 3D ball configuration: mixed vs FP64 PCG to 1e-8, f = 1, and the
+    error against the closed form u = C (1 - |x|^2)^(3/4), C = 0.300901
+    (alpha = 1.5, d = 3)."""
+    import torch
+    from paper_2307_14437_gb300 import Problem
+    v, s, alpha, h, lo, hi = workload("ball256")
+    own = prob is None
+    row = {}
+    if own:
+        t1 = time.perf_counter()
+        prob = Problem(v, s, alpha, h, lo, hi)
+        row["setup_s"] = round(time.perf_counter() - t1, 3)
+        prob.autotune(nb=1)
+    f3 = torch.ones(prob.n_grid, dtype=torch.float64, device=dev)
+    for mode in ("mixed", "fp64"):
+        prob.solve(f3, mode=mode, tol=1e-8)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        u3, info3 = prob.solve(f3, mode=mode, tol=1e-8)
+        torch.cuda.synchronize()
+        row[mode] = {"s": round(time.perf_counter() - t1, 5), "inner_iters": info3["inner_iters"],
+                     "outer_iters": info3["outer_iters"], "rel_res_fp64": info3["rel_res_fp64"]}
+        ex = 0.300901 * np.maximum(0.0, 1.0 - np.sum(v ** 2, axis=1)) ** 0.75
+        row[mode]["rel_l2_err_vs_closed_form"] = float(np.linalg.norm(u3.cpu().numpy() - ex) / np.linalg.norm(ex))
+    row["speedup_mixed_vs_fp64"] = round(row["fp64"]["s"] / row["mixed"]["s"], 3)
+    row["vertices"] = len(v)
+    if own:
+        prob.close()
+    return row
+
+
+def gradient_times(dev, pg, vg, ft):
+    """The differentiation configuration: L = 1/2 ||u - u_target||^2 with
+    u = S^{-1} h^{2s} D_h f (vertex data f = 1), u_target the solve of
+    f_target; time of the forward solve and of the adjoint (its solve and
+    dL/df, dL/dX), both mixed precision to 1e-10."""
+    import torch
+    u_t, _ = pg.solve(ft, rhs="vertex", mode="mixed", tol=1e-10)
+    f = torch.ones(len(vg), dtype=torch.float64, device=dev)
+    for _ in range(2):                                   # the first round warms
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        u, fi = pg.solve(f, rhs="vertex", mode="mixed", tol=1e-10)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        gf, gx, ai = pg.adjoint(f, u, u - u_t, mode="mixed", tol=1e-10)
+        torch.cuda.synchronize()
+        t3 = time.perf_counter()
+    return {"forward_s": round(t2 - t1, 5), "adjoint_s": round(t3 - t2, 5), "total_s": round(t3 - t1, 5),
+            "forward_inner_iters": fi["inner_iters"], "adjoint_inner_iters": ai["inner_iters"],
+            "grad_f_entries": int(gf.numel()), "grad_X_entries": int(gx.numel()),
+            "finite": bool(torch.isfinite(gf).all() and torch.isfinite(gx).all())}
+
+
 def run_gofd(args):
     import torch
     from paper_2307_14437_gb300 import Problem
@@ -275,35 +323,44 @@ def run_gofd(args):
     stages = {}
     for i in range(max(10, min(args.steps, 100))):
         flush.fill_(float(i))
-        for name, t in prob.apply_interior_profiled(x, y):
+        prof = prob.apply_interior_profiled(x, y)
+        kernels_per_product = len(prof)          # one event pair per kernel launch
+        for name, t in prof:
             stages.setdefault(name, []).append(t)
     stage_ms = {k: statistics.mean(vv) for k, vv in stages.items()}
-    dom = max(stage_ms, key=stage_ms.get)
+    dom = max(stage_ms, key=stage_ms.get)   # slowest stage (events between kernels)
     H = P // 2 + 1
     n = inf["n"][0]
     # algorithmic bytes per launch of each kernel (FP32)
     nl = n ** (d - 1)
+    # algorithmic bytes of each stage, the SURVEY 8(d) terms it accounts for
+    # (FFT-internal spectrum passes excluded): ELL, x, v; v, FFT output; the
+    # symbol; FFT output read at the located nodes, I^T, y
     kbytes = {
-        "gather_row_fft": (d + 1) * 8 * n_loc + 4 * nint + 8 * nl * H,
         "gather": (d + 1) * 8 * n_loc + 4 * nint + 4 * n ** d,
-        "row_fft": 4 * n ** d + 8 * nl * H,
-        "col_fft_conv": 8 * n * H * 2 + 4 * H * H,
-        "row_ifft": 8 * nl * H + 4 * n ** d,
-        "scatter": inf["nnz_t"] * 8 + 4 * (nint + 1) + 4 * inf["nnz_t"] + 4 * nint,
-        "axis12_conv": 2 * 8 * nl * H + 4 * H ** 3,   # planes read and written, symbol; middle buffer in L2
-        "symbol_mul": 2 * 8 * H + 4 * H,
+        "gather_row_fft": (d + 1) * 8 * n_loc + 4 * nint + 4 * n ** d,
+        "row_fft": 4 * n ** d,
+        "col_fft_conv": 4 * H ** d,
+        "axis12_conv": 4 * H ** d,
+        "symbol_mul": 4 * H ** d,
+        "row_ifft": 4 * n ** d,
+        "scatter": 4 * n_loc + (d + 1) * 8 * n_loc + 4 * (n_v + 1) + 4 * nint,
     }
     pk = peaks()
     hbm = pk.get("hbm_gbs", 6800.0)
-    achieved = kbytes[dom] / (stage_ms[dom] * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                "frac": round(achieved / hbm, 4), "traffic": NCU_DRAM_BYTES.get(args.workload, {}).get(dom),
-                "traffic_source": "ncu --set full, one launch (profiles/)" if dom in NCU_DRAM_BYTES.get(
-                    args.workload, {}) else None,
-                "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)" if "hbm_gbs" in pk else "fallback 6.8 TB/s",
+    achieved = B32 / (ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "stiffness product (%d kernels: %s)" % (len(stage_ms), ", ".join(stage_ms)),
+                "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                "traffic": NCU_PRODUCT_DRAM_BYTES.get(args.workload),
+                "bytes_alg": B32, "ms_per_product": round(ms, 5),
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy), of measured" if "hbm_gbs" in pk
+                else "fallback 6.8 TB/s",
                 "stage_ms": {k: round(vv, 5) for k, vv in stage_ms.items()},
-                "stage_GBps": {k: round(kbytes[k] / (stage_ms[k] * 1e-3) / 1e9, 1) for k in stage_ms if k in kbytes},
-                "matvec_B_alg_bytes": B32, "matvec_frac": round(B32 / (ms * 1e-3) / 1e9 / hbm, 4)}
+                "stage_note": "events after every kernel (no launch overlap between stages); 2 us timer steps"}
+    dominant = {"kernel": dom, "ms": round(stage_ms[dom], 5), "bytes_alg": kbytes.get(dom),
+                "achieved": round(kbytes[dom] / (stage_ms[dom] * 1e-3) / 1e9, 1) if dom in kbytes else None,
+                "unit": "GB/s", "frac": round(kbytes[dom] / (stage_ms[dom] * 1e-3) / 1e9 / hbm, 4)
+                if dom in kbytes else None}
 
     # end to end through the host-buffer C-ABI call (pinned host memory)
     u_h = torch.empty(n_v, dtype=torch.float32, pin_memory=True)
@@ -423,6 +480,8 @@ def run_gofd(args):
                                                  "inner_iters": info["inner_iters"],
                                                  "outer_iters": info["outer_iters"],
                                                  "rel_res_fp64": info["rel_res_fp64"]}
+        row["gradients dL/df, dL/dX"] = gradient_times(dev, pg, vg, ft)
+        row["gradients dL/df, dL/dX, diagonal precond"] = gradient_times(dev, pj, vg, ft)
         pj.close()
         pcg["graded disk 2048^2 alpha=1.2, f_target vertex data"] = row
         if pg is not prob:
@@ -469,22 +528,17 @@ def run_gofd(args):
             "rel_l2_err_vs_closed_form": float(np.linalg.norm(err) / np.linalg.norm(ex))}
         p1.close()
     if not args.no_pcg and args.workload == "ball256":
-        # the ball configuration: mixed vs FP64 PCG to 1e-8, f = 1, and the
-        # closed form u = C (1 - |x|^2)^(3/4), C = 0.300901 (alpha = 1.5, d = 3)
-        f3 = torch.ones(prob.n_grid, dtype=torch.float64, device=dev)
-        row = {}
-        for mode in ("mixed", "fp64"):
-            prob.solve(f3, mode=mode, tol=1e-8)
-            torch.cuda.synchronize()
-            t1 = time.perf_counter()
-            u3, info3 = prob.solve(f3, mode=mode, tol=1e-8)
-            torch.cuda.synchronize()
-            row[mode] = {"s": round(time.perf_counter() - t1, 5), "inner_iters": info3["inner_iters"],
-                         "outer_iters": info3["outer_iters"], "rel_res_fp64": info3["rel_res_fp64"]}
-        row["speedup_mixed_vs_fp64"] = round(row["fp64"]["s"] / row["mixed"]["s"], 3)
-        ex = 0.300901 * np.maximum(0.0, 1.0 - np.sum(v ** 2, axis=1)) ** 0.75
-        row["rel_l2_err_vs_closed_form"] = float(np.linalg.norm(u3.cpu().numpy() - ex) / np.linalg.norm(ex))
-        pcg["ball 256^3 alpha=1.5 f=1"] = row
+        pcg["ball 256^3 alpha=1.5 f=1"] = ball_solves(dev, prob)
+    if not args.no_pcg and args.workload == "lshape1024":
+        # the 3D ball configuration and the batched configuration beside the L-shape line
+        t1 = time.perf_counter()
+        pcg["ball 256^3 alpha=1.5 f=1"] = ball_solves(dev)
+        pcg["ball 256^3 alpha=1.5 f=1"]["wall_s"] = round(time.perf_counter() - t1, 2)
+        t1 = time.perf_counter()
+        batch = batch_workload(dev, rank, world, warm=1, steps=1, single="sampled")
+        batch["wall_s"] = round(time.perf_counter() - t1, 2)
+    else:
+        batch = None
     clk = clocks.stop()
 
     if rank == 0:
@@ -501,8 +555,9 @@ def run_gofd(args):
                                              "scatter_lanes": inf["tune_scatter_lanes"],
                                              "col_elems": inf["tune_col_elems"],
                                              "row_elems": inf["tune_row_elems"]}},
-                "roofline": roofline, "roofline_fp64_product": roofline_fp64, "e2e": e2e, "pcg": pcg,
-                "gpu_launches": launches_per_product(d, inf["n"][0], P) * args.steps, "clocks": clk}
+                "roofline": roofline, "dominant_kernel": dominant, "roofline_fp64_product": roofline_fp64,
+                "e2e": e2e, "pcg": pcg, "batch": batch,
+                "gpu_launches": kernels_per_product * args.steps, "clocks": clk}
         if world == 1 and not args.no_cpu and args.workload == "lshape1024":
             try:
                 line["cpu_baseline"] = cpu_baseline()[1]
@@ -536,19 +591,15 @@ def batch_grid_nodes(a_h):
     return 2048
 
 
-def run_batch(args):
-    """The batched workload: every instance solves its 8 right-hand sides with
-    lock-step block PCG (FP32 inner, FP64 refinement, autotuned launch shapes),
-    all instances concurrently on their own streams.  A step is the whole
-    batch.  Compared with one right-hand side at a time in plain FP64 PCG."""
+def batch_workload(dev, rank, world, warm=1, steps=1, single="sampled"):
+    """The batched workload: 48 instances x 8 right-hand sides.  Instances on
+    one overlay grid form a Group (all their columns in one lock-step block
+    PCG, FP32 inner, FP64 refinement, launch shapes from the group autotuner);
+    the groups run concurrently.  A step is the whole batch.  Beside it, one
+    right-hand side at a time in plain FP64 PCG: all 384 (single="all"), or
+    column i mod 8 of instance i, scaled by 8 (single="sampled")."""
     import torch
-    from paper_2307_14437_gb300 import Problem, solve_many
-    rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
+    from paper_2307_14437_gb300 import Group, Problem, grid_key, solve_many
     all_specs = mg.batch_instances()
     specs = shard(all_specs, rank, world)              # instances are independent: shard, no collective
     meshes, probs, Fs, rows = {}, [], [], []
@@ -570,23 +621,27 @@ def run_batch(args):
         rows.append({"kind": sp["kind"], "n_v": len(v), "n": n, "alpha": sp["alpha"], "setup_s": round(t_setup, 3)})
     t_build = time.perf_counter() - t0
     t1 = time.perf_counter()
-    for pr, r in zip(probs, rows):
-        r["tuned_ms_per_product"] = round(pr.autotune(nb=BATCH_RHS), 4)
-        r["batch_chunk"] = pr.info()["tune_batch_chunk"]
+    members = {}
+    for i, pr in enumerate(probs):
+        members.setdefault(grid_key(pr), []).append(i)
+    groups, gtune = {}, {}
+    for key, idx in members.items():
+        groups[key] = Group([probs[i] for i in idx], BATCH_RHS)
+        gtune[f"{key[1][0]}^2 ({len(idx)} instances)"] = round(groups[key].autotune(), 4)
+    for pr in probs:                                     # shapes of the one-at-a-time solves
+        pr.autotune(nb=1)
     t_tune = time.perf_counter() - t1
     torch.cuda.synchronize()
 
-    warm, steps = max(1, min(args.warmup, 1)), max(1, min(args.steps, 2))
     for _ in range(warm):
-        solve_many(probs, Fs, mode="mixed", tol=1e-8)
-    clocks = Clocks(local)
+        solve_many(probs, Fs, mode="mixed", tol=1e-8, groups=groups)
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     for _ in range(steps):
-        out = solve_many(probs, Fs, mode="mixed", tol=1e-8)
+        out = solve_many(probs, Fs, mode="mixed", tol=1e-8, groups=groups)
     torch.cuda.synchronize()
     t_batch = (time.perf_counter() - t1) / steps
     worst = max(i["rel_res_fp64"] for _, infos in out for i in infos)
@@ -599,7 +654,7 @@ def run_batch(args):
     torch.cuda.synchronize()
     t1 = time.perf_counter()
     Fd = [f.to(dev, non_blocking=True) for f in Fh]
-    res = solve_many(probs, Fd, mode="mixed", tol=1e-8)
+    res = solve_many(probs, Fd, mode="mixed", tol=1e-8, groups=groups)
     for u_h, (U, _) in zip(Uh, res):
         u_h.copy_(U, non_blocking=True)
     torch.cuda.synchronize()
@@ -607,11 +662,14 @@ def run_batch(args):
 
     # one right-hand side at a time, plain FP64 PCG (no batching, no refinement)
     t1 = time.perf_counter()
-    for pr, F in zip(probs, Fs):
-        for c in range(BATCH_RHS):
+    n_single = 0
+    for i, (pr, F) in enumerate(zip(probs, Fs)):
+        cols = range(BATCH_RHS) if single == "all" else ((i + rank) % BATCH_RHS,)
+        for c in cols:
             pr.solve(F[c].contiguous(), mode="fp64", tol=1e-8)
+            n_single += 1
     torch.cuda.synchronize()
-    t_single = time.perf_counter() - t1
+    t_single = (time.perf_counter() - t1) * (len(probs) * BATCH_RHS / max(1, n_single))
 
     # the batched FP32 product of the largest instance against the HBM roofline
     big = max(range(len(probs)), key=lambda i: rows[i]["n"] * 1e9 + rows[i]["n_v"])
@@ -622,6 +680,7 @@ def run_batch(args):
     X[:, :ld - 1] = torch.rand((BATCH_RHS, ld - 1), device=dev) * 2 - 1
     Y = torch.empty_like(X)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    pr.autotune(nb=BATCH_RHS)
     for _ in range(3):
         pr.apply_interior_batch(X, Y)
     st = torch.cuda.current_stream()
@@ -636,34 +695,61 @@ def run_batch(args):
     B = BATCH_RHS * b_alg(2, inf["n_loc"], inf["n_v"], inf["n_grid"], inf["P"], 4) \
         - (BATCH_RHS - 1) * 4 * (inf["P"] // 2 + 1) ** 2        # the symbol is read once per batch
     hbm = peaks().get("hbm_gbs", 6800.0)
-    clk = clocks.stop()
     nsolves = len(all_specs) * BATCH_RHS                # all ranks together
     t_max = max_over_ranks(t_batch, world, dev)
     t_single = max_over_ranks(t_single, world, dev)
     t_e2e = max_over_ranks(t_e2e, world, dev)
-    if rank == 0:
-        line = {"metric": BATCH_METRIC, "value": round(nsolves / t_max, 3), "unit": "solves/s", "n_gpus": world,
-                "steps": steps, "warmup": warm, "ms_per_step": round(1e3 * t_max, 2), "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 refinement)",
-                "data": "synthetic (seeded jittered Delaunay disks and L-shapes, f=1 + Gaussian bumps)",
-                "config": {"workload": WORKLOADS["batch48"], "instances": len(probs), "rhs_per_instance": BATCH_RHS,
-                           "grids": {str(k): sum(r["n"] == k for r in rows) for k in (256, 512, 1024, 2048)},
-                           "l2": "inputs larger than L2 for the large instances; no flush between solves",
-                           "build_s": round(t_build, 2), "autotune_s": round(t_tune, 2)},
-                "worst_rel_res_fp64": worst,
-                "one_at_a_time_fp64": {"s": round(t_single, 3), "solves_per_s": round(nsolves / t_single, 3),
-                                       "speedup_batched_mixed": round(t_single / t_batch, 3)},
-                "e2e": {"value": round(nsolves / t_e2e, 3), "unit": "solves/s",
-                        "h2d_bytes_per_step": int(sum(f.numel() * 8 for f in Fh)),
-                        "d2h_bytes_per_step": int(sum(u.numel() * 8 for u in Uh))},
-                "roofline": {"bound": "hbm", "kernel": "batched FP32 product (8 columns), largest instance",
-                             "instance": rows[big], "achieved": round(B / (ms * 1e-3) / 1e9, 1), "peak": hbm,
-                             "unit": "GB/s", "frac": round(B / (ms * 1e-3) / 1e9 / hbm, 4), "traffic": None,
-                             "ms": round(ms, 4)},
-                "instances": rows, "clocks": clk}
-        print(json.dumps(line), flush=True)
+    result = {
+        "solves_per_s": round(nsolves / t_max, 3), "s_per_batch": round(t_max, 4), "steps": steps, "warmup": warm,
+        "worst_rel_res_fp64": worst,
+        "config": {"workload": WORKLOADS["batch48"], "instances": len(all_specs), "rhs_per_instance": BATCH_RHS,
+                   "grids": {str(k): sum(r["n"] == k for r in rows) for k in (256, 512, 1024, 2048)},
+                   "groups": gtune, "group_note": "Group autotune ms per product of all the group's columns",
+                   "l2": "inputs larger than L2 for the large instances; no flush between solves",
+                   "build_s": round(t_build, 2), "autotune_s": round(t_tune, 2)},
+        "one_at_a_time_fp64": {
+            "s": round(t_single, 3), "solves_per_s": round(nsolves / t_single, 3),
+            "speedup_batched_mixed": round(t_single / t_max, 3),
+            "sample": "all %d right-hand sides" % nsolves if single == "all" else
+            "%d solves (column i mod 8 of instance i), time scaled by 8 to the %d right-hand sides"
+            % (n_single, len(probs) * BATCH_RHS)},
+        "e2e": {"value": round(nsolves / t_e2e, 3), "unit": "solves/s",
+                "h2d_bytes_per_step": int(sum(f.numel() * 8 for f in Fh)),
+                "d2h_bytes_per_step": int(sum(u.numel() * 8 for u in Uh))},
+        "roofline": {"bound": "hbm", "kernel": "batched FP32 product (8 columns), largest instance",
+                     "instance": rows[big], "achieved": round(B / (ms * 1e-3) / 1e9, 1), "peak": hbm,
+                     "unit": "GB/s", "frac": round(B / (ms * 1e-3) / 1e9 / hbm, 4), "traffic": None,
+                     "ms": round(ms, 4)},
+        "instances": rows}
+    for g in groups.values():
+        g.close()
     for pr in probs:
         pr.close()
+    return result
+
+
+def run_batch(args):
+    """The batched workload as its own line (all 384 one-at-a-time solves)."""
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    clocks = Clocks(local)
+    r = batch_workload(dev, rank, world, warm=max(1, min(args.warmup, 1)), steps=max(1, min(args.steps, 2)),
+                       single="all")
+    clk = clocks.stop()
+    if rank == 0:
+        line = {"metric": BATCH_METRIC, "value": r["solves_per_s"], "unit": "solves/s", "n_gpus": world,
+                "steps": r["steps"], "warmup": r["warmup"], "ms_per_step": round(1e3 * r["s_per_batch"], 2),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (FP64 refinement)",
+                "data": "synthetic (seeded jittered Delaunay disks and L-shapes, f=1 + Gaussian bumps)",
+                "config": r["config"], "worst_rel_res_fp64": r["worst_rel_res_fp64"],
+                "one_at_a_time_fp64": r["one_at_a_time_fp64"], "e2e": r["e2e"], "roofline": r["roofline"],
+                "instances": r["instances"], "clocks": clk}
+        print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.barrier()

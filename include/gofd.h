@@ -210,7 +210,9 @@ gofd_status gofd_apply_interior_batch(gofd_problem* p, gofd_precision prec, int 
  * recorded on `stream` after each kernel of the product; on return (the
  * stream is synchronised) stage_ms[i] holds the time of stage i in ms and
  * stage_names[i] (if stage_names is not NULL) a static name; *n_stages is the
- * number of stages written (at most cap).  For measurement only.
+ * number of stages written (at most cap; the first 32 kernels of a product are
+ * marked).  One stage per kernel launch, so *n_stages counts the launches of a
+ * product of up to 32 kernels.  For measurement only.
  */
 gofd_status gofd_apply_interior_profiled(gofd_problem* p, gofd_precision prec, const void* x_dev,
                                          void* y_dev, void* stream, float* stage_ms,

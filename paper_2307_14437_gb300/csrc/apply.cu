@@ -577,14 +577,15 @@ void setup_apply(gofd_problem* p) {
 // Optional stage markers: when non-null, an event is recorded on the stream
 // after every launch of the product (used by gofd_apply_interior_profiled).
 struct StageEvents {
-    cudaEvent_t ev[8];
-    const char* name[8];
+    static constexpr int kMax = 32;
+    cudaEvent_t ev[kMax];
+    const char* name[kMax];
     int n = 0;
 };
 static thread_local StageEvents* g_marks = nullptr;
 
 void mark_stage(cudaStream_t st, const char* name) {
-    if (!g_marks || g_marks->n >= 8) return;
+    if (!g_marks || g_marks->n >= StageEvents::kMax) return;
     GOFD_CUDA_TRY(cudaEventRecord(g_marks->ev[g_marks->n], st));
     g_marks->name[g_marks->n++] = name;
 }
@@ -702,7 +703,7 @@ void apply_interior(gofd_problem* p, bool fp64, const void* x, void* y, cudaStre
 int apply_interior_profiled(gofd_problem* p, bool fp64, const void* x, void* y, cudaStream_t st, float* ms,
                             const char** names, int cap) {
     StageEvents se;
-    for (int i = 0; i < 8; ++i) GOFD_CUDA_TRY(cudaEventCreate(&se.ev[i]));
+    for (int i = 0; i < StageEvents::kMax; ++i) GOFD_CUDA_TRY(cudaEventCreate(&se.ev[i]));
     cudaEvent_t start;
     GOFD_CUDA_TRY(cudaEventCreate(&start));
     GOFD_CUDA_TRY(cudaEventRecord(start, st));
@@ -722,7 +723,7 @@ int apply_interior_profiled(gofd_problem* p, bool fp64, const void* x, void* y, 
         if (names) names[i] = se.name[i];
         prev = se.ev[i];
     }
-    for (int i = 0; i < 8; ++i) cudaEventDestroy(se.ev[i]);
+    for (int i = 0; i < StageEvents::kMax; ++i) cudaEventDestroy(se.ev[i]);
     cudaEventDestroy(start);
     return n;
 }

@@ -175,11 +175,11 @@ class Problem:
         """apply_interior with per-stage CUDA-event times: returns [(name, ms), ...]."""
         torch = _torch()
         prec = "fp64" if x.dtype == torch.float64 else "fp32"
-        ms = (C.c_float * 8)()
-        names = (C.c_char_p * 8)()
+        ms = (C.c_float * 32)()
+        names = (C.c_char_p * 32)()
         cnt = C.c_int(0)
         self._check(self._lib.gofd_apply_interior_profiled(self._h, _PREC[prec], _ptr(x), _ptr(y),
-                                                           _stream_ptr(stream), ms, names, 8, C.byref(cnt)))
+                                                           _stream_ptr(stream), ms, names, 32, C.byref(cnt)))
         return [(names[i].decode(), float(ms[i])) for i in range(cnt.value)]
 
     def apply_host(self, u: np.ndarray, op: str = "stiffness", out: np.ndarray | None = None, stream=None):

@@ -50,12 +50,3 @@ def test_batch_grid_rule():
             n_of[key] = bench.batch_grid_nodes(bench._min_height(v, s))
         counts[n_of[key]] += 1
     assert dict(counts) == {512: 6, 1024: 20, 2048: 22}
-
-
-def test_launches_per_product():
-    # 2D: four kernels; 3D 256^3 (P = 512): the middle stage fits one chunk
-    # (257 planes of 2 MB), 3 + 3 kernels; 3D 513^3 (P = 1024): 513 planes of
-    # 8.4 MB in chunks of 127, 3 + 3 x 5
-    assert bench.launches_per_product(2, 1024, 2048) == 4
-    assert bench.launches_per_product(3, 256, 512) == 6
-    assert bench.launches_per_product(3, 513, 1024) == 18

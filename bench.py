@@ -593,13 +593,14 @@ def batch_grid_nodes(a_h):
 
 def batch_workload(dev, rank, world, warm=1, steps=1, single="sampled"):
     """The batched workload: 48 instances x 8 right-hand sides.  Instances on
-    one overlay grid form a Group (all their columns in one lock-step block
-    PCG, FP32 inner, FP64 refinement, launch shapes from the group autotuner);
+    one overlay grid at one alpha form a Group (all their columns in one
+    lock-step block PCG, FP32 inner, FP64 refinement, converged columns
+    skipped by the product kernels, launch shapes from the group autotuner);
     the groups run concurrently.  A step is the whole batch.  Beside it, one
     right-hand side at a time in plain FP64 PCG: all 384 (single="all"), or
     column i mod 8 of instance i, scaled by 8 (single="sampled")."""
     import torch
-    from paper_2307_14437_gb300 import Group, Problem, grid_key, solve_many
+    from paper_2307_14437_gb300 import Group, Problem, group_key, solve_many
     all_specs = mg.batch_instances()
     specs = shard(all_specs, rank, world)              # instances are independent: shard, no collective
     meshes, probs, Fs, rows = {}, [], [], []
@@ -623,11 +624,11 @@ def batch_workload(dev, rank, world, warm=1, steps=1, single="sampled"):
     t1 = time.perf_counter()
     members = {}
     for i, pr in enumerate(probs):
-        members.setdefault(grid_key(pr), []).append(i)
+        members.setdefault(group_key(pr), []).append(i)
     groups, gtune = {}, {}
     for key, idx in members.items():
         groups[key] = Group([probs[i] for i in idx], BATCH_RHS)
-        gtune[f"{key[1][0]}^2 ({len(idx)} instances)"] = round(groups[key].autotune(), 4)
+        gtune[f"{key[1][0]}^2 alpha={key[4]} ({len(idx)} instances)"] = round(groups[key].autotune(), 4)
     for pr in probs:                                     # shapes of the one-at-a-time solves
         pr.autotune(nb=1)
     t_tune = time.perf_counter() - t1

@@ -264,12 +264,13 @@ __global__ void __launch_bounds__(256) scatter_kernel(const int32_t* __restrict_
                                                       const Real* __restrict__ val, const Real* __restrict__ w,
                                                       int64_t nint, Real* __restrict__ y, Real scale, int64_t ws,
                                                       int64_t ys, unsigned nshort, LongRows lr, Real* partial,
-                                                      unsigned* counters) {
+                                                      unsigned* counters, GroupArg ga) {
     pdl_trigger();
     w += blockIdx.y * ws;
     y += blockIdx.y * ys;
     if (blockIdx.x >= nshort) {
         pdl_wait();
+        if (column_skipped(ga)) return;
         __shared__ Real part[256];
         __shared__ bool last;
         const int64_t c = blockIdx.x - nshort;
@@ -328,6 +329,7 @@ __global__ void __launch_bounds__(256) scatter_kernel(const int32_t* __restrict_
     bounds(t0);
     first4();
     pdl_wait();
+    if (column_skipped(ga)) return;
     for (; t0 < nint * TPR; t0 += nthreads) {
         if (t0 != gid - (threadIdx.x & 31)) {
             bounds(t0);
@@ -394,6 +396,7 @@ __global__ void __launch_bounds__(PACK_THREADS) scatter_packed_kernel(
     if (blockIdx.x >= npack) {
         pdl_trigger();
         pdl_wait();
+        if (column_skipped(ga)) return;
         __shared__ Real part[256];
         __shared__ bool last;
         const int64_t c = blockIdx.x - npack;
@@ -433,6 +436,7 @@ __global__ void __launch_bounds__(PACK_THREADS) scatter_packed_kernel(
     }
     pdl_trigger();
     pdl_wait();
+    if (column_skipped(ga)) return;
 #pragma unroll
     for (int j = 0; j < PER; ++j)
         if (cc[j] >= 0) pr[threadIdx.x + PACK_THREADS * j] = vv[j] * __ldg(&w[cc[j]]);
@@ -672,7 +676,7 @@ static void scatter_b(gofd_problem* p, const Real* wgrid, Real* y, Real scale, i
     const dim3 grid(nshort + (unsigned)p->n_long_chunks, nb);
 #define SCAT(TPR)                                                                                              \
     launch_pdl(scatter_kernel<Real, TPR>, grid, dim3(threads), 0, st, p->csr_ptr.as<int32_t>(),                   \
-               p->csr_col.as<int32_t>(), val, wgrid, p->nint, y, scale, ws, ys, nshort, lr, part, cnt)
+               p->csr_col.as<int32_t>(), val, wgrid, p->nint, y, scale, ws, ys, nshort, lr, part, cnt, ga)
     if (tpr == 32) SCAT(32);
     else if (tpr == 16) SCAT(16);
     else if (tpr == 8) SCAT(8);
@@ -732,7 +736,8 @@ int apply_interior_profiled(gofd_problem* p, bool fp64, const void* x, void* y, 
 // slot zero), Y[b] = y + b ld.  2D: one launch sequence over the batch with
 // the scratch of the batch workspace; otherwise one product per vector.
 void apply_interior_batch(gofd_problem* p, bool fp64, const void* x, void* y, int nb, int64_t ld, void* grid_ws,
-                          void* spec_ws, void* partial_ws, void* counter_ws, cudaStream_t st) {
+                          void* spec_ws, void* partial_ws, void* counter_ws, cudaStream_t st, const int* skip,
+                          int skip_stride) {
     if (p->d == 2) {
         // columns in sub-batches of p->tune_bchunk (0: all at once); each
         // sub-batch reuses the first workspace slots, so a small one keeps its
@@ -744,14 +749,18 @@ void apply_interior_batch(gofd_problem* p, bool fp64, const void* x, void* y, in
             const int k = std::min(cs, nb - c0);
             const char* xc = (const char*)x + (int64_t)c0 * ld * b;
             char* yc = (char*)y + (int64_t)c0 * ld * b;
+            GroupArg ga;
+            ga.skip = skip;
+            ga.skip_stride = skip_stride;
+            ga.col0 = c0;
             if (fp64) {
-                afd_2d_f64(p, (const double*)xc, nullptr, (double*)grid_ws, k, ld, ws, spec_ws, st);
+                afd_2d_f64(p, (const double*)xc, nullptr, (double*)grid_ws, k, ld, ws, spec_ws, st, ga);
                 scatter_b<double>(p, (const double*)grid_ws, (double*)yc, 1.0, k, ws, ld, (double*)partial_ws,
-                                  (unsigned*)counter_ws, st);
+                                  (unsigned*)counter_ws, st, ga);
             } else {
-                afd_2d_f32(p, (const float*)xc, nullptr, (float*)grid_ws, k, ld, ws, spec_ws, st);
+                afd_2d_f32(p, (const float*)xc, nullptr, (float*)grid_ws, k, ld, ws, spec_ws, st, ga);
                 scatter_b<float>(p, (const float*)grid_ws, (float*)yc, 1.0f, k, ws, ld, (float*)partial_ws,
-                                 (unsigned*)counter_ws, st);
+                                 (unsigned*)counter_ws, st, ga);
             }
         }
         return;

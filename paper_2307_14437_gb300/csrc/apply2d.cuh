@@ -223,6 +223,7 @@ __global__ void __launch_bounds__(MAXT, MINB) row_fwd_t_kernel(
             }
     }
     pdl_wait();
+    if (column_skipped(ga)) return;
     // pass-0 inputs z[m] = (v[2m], v[2m+1]) gathered straight into registers
     C v[E];
     if (vgrid || rs.n > 2) {
@@ -327,6 +328,7 @@ __global__ void __launch_bounds__(MAXT, MINB) col_conv_t_kernel(typename Cplx<Re
                                                        const Real* __restrict__ lamT, int64_t sstride, int pm,
                                                        int64_t col0, GroupArg ga) {
     pdl_enter();
+    if (column_skipped(ga)) return;
     if (ga.iv) {
         const InstView& I = ga.iv[blockIdx.y / ga.nbper];
         lamT = sizeof(Real) == 4 ? reinterpret_cast<const Real*>(I.lamT32) : reinterpret_cast<const Real*>(I.lamT64);
@@ -380,8 +382,9 @@ template <class Real, int N, int E, int MAXT = 512, int MINB = 1>
 __global__ void __launch_bounds__(MAXT, MINB) row_inv_t_kernel(const typename Cplx<Real>::T* __restrict__ specT, int ld,
                                                       int nlines, int n, const typename Cplx<Real>::T* __restrict__ tw,
                                                       Real* __restrict__ wgrid, int lpc, int64_t sstride,
-                                                      int64_t wstride) {
+                                                      int64_t wstride, GroupArg ga) {
     pdl_enter();
+    if (column_skipped(ga)) return;
     using C = typename Cplx<Real>::T;
     specT += blockIdx.y * sstride;
     wgrid += blockIdx.y * wstride;

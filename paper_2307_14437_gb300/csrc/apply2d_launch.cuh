@@ -97,7 +97,7 @@ void run_e(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, int n
                p->ldT, n, H, H, tw, lamT, sb, 0, (int64_t)0, ga);
     mark_stage(st, "col_fft_conv");
     launch_pdl(row_inv_t_kernel<Real, NR, ER>, dim3(rblocks, nb), dim3(lpc * tr), row_smem(NR, lpc), st, S, p->ldT,
-               nlines, n, tw, wgrid, lpc, sb, ws);
+               nlines, n, tw, wgrid, lpc, sb, ws, ga);
     mark_stage(st, "row_ifft");
 }
 

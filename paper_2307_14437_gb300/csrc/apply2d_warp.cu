@@ -221,6 +221,7 @@ __global__ void __launch_bounds__(GTH, 12) gather_w_kernel(const float* __restri
     }
     pdl_trigger();
     pdl_wait();
+    if (column_skipped(ga)) return;
     float xv[GRW][3];
 #pragma unroll
     for (int q = 0; q < GRW; ++q)
@@ -281,6 +282,7 @@ __global__ void __launch_bounds__(128, 3) row_fwd_w_kernel(
         prefetch_share(pf2, pb2, blockIdx.x, gridDim.x);
         prefetch_share(pf3, pb3, blockIdx.x, gridDim.x);
     }
+    if (column_skipped(ga)) return;
     // z[t + 32 r] = (v[2t + 64 r], v[2t + 64 r + 1]); z[m] = 0 for m >= 512 (n <= 1024)
     float2 z[32];
     const float* vl = vgrid + (int64_t)line * n;
@@ -349,6 +351,7 @@ __global__ void __launch_bounds__(64, 7) col_conv_w_kernel(float2* __restrict__ 
     const float* lc = lamT + (int64_t)col * WH;
     for (int i = threadIdx.x; i < WH; i += 64) lb[i] = __ldcg(&lc[i]);
     pdl_wait();
+    if (column_skipped(ga)) return;
 #pragma unroll
     for (int i = 0; i < WN / 64; ++i) {
         const int m = threadIdx.x + 64 * i;
@@ -399,7 +402,7 @@ __global__ void __launch_bounds__(128, 3) row_inv_w_kernel(const float2* __restr
                                                            int n, const float2* __restrict__ tw,
                                                            const float2* __restrict__ twp,
                                                            float* __restrict__ wgrid, int64_t sstride,
-                                                           int64_t wstride) {
+                                                           int64_t wstride, GroupArg ga) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float2* tile = reinterpret_cast<float2*>(smem_raw);   // [WH][TLD]
     const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
@@ -408,6 +411,7 @@ __global__ void __launch_bounds__(128, 3) row_inv_w_kernel(const float2* __restr
     wgrid += blockIdx.y * wstride;
     const LaneTw t = lane_twiddles(twp, tw, lane);
     pdl_wait();
+    if (column_skipped(ga)) return;
 #pragma unroll
     for (int q = 0; q < (WH * LINES + 127) / 128; ++q) {
         const int i = threadIdx.x + 128 * q;
@@ -520,7 +524,7 @@ void afd_2d_warp_f32(gofd_problem* p, const float* x, float* wgrid, int nb, int6
     launch_pdl(col_conv_w_kernel, dim3(WH, nb), dim3(64), 0, st, S, p->ldT, n, tw, twp, lam, sb, ga);
     mark_stage(st, "col_fft_conv");
     launch_pdl(row_inv_w_kernel, dim3(rblocks, nb), dim3(128), ROW_SMEM, st, (const float2*)S, p->ldT, nlines, n,
-               tw, twp, wgrid, sb, ws);
+               tw, twp, wgrid, sb, ws, ga);
     mark_stage(st, "row_ifft");
 }
 

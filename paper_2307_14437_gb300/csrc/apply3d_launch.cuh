@@ -87,7 +87,7 @@ void run3_e(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, cuda
     }
     mark_stage(st, "axis12_conv");
     launch_pdl(row_inv_t_kernel<Real, NR, ER>, dim3(rblocks), dim3(lpc * tr), row_smem3(NR, lpc), st, (const C*)S,
-               (int)ld, nlines, n, tw, wgrid, lpc, (int64_t)0, (int64_t)0);
+               (int)ld, nlines, n, tw, wgrid, lpc, (int64_t)0, (int64_t)0, GroupArg{});
     mark_stage(st, "row_ifft");
 }
 

@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstddef>
 #include <memory>
 #include <vector>
 
@@ -140,9 +141,12 @@ __global__ void bupdate_kernel(V* __restrict__ X, V* __restrict__ R, const V* __
     const V* q = Q + blockIdx.y * ld;
     double acc = 0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const V ri = (V)((double)r[i] - a * (double)q[i]);
-        x[i] = (V)((double)x[i] + a * (double)p[i]);
-        r[i] = ri;
+        V ri = r[i];
+        if (a != 0.0) {   // alpha = 0 (a converged column): q was not computed, x and r stay
+            ri = (V)((double)ri - a * (double)q[i]);
+            x[i] = (V)((double)x[i] + a * (double)p[i]);
+            r[i] = ri;
+        }
         acc += (double)ri * (double)ri;
     }
     acc = bblock_sum(acc, sh);
@@ -295,12 +299,20 @@ struct BOp {
     GroupArg ga;
     int64_t n = 0;
     gofd_problem* member(int c) const { return members ? (*members)[c / nbper] : p; }
-    void apply(bool f64, const void* X, void* Y, int nb, int64_t ld, BatchWork* w, cudaStream_t st) const {
-        if (members)
-            apply_interior_group(p, f64, X, Y, nb, ld, w->grid.ptr, w->spec.ptr, w->partial.ptr, w->counters.ptr, ga,
+    // skip: per-column flags (device; column c at skip[c * skip_stride]);
+    // a column whose flag is set is not computed (block PCG: converged)
+    void apply(bool f64, const void* X, void* Y, int nb, int64_t ld, BatchWork* w, cudaStream_t st,
+               const int* skip = nullptr, int skip_stride = 0) const {
+        if (members) {
+            GroupArg g = ga;
+            g.skip = skip;
+            g.skip_stride = skip_stride;
+            apply_interior_group(p, f64, X, Y, nb, ld, w->grid.ptr, w->spec.ptr, w->partial.ptr, w->counters.ptr, g,
                                  st);
-        else
-            apply_interior_batch(p, f64, X, Y, nb, ld, w->grid.ptr, w->spec.ptr, w->partial.ptr, w->counters.ptr, st);
+        } else {
+            apply_interior_batch(p, f64, X, Y, nb, ld, w->grid.ptr, w->spec.ptr, w->partial.ptr, w->counters.ptr, st,
+                                 skip, skip_stride);
+        }
     }
 };
 
@@ -354,8 +366,13 @@ static int bpcg(const BOp& op, BatchWork* w, int nb, V* D, V* R, V* Pd, V* Q, V*
         GOFD_CHECK_LAUNCH();
     }
     int it = 0;
+    // converged columns (BScal::done) are skipped by the product kernels:
+    // their alpha is 0 from then on, so their q is never used
+    static_assert(sizeof(BScal) % sizeof(int) == 0, "flag stride");
+    const int* done_flags = reinterpret_cast<const int*>(reinterpret_cast<const char*>(s) + offsetof(BScal, done));
+    const int done_stride = (int)(sizeof(BScal) / sizeof(int));
     auto iteration = [&]() {
-        op.apply(f64, Pd, Q, nb, ld, w, st);
+        op.apply(f64, Pd, Q, nb, ld, w, st, done_flags, done_stride);
         launch_pdl(bdot_kernel<V>, rg, dim3(BRED_THREADS), 0, st, Pd, Q, n, ld, red, cnt, s, 2);
         launch_pdl(bupdate_kernel<V>, rg, dim3(BRED_THREADS), 0, st, D, R, Pd, Q, n, ld, red, cnt, s, pc ? 1 : 0);
         if (pc) {

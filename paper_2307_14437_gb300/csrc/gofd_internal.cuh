@@ -188,7 +188,21 @@ struct GroupArg {
     int nbper = 1;                  // columns per instance
     int64_t max_nloc = 0;           // host side: largest n_loc / scatter grid over the instances
     int64_t max_scatter = 0;
+    // block PCG: column c of the launch (blockIdx.y) is left untouched when
+    // skip[(col0 + c) * skip_stride] != 0 (the column has converged; its
+    // output is not read).  nullptr: every column is computed.
+    const int* skip = nullptr;
+    int skip_stride = 0;
+    int col0 = 0;
 };
+
+// True when this CTA's column is to be left alone.  Call it after pdl_wait():
+// the flags are written by an earlier kernel of the same stream, and only
+// after the wait is that kernel known to be complete.  The flag is the same
+// for every CTA of a column, so a whole column returns or none of it.
+__device__ __forceinline__ bool column_skipped(const GroupArg& ga) {
+    return ga.skip && *(const volatile int*)(ga.skip + (int64_t)(ga.col0 + (int)blockIdx.y) * ga.skip_stride) != 0;
+}
 
 struct Precond;   // defined in precond.cu
 
@@ -349,8 +363,11 @@ int grid_blocks(int64_t work, int threads, int cap = 152 * 16);
 void sort_packed_rows(const int32_t* ptr, int64_t nrows, int64_t* packed, int64_t nnz, cudaStream_t st);
 // partial_ws: nb x n_long_chunks reals (8 bytes each), counter_ws: nb x n_long_rows
 // unsigned, zero on entry and on exit
+// skip (2D): column c is left untouched when skip[c * skip_stride] != 0
+// (device flags, read by the kernels; nullptr: every column is computed)
 void apply_interior_batch(gofd_problem* p, bool fp64, const void* x, void* y, int nb, int64_t ld, void* grid_ws,
-                          void* spec_ws, void* partial_ws, void* counter_ws, cudaStream_t st);
+                          void* spec_ws, void* partial_ws, void* counter_ws, cudaStream_t st,
+                          const int* skip = nullptr, int skip_stride = 0);
 // a group of 2D problems on one grid (apply.cu): the view of one problem, and
 // Y[c] = S_{c / nbper} X[c] for all columns of the group in one launch sequence
 InstView inst_view(const gofd_problem* p);

@@ -325,21 +325,29 @@ def grid_key(problem):
     return (inf["d"], tuple(inf["n"]), inf["P"], float(problem.h))
 
 
+def group_key(problem):
+    """The partition solve_many uses: one overlay grid and one alpha.  Columns
+    of one alpha need similar iteration counts (the condition number grows
+    with alpha), so a lock-step group wastes little on columns that finish
+    early, and its members share one symbol."""
+    return grid_key(problem) + (float(problem.alpha),)
+
+
 def solve_many(problems, batches, rhs: str = "grid", mode: str = "mixed", tol: float = 1e-8,
                maxit: int = 100000, groups=None):
     """Independent problems solved together.  2D problems are grouped by grid
-    (grid_key): each group is solved as one Group (all its columns in one
-    block PCG); groups, and problems of other dimensions (solve_batch), run
-    concurrently, one host thread and stream each (the C calls release the
-    interpreter lock).  groups: optional dict key -> Group built earlier for
-    these problems (reused; keeps its tuned launch shapes).  Returns the list
-    of (U, infos) in the problems' order."""
+    and alpha (group_key): each group is solved as one Group (all its columns
+    in one block PCG); groups, and problems of other dimensions (solve_batch),
+    run concurrently, one host thread and stream each (the C calls release
+    the interpreter lock).  groups: optional dict group_key -> Group built
+    earlier for these problems (reused; keeps its tuned launch shapes).
+    Returns the list of (U, infos) in the problems' order."""
     import threading
     torch = _torch()
     dev = torch.cuda.current_device()
     units = {}
     for i, q in enumerate(problems):
-        key = grid_key(q) if q.d == 2 else ("single", i)
+        key = group_key(q) if q.d == 2 else ("single", i)
         units.setdefault(key, []).append(i)
     keys = list(units)
     streams = [torch.cuda.Stream() for _ in keys]

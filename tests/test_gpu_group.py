@@ -1,7 +1,8 @@
 """Groups: several 2D problems on one overlay grid solved together.
 
 Every column of every instance of a group (different meshes, different
-alpha) must reach the FP64 tolerance with the oracle's operator of its own
+alpha: columns converge at different iterations, and the product kernels
+skip the converged ones) must reach the FP64 tolerance with the oracle's operator of its own
 instance (Section 3.2, (GoFD-2)) and agree with the same instance solved
 alone in FP64.  Groups of different grids go through solve_many; one group
 runs on the one-warp-per-FFT kernels (circulant 2048).
@@ -83,12 +84,14 @@ def test_group_matches_oracle_and_single_solves(mode):
 
 
 def test_groups_of_two_grids_through_solve_many():
-    from paper_2307_14437_gb300 import grid_key, solve_many
+    from paper_2307_14437_gb300 import grid_key, group_key, solve_many
     pa, ra, fa = _build(129)
     pb, rb, fb = _build(600)          # circulant 2048: the one-warp-per-FFT kernels
     assert all(q.info()["warp_fft_path"] == 1 for q in pb)
     probs, refs, Fs = pa + pb, ra + rb, fa + fb
     assert len({grid_key(q) for q in probs}) == 2
+    # solve_many's groups: (129, 0.5), (129, 1.5) of two instances, (600, 1.0), (600, 0.7)
+    assert len({group_key(q) for q in probs}) == 4
     res = solve_many(probs, Fs, mode="mixed", tol=1e-8)
     _check(probs, refs, Fs, res, 1e-8, single=False)
     for q in probs:

@@ -496,7 +496,9 @@ static void solve_cols(const BOp& op, BatchWork* w, const Cols& cols, gofd_solve
             colv[c] = inv[c];
             colv[nb + c] = scale[c];
             // FP64: each column straight to its own tolerance; mixed: the inner FP32 tolerance
-            colv[2 * nb + c] = mode == GOFD_SOLVE_FP64 ? (scale[c] > 0 ? 0.5 * tol * bn[c] / scale[c] : 1.0) : itol;
+            // mixed: 1e-4, or the smaller reduction a column near tol still needs
+            const double need = scale[c] > 0 ? 0.5 * tol * bn[c] / scale[c] : 1.0;
+            colv[2 * nb + c] = mode == GOFD_SOLVE_FP64 ? need : std::max(itol, need);
         }
         GOFD_CUDA_TRY(cudaMemcpyAsync(w->colv.ptr, colv.data(), 8 * 3 * nb, cudaMemcpyHostToDevice, st));
         const double* dinv = w->colv.as<double>();

@@ -8,6 +8,7 @@
 // last block to finish adds the partials in block order), so results do not
 // depend on scheduling.  Scalars stay on the device; the host reads the
 // residual only every `check_every` iterations.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 
@@ -452,7 +453,11 @@ void solve_core(gofd_problem* p, gofd_solve_mode mode, const double* b, double t
             // inner FP32 PCG on S d = r / ||r||
             to_f32_kernel<<<nb, 256, 0, st>>>(r, w->r32.as<float>(), 1.0 / rn, n);
             GOFD_CHECK_LAUNCH();
-            const double itol = p->opt.inner_tol > 0 ? p->opt.inner_tol : 1e-4;
+            // the inner reduction a round needs: 1e-4 (the FP32 solve's
+            // reach), or less when the residual is already near tol (half of
+            // the remaining factor, so that the round's FP32 error still fits)
+            const double itol0 = p->opt.inner_tol > 0 ? p->opt.inner_tol : 1e-4;
+            const double itol = std::max(itol0, 0.5 * tol * bn / rn);
             int its = pcg<float>(p, w, w->d32.as<float>(), w->r32.as<float>(), w->p32.as<float>(),
                                  w->q32.as<float>(), w->z32.as<float>(), itol, maxit - inner, st, &inner_rel);
             inner += its;

@@ -21,6 +21,12 @@
  *  - Host inputs are copied; the caller keeps ownership of everything it
  *    passes.  A gofd_problem owns all of its device memory and frees it in
  *    gofd_destroy().  A handle is not thread safe: serialise calls on it.
+ *  - Different handles may be used from different threads at once, with one
+ *    restriction: the solvers capture their iterations as CUDA graphs on
+ *    first use, and a capture fails if the device is synchronised meanwhile.
+ *    gofd_destroy and gofd_group_destroy synchronise the device (they free
+ *    device memory), so do not destroy a handle or group on a device while
+ *    another thread is inside a solve on that device.
  *  - Device vectors are caller-owned device pointers, used in stream order on
  *    the caller's stream (`stream` is a cudaStream_t cast to void*; NULL is
  *    the legacy default stream).  The library allocates nothing per call on
@@ -88,7 +94,8 @@ typedef struct {
     int richardson_levels;     /* Filon levels M, M/2, ...; 0 = 4                                                     */
     uint64_t wait_budget_cycles; /* bound on device-side spin waits (clock64 cycles); 0 = 2e9.  No kernel of this
                                     build spins on a flag; the field is kept for ABI stability                    */
-    double inner_tol;          /* mixed mode: relative reduction of each inner FP32 PCG; 0 = 1e-4                   */
+    double inner_tol;          /* mixed mode: relative reduction of each inner FP32 PCG (0 = 1e-4); a round that
+                                  needs less (residual near tol) asks for half the remaining factor              */
     int check_every;           /* iterations between convergence checks (on the device); 0 = 8                      */
     int ordering;              /* IC unknown order: 0 natural vertex order, 1 multicolour (shorter dependency chains)  */
     int chunk_planes;          /* 3D: spectrum planes k_x0 per chunk of the axis-1/axis-2 stage; 0 = as many as fit a

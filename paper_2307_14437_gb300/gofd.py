@@ -350,33 +350,37 @@ def solve_many(problems, batches, rhs: str = "grid", mode: str = "mixed", tol: f
         key = group_key(q) if q.d == 2 else ("single", i)
         units.setdefault(key, []).append(i)
     keys = list(units)
+    nb = {i: batches[i].shape[0] for i in range(len(problems))}
+    # groups this call builds: made here, before any worker starts, and closed
+    # after every worker has returned -- creating or destroying a handle
+    # allocates or frees device memory, and a free synchronises the device,
+    # which would break another worker's CUDA graph capture
+    own = {}
+    for key in keys:
+        idx = units[key]
+        if key[0] != "single" and len(set(nb[i] for i in idx)) == 1 and not (groups and key in groups):
+            own[key] = Group([problems[i] for i in idx], nb[idx[0]])
     streams = [torch.cuda.Stream() for _ in keys]
     for s in streams:
         s.wait_stream(torch.cuda.current_stream())
     out = [None] * len(problems)
     errs = [None] * len(keys)
-    nb = {i: batches[i].shape[0] for i in range(len(problems))}
 
     def work(u):
         try:
             torch.cuda.set_device(dev)
             idx = units[keys[u]]
             with torch.cuda.stream(streams[u]):
-                if keys[u][0] == "single" or len(set(nb[i] for i in idx)) != 1:
+                g = own.get(keys[u]) or (groups.get(keys[u]) if groups else None)
+                if g is None:
                     for i in idx:
                         out[i] = problems[i].solve_batch(batches[i], rhs=rhs, mode=mode, tol=tol, maxit=maxit,
                                                          stream=streams[u])
                     return
-                g = groups.get(keys[u]) if groups else None
-                own = g is None
-                if own:
-                    g = Group([problems[i] for i in idx], nb[idx[0]])
                 res = g.solve([batches[i] for i in idx], rhs=rhs, mode=mode, tol=tol, maxit=maxit,
                               stream=streams[u])
                 for i, r in zip(idx, res):
                     out[i] = r
-                if own:
-                    g.close()
         except Exception as e:  # re-raised on the caller's thread
             errs[u] = e
 
@@ -387,6 +391,8 @@ def solve_many(problems, batches, rhs: str = "grid", mode: str = "mixed", tol: f
         t.join()
     for s in streams:
         torch.cuda.current_stream().wait_stream(s)
+    for g in own.values():
+        g.close()
     for e in errs:
         if e is not None:
             raise e

@@ -66,11 +66,13 @@ WORKLOADS = {
     "batch48": "48 instances (16 ring disks + 16 L-shapes, 5e3-1.5e5 vertices log-uniform, alpha cycling "
                "0.5/1/1.5, grids 256^2-2048^2) x 8 right-hand sides (f=1 + 7 Gaussian bumps, width 0.1)",
 }
-# DRAM bytes of one FP32 L-shape product (dram__bytes_read.sum +
-# dram__bytes_write.sum summed over its kernels), from an ncu capture of this
-# build that keeps L2 between kernels (--cache-control none) after the same
-# 256 MB L2 flush the timed loop does; None until captured for these kernels.
-NCU_PRODUCT_DRAM_BYTES = {"lshape1024": None}
+# DRAM bytes of one FP32 L-shape product: dram__bytes_read.sum +
+# dram__bytes_write.sum of each of its five kernels, averaged over five
+# products of an ncu launch list of these kernels that keeps L2 as the program
+# leaves it (--cache-control none) after the same 256 MB L2 flush the timed
+# loop does, summed over the kernels; the writes are mostly the flush
+# buffer's dirty lines written back.  (total, reads)
+NCU_PRODUCT_DRAM_BYTES = {"lshape1024": (86144870, 45751091)}
 BATCH_METRIC = "batched block-PCG: right-hand sides solved to rel-res 1e-8 per second (mixed), 1 GB300"
 BATCH_RHS = 8
 
@@ -351,7 +353,10 @@ def run_gofd(args):
     achieved = B32 / (ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "kernel": "stiffness product (%d kernels: %s)" % (len(stage_ms), ", ".join(stage_ms)),
                 "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-                "traffic": NCU_PRODUCT_DRAM_BYTES.get(args.workload),
+                "traffic": NCU_PRODUCT_DRAM_BYTES[args.workload][0] if args.workload in NCU_PRODUCT_DRAM_BYTES
+                and not args.grid else None,
+                "traffic_read": NCU_PRODUCT_DRAM_BYTES[args.workload][1] if args.workload in NCU_PRODUCT_DRAM_BYTES
+                and not args.grid else None,
                 "bytes_alg": B32, "ms_per_product": round(ms, 5),
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy), of measured" if "hbm_gbs" in pk
                 else "fallback 6.8 TB/s",

@@ -800,6 +800,10 @@ InstView inst_view(const gofd_problem* p) {
     v.run_len = p->run_len.as<int32_t>();
     v.run_e0 = p->run_e0.as<int32_t>();
     v.wdesc_line = p->wdesc_line.as<int4>();
+    v.ell4_node = p->ell4_node.as<int32_t>();
+    v.ell4_iidx = p->ell4_iidx.as<int32_t>();
+    v.ell4_w32 = p->ell4_w32.as<float>();
+    v.ell4_ld = p->ell4_ld;
     v.lamT32 = p->lamT32.as<float>();
     v.lamT64 = p->lamT64.as<double>();
     v.csr_ptr = p->csr_ptr.as<int32_t>();

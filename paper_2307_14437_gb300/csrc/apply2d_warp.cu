@@ -3,9 +3,10 @@
 // FFT (Section 2.2, (AU-1); gather of (IhFD-1) in front).
 //
 //   gather_w    v = I x at the located grid nodes, linear over the ELL rows
-//               (four rows per thread; the ELL and the node index of each row
-//               are set-up data and are loaded before the launch dependency
-//               is resolved).  v goes into the output grid buffer, which the
+//               (four consecutive rows per thread, one 16-byte load per ELL
+//               array from a copy whose slot stride is padded to four rows;
+//               the ELL is set-up data and is loaded before the launch
+//               dependency is resolved).  v goes into the output grid buffer, which the
 //               inverse row kernel overwrites with w only after the forward
 //               row kernel has read v.
 //   row_fwd_w   per grid line, one warp: z[m] = v[2m] + i v[2m+1] (zero off the
@@ -187,53 +188,50 @@ __device__ __forceinline__ void prefetch_share(const void* base, int64_t bytes, 
 // kernel 0: gather v = I x at the located grid nodes
 // ---------------------------------------------------------------------------
 constexpr int GTH = 128;   // threads of the gather kernel
-constexpr int GRW = 4;     // ELL rows per thread
 __global__ void __launch_bounds__(GTH, 12) gather_w_kernel(const float* __restrict__ x,
                                                           const int32_t* __restrict__ iidx,
                                                           const float* __restrict__ w,
-                                                          const int32_t* __restrict__ node, int64_t nloc,
+                                                          const int32_t* __restrict__ node, int64_t ld4,
                                                           float* __restrict__ vgrid, int64_t xstride,
                                                           int64_t vstride, GroupArg ga) {
     if (ga.iv) {   // a group: this column's instance
         const InstView& I = ga.iv[blockIdx.y / ga.nbper];
-        iidx = I.ell_iidx;
-        w = I.ell_w32;
-        node = I.ell_node;
-        nloc = I.nloc;
+        iidx = I.ell4_iidx;
+        w = I.ell4_w32;
+        node = I.ell4_node;
+        ld4 = I.ell4_ld;
     }
     x += blockIdx.y * xstride;
     vgrid += blockIdx.y * vstride;
-    const int64_t e0 = ((int64_t)blockIdx.x * GTH) * GRW + threadIdx.x;
-    int ii[GRW][3], nd[GRW];
-    float ww[GRW][3];
-    // set-up data, loaded before the predecessor completes (rows GTH apart
-    // within a thread, so every warp load is one contiguous 128-byte run)
+    // rows 4e .. 4e + 3: one 16-byte load per slot array (set-up data, loaded
+    // before the predecessor completes); a warp reads 512 contiguous bytes of each
+    const int64_t e = (int64_t)blockIdx.x * GTH + threadIdx.x;
+    const bool in = 4 * e < ld4;
+    int4 nd = make_int4(-1, -1, -1, -1), ii[3];
+    float4 ww[3];
+    if (in) nd = __ldg(reinterpret_cast<const int4*>(node) + e);
 #pragma unroll
-    for (int q = 0; q < GRW; ++q) {
-        const int64_t e = e0 + (int64_t)q * GTH;
-        const bool in = e < nloc;
-        nd[q] = in ? __ldg(&node[e]) : -1;
-#pragma unroll
-        for (int sl = 0; sl < 3; ++sl) {
-            ii[q][sl] = in ? __ldg(&iidx[sl * nloc + e]) : 0;
-            ww[q][sl] = in ? __ldg(&w[sl * nloc + e]) : 0.f;
-        }
+    for (int sl = 0; sl < 3; ++sl) {
+        ii[sl] = in ? __ldg(reinterpret_cast<const int4*>(iidx + sl * ld4) + e) : make_int4(0, 0, 0, 0);
+        ww[sl] = in ? __ldg(reinterpret_cast<const float4*>(w + sl * ld4) + e) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     pdl_trigger();
     pdl_wait();
     if (column_skipped(ga)) return;
-    float xv[GRW][3];
+    const int n4[4] = {nd.x, nd.y, nd.z, nd.w};
+    float acc[4];
 #pragma unroll
-    for (int q = 0; q < GRW; ++q)
+    for (int r = 0; r < 4; ++r) acc[r] = 0.f;
 #pragma unroll
-        for (int sl = 0; sl < 3; ++sl) xv[q][sl] = nd[q] >= 0 ? __ldcg(&x[ii[q][sl]]) : 0.f;
+    for (int sl = 0; sl < 3; ++sl) {
+        const int i4[4] = {ii[sl].x, ii[sl].y, ii[sl].z, ii[sl].w};
+        const float w4[4] = {ww[sl].x, ww[sl].y, ww[sl].z, ww[sl].w};
 #pragma unroll
-    for (int q = 0; q < GRW; ++q) {
-        float acc = 0.f;
-#pragma unroll
-        for (int sl = 0; sl < 3; ++sl) acc = fmaf(ww[q][sl], xv[q][sl], acc);
-        if (nd[q] >= 0) vgrid[nd[q]] = acc;
+        for (int r = 0; r < 4; ++r) acc[r] = fmaf(w4[r], n4[r] >= 0 ? __ldcg(&x[i4[r]]) : 0.f, acc[r]);
     }
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+        if (n4[r] >= 0) vgrid[n4[r]] = acc[r];
 }
 
 // ---------------------------------------------------------------------------
@@ -493,6 +491,24 @@ void setup_apply_2d_warp(gofd_problem* p) {
                           (const void*)gather_w_kernel})
         GOFD_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout,
                                            (int)cudaSharedmemCarveoutMaxShared));
+    // the ELL with its slot stride rounded up to four rows (gather_w_kernel
+    // reads four rows with one 16-byte load per array)
+    const int64_t nloc = p->nloc, ld4 = (nloc + 3) / 4 * 4;
+    p->ell4_node.alloc(sizeof(int32_t) * std::max<int64_t>(ld4, 4));
+    p->ell4_iidx.alloc(sizeof(int32_t) * 3 * std::max<int64_t>(ld4, 4));
+    p->ell4_w32.alloc(sizeof(float) * 3 * std::max<int64_t>(ld4, 4));
+    const cudaStream_t ss = p->setup_stream;   // after the ELL's own set-up kernels
+    GOFD_CUDA_TRY(cudaMemsetAsync(p->ell4_node.ptr, 0xff, p->ell4_node.bytes, ss));   // node -1
+    GOFD_CUDA_TRY(cudaMemsetAsync(p->ell4_iidx.ptr, 0, p->ell4_iidx.bytes, ss));
+    GOFD_CUDA_TRY(cudaMemsetAsync(p->ell4_w32.ptr, 0, p->ell4_w32.bytes, ss));
+    if (nloc > 0) {
+        GOFD_CUDA_TRY(cudaMemcpyAsync(p->ell4_node.ptr, p->ell_node.ptr, 4 * nloc, cudaMemcpyDeviceToDevice, ss));
+        GOFD_CUDA_TRY(cudaMemcpy2DAsync(p->ell4_iidx.ptr, 4 * ld4, p->ell_iidx.ptr, 4 * nloc, 4 * nloc, 3,
+                                        cudaMemcpyDeviceToDevice, ss));
+        GOFD_CUDA_TRY(cudaMemcpy2DAsync(p->ell4_w32.ptr, 4 * ld4, p->ell_w32.ptr, 4 * nloc, 4 * nloc, 3,
+                                        cudaMemcpyDeviceToDevice, ss));
+    }
+    p->ell4_ld = ld4;
     p->wdesc_line.alloc(sizeof(int4) * 2 * nl);
     GOFD_CUDA_TRY(cudaMemcpy(p->wdesc_line.ptr, ldesc.data(), sizeof(int4) * 2 * nl, cudaMemcpyHostToDevice));
 }
@@ -511,9 +527,9 @@ void afd_2d_warp_f32(gofd_problem* p, const float* x, float* wgrid, int nb, int6
     const unsigned rblocks = (unsigned)((nlines + LINES - 1) / LINES);
     const float* lam = p->lamT32.as<float>();
     const int64_t nloc_max = ga.iv ? ga.max_nloc : p->nloc;
-    const unsigned gblocks = (unsigned)std::max<int64_t>(1, (nloc_max + GTH * GRW - 1) / (GTH * GRW));
-    launch_pdl(gather_w_kernel, dim3(gblocks, nb), dim3(GTH), 0, st, x, p->ell_iidx.as<int32_t>(),
-               p->ell_w32.as<float>(), p->ell_node.as<int32_t>(), p->nloc, wgrid, xs, ws, ga);
+    const unsigned gblocks = (unsigned)std::max<int64_t>(1, (nloc_max + 4 * GTH - 1) / (4 * GTH));
+    launch_pdl(gather_w_kernel, dim3(gblocks, nb), dim3(GTH), 0, st, x, p->ell4_iidx.as<int32_t>(),
+               p->ell4_w32.as<float>(), p->ell4_node.as<int32_t>(), p->ell4_ld, wgrid, xs, ws, ga);
     mark_stage(st, "gather");
     launch_pdl(row_fwd_w_kernel, dim3(rblocks, nb), dim3(128), ROW_SMEM, st, (const float*)wgrid,
                p->wdesc_line.as<int4>(), p->run_k0.as<int32_t>(), p->run_len.as<int32_t>(), nlines, n, tw, twp,

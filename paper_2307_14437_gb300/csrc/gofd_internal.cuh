@@ -172,6 +172,10 @@ struct InstView {
     int64_t nloc;
     const int32_t *run_ptr, *run_k0, *run_len, *run_e0;
     const int4* wdesc_line;
+    const int32_t* ell4_node;   // 2D warp-FFT path: the ELL with its slot stride padded to ell4_ld
+    const int32_t* ell4_iidx;
+    const float* ell4_w32;
+    int64_t ell4_ld;
     const float* lamT32;
     const double* lamT64;
     const int32_t *csr_ptr, *csr_col;
@@ -241,6 +245,11 @@ struct gofd_problem {
     gofd::DevBuf ell_w32;      // float [(d+1)*nloc]
     gofd::DevBuf ell_iidx;     // int32 [(d+1)*nloc] interior numbering, boundary -> nint (zero slot)
     gofd::DevBuf wdesc_line;   // 2D warp-FFT path: per-line run descriptors (2 int4 per line)
+    // 2D warp-FFT path: node, interior index and FP32 weight of the ELL with
+    // the slot stride ell4_ld = n_loc rounded up to 4 (every slot 16-byte
+    // aligned; padding rows: node -1, index 0, weight 0), read four rows at a time
+    gofd::DevBuf ell4_node, ell4_iidx, ell4_w32;
+    int64_t ell4_ld = 0;
     int64_t nruns = 0;
     gofd::DevBuf line_run_ptr; // int32 [nlines+1]
     gofd::DevBuf run_k0;       // int32 [nruns]   first k0 of the run

@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(GTH, 12) gather_w_kernel(const float* __restri
         const int i4[4] = {ii[sl].x, ii[sl].y, ii[sl].z, ii[sl].w};
         const float w4[4] = {ww[sl].x, ww[sl].y, ww[sl].z, ww[sl].w};
 #pragma unroll
-        for (int r = 0; r < 4; ++r) acc[r] = fmaf(w4[r], n4[r] >= 0 ? __ldcg(&x[i4[r]]) : 0.f, acc[r]);
+        for (int r = 0; r < 4; ++r) acc[r] = fmaf(w4[r], n4[r] >= 0 ? __ldg(&x[i4[r]]) : 0.f, acc[r]);
     }
 #pragma unroll
     for (int r = 0; r < 4; ++r)

@@ -27,6 +27,10 @@ Parity status of each function (what pins it is in ``tests/test_oracle_*.py``):
                                         L L^T = A on the kept pattern)
   jacobi_diagonal                      pinned (the diagonal of S assembled column by
                                         column from the stiffness product)
+  circulant_inverse_apply / _precond   pinned (dense circulant solve on a small P,
+                                        C applied to C^{-1} v by the direct Toeplitz
+                                        wrap, symmetry, positivity, grid-aligned mesh
+                                        where I is a selection and D_h = 1)
 """
 from __future__ import annotations
 
@@ -965,6 +969,44 @@ def pcg_ic(prob: Problem, b: np.ndarray, pattern: int = 9, tol: float = 1e-10, m
     x, info = solve(prob, b, tol, maxit=maxit, precond=precond)
     info["ic_shift"] = shift
     return x, info
+
+
+def circulant_inverse_apply(prob: Problem, v_flat: np.ndarray) -> np.ndarray:
+    """R C^{-1} R^T v: the inverse of the P^d circulant C whose first column is
+    the even embedding of T (Section 2.2; C restricted to the grid is A_FD),
+    applied to the grid vector v zero-padded to P^d, kept on the n^d corner.
+    C^{-1} has the symbol 1/lambda (lambda > 0: T_0 > 0 and T_m < 0 for m != 0,
+    so every lambda_k >= lambda_0 = the sum of the embedded T > 0)."""
+    d = prob.d
+    n = prob.n[0]
+    P = prob.P
+    vp = np.zeros((P,) * d)
+    vp[(slice(0, n),) * d] = prob.grid_vector(v_flat)
+    lam = _full_symbol(prob.lam, P)
+    w = scipy.fft.ifftn(scipy.fft.fftn(vp) / lam).real
+    return np.ascontiguousarray(w[(slice(0, n),) * d]).ravel()
+
+
+def circulant_precond(prob: Problem, r: np.ndarray) -> np.ndarray:
+    """z = M^{-1} r for the circulant alternative of Section 3.3 (reading R24):
+    M = I^T C I with C the circulant of A_FD; its inverse is taken as
+    M^{-1} = D_h^{-1} I^T C^{-1} I D_h^{-1}, i.e. (I^T C I)^{-1} with I replaced
+    by its lumped pseudo-inverse D_h^{-1} I^T (the barycentric weights of a
+    grid node sum to 1, so I^T I 1 = D_h).  Interior entries only."""
+    ii = prob.interior
+    dinv = np.zeros(len(prob.verts))
+    dinv[ii] = 1.0 / prob.Dh[ii]
+    v = prob.I @ (dinv * r)
+    w = circulant_inverse_apply(prob, v)
+    y = prob.I.T @ w
+    out = np.zeros_like(r)
+    out[ii] = dinv[ii] * y[ii]
+    return out
+
+
+def pcg_circulant(prob: Problem, b: np.ndarray, tol: float = 1e-10, maxit=100000):
+    """PCG on (GoFD-2) with the circulant preconditioner (circulant_precond)."""
+    return solve(prob, b, tol, maxit=maxit, precond=lambda r: circulant_precond(prob, r))
 
 
 def jacobi_diagonal(prob: Problem) -> np.ndarray:

@@ -101,3 +101,88 @@ def test_jacobi_pcg_matches_plain_cg():
     x1, _ = o.solve(ref, b, tol=1e-13)
     x2, _ = o.pcg_jacobi(ref, b, tol=1e-13)
     assert np.linalg.norm(x1 - x2) <= 1e-10 * np.linalg.norm(x1)
+
+
+# ---------------------------------------------------------------------------
+# the circulant alternative of Section 3.3 (reading R24)
+# ---------------------------------------------------------------------------
+def _dense_circulant(c):
+    """The circulant matrix with first column c (shape (P,)*d), entry by entry:
+    C[(i), (j)] = c[(i - j) mod P] per axis."""
+    P = c.shape[0]
+    d = c.ndim
+    idx = np.array(np.unravel_index(np.arange(P ** d), (P,) * d)).T
+    diff = (idx[:, None, :] - idx[None, :, :]) % P
+    return c[tuple(diff[..., a] for a in range(d))]
+
+
+@pytest.mark.parametrize("d,n", [(1, 9), (2, 5)])
+def test_circulant_inverse_is_a_dense_circulant_solve(d, n):
+    T = o.coefficients(d, 0.6, n, 2 ** 10)
+    P = o.circulant_size(n)
+    C = _dense_circulant(o.circulant_first_column(T, P))
+    rng = np.random.default_rng(7)
+    vg = rng.standard_normal((n,) * d)
+    vp = np.zeros((P,) * d)
+    vp[(slice(0, n),) * d] = vg
+    want = np.linalg.solve(C, vp.ravel()).reshape((P,) * d)[(slice(0, n),) * d].ravel()
+
+    class _G:   # the fields circulant_inverse_apply reads
+        pass
+    g = _G()
+    g.d, g.n, g.P, g.lam = d, (n,) * d, P, o.symbol(T, P)
+    g.grid_vector = lambda f: f.reshape((n,) * d)
+    got = o.circulant_inverse_apply(g, vg.ravel())
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+
+
+def test_symbol_of_the_fractional_stencil_is_positive_with_minimum_at_zero():
+    # T_0 > 0 and T_m < 0 otherwise (the kernel of (T-1) is positive off the
+    # origin), so lambda_k >= lambda_0 = sum of the embedded T > 0: C is SPD
+    for d, n, s in [(1, 33, 0.3), (2, 17, 0.75), (3, 9, 0.5)]:
+        T = o.coefficients(d, s, n, 2 ** 10 if d < 3 else 2 ** 8)
+        off = T.ravel()[1:]
+        assert T.ravel()[0] > 0 and np.all(off < 0)
+        lam = o.symbol(T, o.circulant_size(n))
+        assert lam.min() > 0 and np.argmin(lam) == 0
+
+
+def test_circulant_precond_on_a_grid_aligned_mesh_is_the_restricted_inverse():
+    # every vertex on a grid node: I is a 0/1 selection, D_h = 1, so
+    # M^{-1} r = (R C^{-1} R^T r) at the vertices' nodes (dense solve)
+    n, cells, off = 11, 6, 2
+    lo, hi, h = mg.grid_box(2, n)
+    verts, simp = mg.grid_aligned_mesh(2, -1.0, h, cells, origin_cells=off)
+    P = o.build(2, verts, simp, 1.2, h, lo, hi, M=2 ** 10)
+    assert np.allclose(P.Dh, 1.0)
+    r = mg.random_vector(len(verts), 11)
+    r[P.boundary] = 0.0
+    k = np.rint((verts - lo) / h).astype(np.int64)
+    vp = np.zeros((P.P, P.P))
+    vp[k[:, 1], k[:, 0]] = r
+    C = _dense_circulant(o.circulant_first_column(P.T, P.P))
+    w = np.linalg.solve(C, vp.ravel()).reshape(P.P, P.P)
+    want = np.where(P.boundary, 0.0, w[k[:, 1], k[:, 0]])
+    got = o.circulant_precond(P, r)
+    assert np.abs(got - want).max() <= 1e-12 * np.abs(want).max()
+
+
+def test_circulant_precond_is_symmetric_positive_definite():
+    P = _disk(1.5)
+    a = mg.random_vector(len(P.verts), 12)
+    b = mg.random_vector(len(P.verts), 13)
+    a[P.boundary] = 0.0
+    b[P.boundary] = 0.0
+    Ma, Mb = o.circulant_precond(P, a), o.circulant_precond(P, b)
+    assert abs(a @ Mb - b @ Ma) <= 1e-12 * abs(a @ Mb)
+    assert a @ Ma > 0 and b @ Mb > 0
+    assert np.all(Ma[P.boundary] == 0.0)
+
+
+def test_circulant_pcg_reaches_the_plain_cg_solution():
+    P = _disk(1.0)
+    b = o.rhs_grid(P, np.ones(P.n_grid))
+    x0, i0 = o.solve(P, b, tol=1e-12)
+    x1, i1 = o.pcg_circulant(P, b, tol=1e-12)
+    assert i1["rel_res"] <= 1e-12
+    assert np.linalg.norm(x1 - x0) <= 1e-9 * np.linalg.norm(x0)

@@ -450,6 +450,21 @@ def run_gofd(args):
                 "outer_iters": info["outer_iters"], "rel_res_fp64": info["rel_res_fp64"],
                 "levels": pi["precond_levels"], "factor_nnz": pi["precond_nnz"], "build_s": round(t_pc, 3)}
             pp.close()
+    if not args.no_pcg and args.workload == "lshape1024":
+        # the circulant alternative of Section 3.3 (precond = 2) at each alpha
+        for a in ALPHAS:
+            pc = Problem(v, s, a, h, lo, hi, precond=2)
+            pc.autotune(nb=1)
+            f = torch.ones(pc.n_grid, dtype=torch.float64, device=dev)
+            pc.solve(f, mode="mixed", tol=1e-8)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            _, info = pc.solve(f, mode="mixed", tol=1e-8)
+            torch.cuda.synchronize()
+            pcg[f"alpha={a} circulant precond (Section 3.3 alternative)"] = {
+                "mixed_s": round(time.perf_counter() - t1, 5), "inner_iters": info["inner_iters"],
+                "outer_iters": info["outer_iters"], "rel_res_fp64": info["rel_res_fp64"]}
+            pc.close()
     if not args.no_pcg and args.workload in ("lshape1024", "graded2048"):
         # the 2048^2 configuration: graded disk, alpha = 1.2, vertex data f_target (GoFD-3)
         if args.workload == "graded2048":
@@ -495,20 +510,22 @@ def run_gofd(args):
         # the paper's preconditioner in its own setting, h_FD about a_h (Section
         # 3.3, Remark 3.5): the same L-shape mesh on the grid with h just below
         # a_h, alpha 1 and 1.8 (s = 0.9), plain CG against IC(1) of the 5- and
-        # 9-point stencil matrices (multicolour order), mixed precision to 1e-8
+        # 9-point stencil matrices (multicolour order) and against the
+        # circulant alternative the section names, mixed precision to 1e-8
         n_c = int(math.ceil(2.0 / inf["a_h"])) + 1
         lo_c, hi_c, h_c = mg.grid_box(2, n_c)
         ic = {}
         for a in (1.0, 1.8):
-            for pat in (0, 5, 9):
-                pp = Problem(v, s, a, h_c, lo_c, hi_c, precond=pat, ordering=1 if pat else 0)
+            for pat in (0, 5, 9, 2):
+                pp = Problem(v, s, a, h_c, lo_c, hi_c, precond=pat, ordering=1 if pat in (5, 9) else 0)
                 f = torch.ones(pp.n_grid, dtype=torch.float64, device=dev)
                 pp.solve(f, mode="mixed", tol=1e-8)
                 torch.cuda.synchronize()
                 t1 = time.perf_counter()
                 _, info = pp.solve(f, mode="mixed", tol=1e-8)
                 torch.cuda.synchronize()
-                ic[f"alpha={a} {'plain CG' if pat == 0 else f'IC(1) {pat}-point'}"] = {
+                label = {0: "plain CG", 2: "circulant (Section 3.3 alternative)"}.get(pat, f"IC(1) {pat}-point")
+                ic[f"alpha={a} {label}"] = {
                     "s": round(time.perf_counter() - t1, 5), "inner_iters": info["inner_iters"],
                     "rel_res_fp64": info["rel_res_fp64"], "h_over_a_h": round(h_c / info["a_h"], 3)}
                 pp.close()

@@ -87,7 +87,8 @@ typedef enum {
 typedef struct {
     int precond;               /* 0: none; 5 or 9 (2D), 7 or 27 (3D), 3 (1D): IC(ic_level) of I^T A_FD^(k) I (Ah-4);
                                   1: the diagonal of S itself (Jacobi scaling; not in the paper, pays on graded
-                                  meshes where the diagonal spans orders of magnitude)                               */
+                                  meshes where the diagonal spans orders of magnitude);
+                                  2 (2D): the circulant alternative of Section 3.3 (gofd_precond_apply)             */
     int ic_level;              /* level of fill of the incomplete Cholesky factor (paper: 1)                        */
     int64_t filon_M;           /* finest Filon panel count M; 0 = paper default (2^14 in 1D/2D, 2^11 in 3D), raised
                                   so that the coarsest Richardson level keeps M/2^(levels-1) >= n                      */
@@ -182,6 +183,21 @@ gofd_status gofd_build(int d, const double* vertices, int64_t n_v,
  */
 gofd_status gofd_apply(gofd_problem* p, gofd_op op, gofd_precision prec,
                        const void* u_dev, void* y_dev, void* stream);
+
+/*
+ * gofd_precond_apply -- z = M^{-1} r with the handle's preconditioner on
+ * interior-compacted device vectors (r_dev: N_int+1 values, the last one 0;
+ * z_dev receives N_int values and a 0 in slot N_int; r and z must differ).
+ * The solver applies the same operator every PCG iteration.  For the
+ * circulant preconditioner (precond = 2, 2D; Section 3.3 names circulant
+ * preconditioners of A_FD as an alternative to its sparse ones):
+ *   M^{-1} = D_h^{-1} I^T C^{-1} I D_h^{-1},
+ * C the 2n-periodic circulant embedding of A_FD (symbol 1/lambda), one
+ * stiffness product with the inverse symbol between two diagonal scalings.
+ * GOFD_E_ARG if the problem was built without a preconditioner.
+ */
+gofd_status gofd_precond_apply(gofd_problem* p, gofd_precision prec, const void* r_dev, void* z_dev,
+                               void* stream);
 
 /*
  * gofd_apply_host -- gofd_apply on host buffers (N_v values each): copies u to

@@ -54,6 +54,7 @@ EXPORTS = {
     "gofd_apply": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P]),
     "gofd_apply_host": (C.c_int, [_P, C.c_int, C.c_int, _P, _P, _P]),
     "gofd_apply_interior": (C.c_int, [_P, C.c_int, _P, _P, _P]),
+    "gofd_precond_apply": (C.c_int, [_P, C.c_int, _P, _P, _P]),
     "gofd_apply_interior_batch": (C.c_int, [_P, C.c_int, C.c_int, _P, C.c_int64, _P, _P]),
     "gofd_apply_interior_profiled": (C.c_int, [_P, C.c_int, _P, _P, _P, C.POINTER(C.c_float),
                                                C.POINTER(C.c_char_p), C.c_int, C.POINTER(C.c_int)]),

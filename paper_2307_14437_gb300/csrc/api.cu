@@ -185,6 +185,18 @@ gofd_status gofd_apply_interior(gofd_problem* p, gofd_precision prec, const void
     })
 }
 
+gofd_status gofd_precond_apply(gofd_problem* p, gofd_precision prec, const void* r_dev, void* z_dev, void* stream) {
+    if (!p) return GOFD_E_ARG;
+    GOFD_API_BODY(p, {
+        if (!r_dev || !z_dev) gofd::fail(GOFD_E_ARG, "NULL vector");
+        if (prec != GOFD_FP64 && prec != GOFD_FP32) gofd::fail(GOFD_E_ARG, "bad precision");
+        if (r_dev == z_dev) gofd::fail(GOFD_E_ARG, "r and z must not alias");
+        const size_t b = prec == GOFD_FP64 ? 8 : 4;
+        gofd::precond_apply(p, prec == GOFD_FP64, r_dev, z_dev, (cudaStream_t)stream);
+        GOFD_CUDA_TRY(cudaMemsetAsync(static_cast<char*>(z_dev) + b * p->nint, 0, b, (cudaStream_t)stream));
+    })
+}
+
 gofd_status gofd_apply_interior_batch(gofd_problem* p, gofd_precision prec, int nb, const void* x_dev, int64_t ld,
                                       void* y_dev, void* stream) {
     if (!p) return GOFD_E_ARG;

@@ -704,6 +704,22 @@ void apply_interior(gofd_problem* p, bool fp64, const void* x, void* y, cudaStre
     else apply_t<float>(p, (const float*)x, (float*)y, st);
 }
 
+void apply_interior_symbol(gofd_problem* p, bool fp64, const void* x, void* y, const void* lamT, cudaStream_t st) {
+    if (p->d != 2) fail(GOFD_E_ARG, "a replaced symbol is supported in 2D only");
+    GroupArg ga;
+    if (fp64) {
+        ga.lam64 = static_cast<const double*>(lamT);
+        double* wg = p->gridw.as<double>();
+        afd_2d_f64(p, (const double*)x, nullptr, wg, 1, 0, 0, nullptr, st, ga);
+        scatter<double>(p, wg, (double*)y, 1.0, st);
+    } else {
+        ga.lam32 = static_cast<const float*>(lamT);
+        float* wg = p->gridw.as<float>();
+        afd_2d_f32(p, (const float*)x, nullptr, wg, 1, 0, 0, nullptr, st, ga);
+        scatter<float>(p, wg, (float*)y, 1.0f, st);
+    }
+}
+
 int apply_interior_profiled(gofd_problem* p, bool fp64, const void* x, void* y, cudaStream_t st, float* ms,
                             const char** names, int cap) {
     StageEvents se;

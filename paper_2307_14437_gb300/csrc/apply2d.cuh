@@ -332,6 +332,8 @@ __global__ void __launch_bounds__(MAXT, MINB) col_conv_t_kernel(typename Cplx<Re
     if (ga.iv) {
         const InstView& I = ga.iv[blockIdx.y / ga.nbper];
         lamT = sizeof(Real) == 4 ? reinterpret_cast<const Real*>(I.lamT32) : reinterpret_cast<const Real*>(I.lamT64);
+    } else if (sizeof(Real) == 4 ? ga.lam32 != nullptr : ga.lam64 != nullptr) {
+        lamT = sizeof(Real) == 4 ? reinterpret_cast<const Real*>(ga.lam32) : reinterpret_cast<const Real*>(ga.lam64);
     }
     using C = typename Cplx<Real>::T;
     specT += blockIdx.y * sstride;

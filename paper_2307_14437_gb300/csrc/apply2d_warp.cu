@@ -338,6 +338,7 @@ __global__ void __launch_bounds__(64, 7) col_conv_w_kernel(float2* __restrict__ 
                                                         const float* __restrict__ lamT, int64_t sstride,
                                                         GroupArg ga) {
     if (ga.iv) lamT = ga.iv[blockIdx.y / ga.nbper].lamT32;
+    else if (ga.lam32) lamT = ga.lam32;
     __shared__ __align__(16) float2 xb[2][XBUF];
     __shared__ __align__(16) float2 cb[WN];
     __shared__ __align__(16) float lb[WH + 3];

@@ -198,6 +198,10 @@ struct GroupArg {
     const int* skip = nullptr;
     int skip_stride = 0;
     int col0 = 0;
+    // symbol in the column kernels' layout (lamT32 / lamT64) used instead of
+    // the problem's: the circulant preconditioner's 1/lambda (nullptr: lambda)
+    const float* lam32 = nullptr;
+    const double* lam64 = nullptr;
 };
 
 // True when this CTA's column is to be left alone.  Call it after pdl_wait():
@@ -382,6 +386,9 @@ void apply_interior_batch(gofd_problem* p, bool fp64, const void* x, void* y, in
 InstView inst_view(const gofd_problem* p);
 void apply_interior_group(gofd_problem* rp, bool fp64, const void* x, void* y, int nbtot, int64_t ld, void* grid_ws,
                           void* spec_ws, void* partial_ws, void* counter_ws, GroupArg ga, cudaStream_t st);
+// y = I^T C I x (2D, interior-compacted vectors) with the column kernels'
+// symbol replaced by lamT (FP32 or FP64 as the precision, layout of lamT32)
+void apply_interior_symbol(gofd_problem* p, bool fp64, const void* x, void* y, const void* lamT, cudaStream_t st);
 // w = A_FD I x on the grid for an interior-compacted x (n_int + 1 entries)
 void afd_of_interior(gofd_problem* p, bool fp64, const void* x, void* wgrid, cudaStream_t st);
 // adjoint (adjoint.cu)

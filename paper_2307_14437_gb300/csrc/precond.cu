@@ -38,8 +38,29 @@ struct Precond {
     DevBuf level_ptr, level_rows;        // rows grouped by level
     std::vector<int> hlevel_ptr;         // host copy
     DevBuf tmp64a, tmp64b, tmp32a, tmp32b;   // apply work vectors
-    DevBuf diag, dinv64, dinv32;         // pattern 1 (diagonal of S): the diagonal and its inverse
+    DevBuf diag, dinv64, dinv32;         // pattern 1 (diagonal of S): the diagonal and its inverse;
+                                         // pattern 2: 1 / D_h
+    DevBuf lami64, lami32;               // pattern 2: the circulant's inverse symbol, lamT layout
 };
+
+// pattern 2: 1/lambda in the column kernels' symbol layout (lamT holds
+// lambda / P^d; the inverse convolution needs (1/lambda) / P^d), and 1/D_h
+__global__ void circulant_inverse_symbol_kernel(const double* __restrict__ lamT, double* __restrict__ i64,
+                                                float* __restrict__ i32, double p2d, int64_t m) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = 1.0 / (lamT[i] * p2d);
+        i64[i] = v;
+        i32[i] = (float)v;
+    }
+}
+__global__ void inverse_colsum_kernel(const double* __restrict__ colsum, double* __restrict__ i64,
+                                      float* __restrict__ i32, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = 1.0 / colsum[i];
+        i64[i] = v;
+        i32[i] = (float)v;
+    }
+}
 
 void setup_jacobi(gofd_problem* p, DevBuf& diag, DevBuf& dinv64, DevBuf& dinv32);
 void jacobi_apply(const gofd_problem* p, bool fp64, const void* dinv, const void* r, void* z, cudaStream_t st);
@@ -517,10 +538,44 @@ void setup_precond(gofd_problem* p) {
         setup_jacobi(p, pc->diag, pc->dinv64, pc->dinv32);
         return;
     }
+    if (pattern == 2) {   // the circulant alternative of Section 3.3: D_h^{-1} I^T C^{-1} I D_h^{-1}
+        if (p->d != 2) fail(GOFD_E_ARG, "the circulant preconditioner (precond = 2) is 2D");
+        cudaStream_t st = p->setup_stream;
+        Precond* pc = new Precond();
+        p->pc = pc;
+        pc->pattern = 2;
+        pc->n = p->nint;
+        const int64_t H = p->P / 2 + 1, m = H * H, n1 = p->nint + 1;
+        double p2d = 1.0;
+        for (int i = 0; i < 2 * p->d; ++i) p2d *= (double)p->P;
+        pc->lami64.alloc(8 * m);
+        pc->lami32.alloc(4 * m);
+        circulant_inverse_symbol_kernel<<<grid_blocks(m, 256), 256, 0, st>>>(
+            p->lamT64.as<double>(), pc->lami64.as<double>(), pc->lami32.as<float>(), p2d, m);
+        pc->dinv64.alloc(8 * n1);
+        pc->dinv32.alloc(4 * n1);
+        GOFD_CUDA_TRY(cudaMemsetAsync(pc->dinv64.ptr, 0, 8 * n1, st));
+        GOFD_CUDA_TRY(cudaMemsetAsync(pc->dinv32.ptr, 0, 4 * n1, st));
+        inverse_colsum_kernel<<<grid_blocks(p->nint, 256), 256, 0, st>>>(
+            p->colsum.as<double>(), pc->dinv64.as<double>(), pc->dinv32.as<float>(), p->nint);
+        GOFD_CHECK_LAUNCH();
+        // work vectors; entry n_int is the zero pad the gather reads for boundary slots
+        for (DevBuf* b : {&pc->tmp64a, &pc->tmp64b}) {
+            b->alloc(8 * n1);
+            GOFD_CUDA_TRY(cudaMemsetAsync(b->ptr, 0, 8 * n1, st));
+        }
+        for (DevBuf* b : {&pc->tmp32a, &pc->tmp32b}) {
+            b->alloc(4 * n1);
+            GOFD_CUDA_TRY(cudaMemsetAsync(b->ptr, 0, 4 * n1, st));
+        }
+        return;
+    }
     const int d = p->d;
     const bool ok = (d == 1 && pattern == 3) || (d == 2 && (pattern == 5 || pattern == 9)) ||
                     (d == 3 && (pattern == 7 || pattern == 27));
-    if (!ok) fail(GOFD_E_ARG, "preconditioner must be 1 (diagonal), or IC on 3 (1D), 5 or 9 (2D), 7 or 27 (3D)");
+    if (!ok)
+        fail(GOFD_E_ARG,
+             "preconditioner must be 1 (diagonal), 2 (circulant, 2D), or IC on 3 (1D), 5 or 9 (2D), 7 or 27 (3D)");
     if (p->opt.ic_level != 0 && p->opt.ic_level != 1) fail(GOFD_E_ARG, "only ic_level 1 is supported");
     cudaStream_t st = p->setup_stream;
     const int T = 256;
@@ -794,6 +849,15 @@ void precond_apply(gofd_problem* p, bool fp64, const void* r, void* z, cudaStrea
         jacobi_apply(p, fp64, fp64 ? pc->dinv64.ptr : pc->dinv32.ptr, r, z, st);
         return;
     }
+    if (pc->pattern == 2) {   // z = D_h^{-1} I^T C^{-1} I D_h^{-1} r
+        const void* dinv = fp64 ? pc->dinv64.ptr : pc->dinv32.ptr;
+        void* a = fp64 ? pc->tmp64a.ptr : pc->tmp32a.ptr;
+        void* b = fp64 ? pc->tmp64b.ptr : pc->tmp32b.ptr;
+        jacobi_apply(p, fp64, dinv, r, a, st);
+        apply_interior_symbol(p, fp64, a, b, fp64 ? pc->lami64.ptr : pc->lami32.ptr, st);
+        jacobi_apply(p, fp64, dinv, b, z, st);
+        return;
+    }
     if (fp64) {
         apply_t<double>(p, (const double*)r, (double*)z, pc->tmp64a.as<double>(), pc->tmp64b.as<double>(), st);
     } else {
@@ -806,6 +870,7 @@ void precond_export(const gofd_problem* p, int32_t* perm, int32_t* lptr, int32_t
     const Precond* pc = p->pc;
     if (!pc) fail(GOFD_E_ARG, "no preconditioner");
     if (pc->pattern == 1) fail(GOFD_E_ARG, "the diagonal preconditioner has no factor (gofd_export_diagonal)");
+    if (pc->pattern == 2) fail(GOFD_E_ARG, "the circulant preconditioner has no factor");
     const int32_t n = (int32_t)pc->n;
     if (perm) {
         if (pc->ordering == 1) GOFD_CUDA_TRY(cudaMemcpy(perm, pc->perm.ptr, 4 * n, cudaMemcpyDeviceToHost));

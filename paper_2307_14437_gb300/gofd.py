@@ -160,6 +160,16 @@ class Problem:
         self._check(self._lib.gofd_apply_interior(self._h, _PREC[prec], _ptr(x), _ptr(y), _stream_ptr(stream)))
         return y
 
+    def precond_apply(self, r, z=None, stream=None):
+        """z = M^{-1} r with the handle's preconditioner (gofd_precond_apply);
+        r: interior-compacted CUDA tensor of N_int + 1 entries (last one 0)."""
+        torch = _torch()
+        prec = "fp64" if r.dtype == torch.float64 else "fp32"
+        if z is None:
+            z = torch.empty_like(r)
+        self._check(self._lib.gofd_precond_apply(self._h, _PREC[prec], _ptr(r), _ptr(z), _stream_ptr(stream)))
+        return z
+
     def apply_interior_batch(self, X, Y, stream=None):
         """Y[c] = S X[c] for interior-compacted rows (X: nb x ld with ld >= n_int+1
         and X[:, n_int] = 0; Y has the same shape and row stride)."""

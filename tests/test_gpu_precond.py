@@ -140,3 +140,89 @@ def test_diagonal_preconditioner_pays_on_a_graded_mesh():
         assert info["rel_res_fp64"] <= 1e-8
         gp.close()
     assert its[1] < 0.6 * its[0], its
+
+
+# ---------------------------------------------------------------------------
+# the circulant alternative of Section 3.3 (precond = 2) through
+# gofd_precond_apply, against the oracle's circulant_precond
+# ---------------------------------------------------------------------------
+def _interior_vectors(gp, ref, seed):
+    ii, _ = gp.export_vertex_data()
+    iv = np.nonzero(ii >= 0)[0]
+    assert np.array_equal(iv, ref.interior)
+    r = np.zeros(len(ref.verts))
+    r[iv] = mg.random_vector(len(ref.verts), seed)[iv]
+    rc = np.zeros(len(iv) + 1)
+    rc[ii[iv]] = r[iv]
+    return ii, iv, r, rc
+
+
+CIRC = [("disk", 25, 1.5), ("lshape", 33, 1.0), ("lshape600", 600, 0.7)]
+
+
+def _circ_case(name, n, alpha):
+    if name == "lshape600":   # circulant 2048: the one-warp-per-FFT kernels in FP32
+        v, s = mg.lshape_mesh(spacing=0.03, seed=mg.seed_for(2, 31))
+        return v, s, 0
+    d, v, s, _, _, M = _case(name)
+    return v, s, M
+
+
+@pytest.mark.parametrize("name,n,alpha", CIRC)
+def test_circulant_precond_apply_matches_oracle(name, n, alpha):
+    from paper_2307_14437_gb300 import Problem
+    v, s, M = _circ_case(name, n, alpha)
+    lo, hi, h = mg.grid_box(2, n)
+    gp = Problem(v, s, alpha, h, lo, hi, filon_M=M, precond=2)
+    inf = gp.info()
+    ref = o.build(2, v, s, alpha, h, lo, hi, M=inf["filon_M"], exact_weights=False, pruned=True)
+    ii, iv, r, rc = _interior_vectors(gp, ref, 41)
+    want = o.circulant_precond(ref, r)[iv]
+    for dt, tol in ((torch.float64, 1e-12), (torch.float32, 1e-5)):
+        z = gp.precond_apply(torch.tensor(rc, dtype=dt, device="cuda")).cpu().numpy().astype(np.float64)
+        assert z[-1] == 0.0
+        got = z[ii[iv]]
+        assert np.linalg.norm(got - want) <= tol * np.linalg.norm(want), (dt, name)
+    if n == 600:
+        assert inf["warp_fft_path"] == 1
+    gp.close()
+
+
+def test_precond_apply_of_the_diagonal_matches_oracle():
+    from paper_2307_14437_gb300 import Problem
+    d, v, s, n, alpha, M = _case("lshape")
+    lo, hi, h = mg.grid_box(d, n)
+    gp = Problem(v, s, alpha, h, lo, hi, filon_M=M, precond=1)
+    ref = o.build(d, v, s, alpha, h, lo, hi, M=M)
+    ii, iv, r, rc = _interior_vectors(gp, ref, 43)
+    want = r[iv] / o.jacobi_diagonal(ref)
+    z = gp.precond_apply(torch.tensor(rc, device="cuda")).cpu().numpy()
+    assert np.abs(z[ii[iv]] - want).max() <= 1e-5 * np.abs(want).max()
+    gp.close()
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_circulant_pcg_reaches_tolerance_with_oracle_iterations(mode):
+    from paper_2307_14437_gb300 import Problem
+    v, s, M = _circ_case("lshape", 33, 1.0)
+    lo, hi, h = mg.grid_box(2, 33)
+    for alpha in (1.0, 1.8):
+        gp = Problem(v, s, alpha, h, lo, hi, filon_M=M, precond=2)
+        ref = o.build(2, v, s, alpha, h, lo, hi, M=M, exact_weights=False)
+        f = torch.ones(gp.n_grid, dtype=torch.float64, device="cuda")
+        u, info = gp.solve(f, mode=mode, tol=1e-9)
+        b = o.rhs_grid(ref, np.ones(ref.n_grid))
+        assert np.linalg.norm(b - o.stiffness_apply(ref, u.cpu().numpy())) <= 1.05e-9 * np.linalg.norm(b)
+        _, oi = o.pcg_circulant(ref, b, tol=1e-9)
+        if mode == "fp64":   # one PCG run to half the tolerance, checked every 8 iterations on the device
+            assert oi["iters"] - 2 <= info["inner_iters"] <= oi["iters"] + 12, (alpha, oi, info)
+        gp.close()
+
+
+def test_circulant_precond_is_2d_only():
+    from paper_2307_14437_gb300 import GofdError, Problem
+    d, v, s, n, alpha, M = _case("ball")
+    lo, hi, h = mg.grid_box(d, n)
+    with pytest.raises(GofdError) as e:
+        Problem(v, s, alpha, h, lo, hi, filon_M=M, precond=2)
+    assert e.value.code == "GOFD_E_ARG"

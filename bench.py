@@ -405,12 +405,33 @@ def run_gofd(args):
     torch.cuda.synchronize()
     ms64 = statistics.mean(a_.elapsed_time(b_) for a_, b_ in ev64)
     fft_flops = 2 * 2.5 * P ** d * math.log2(P ** d)
+    # the mixed solver's residual product: FP64 gather and scatter, the FFT
+    # convolution in double-float arithmetic (2D)
+    df = None
+    if d == 2:
+        ydf = torch.empty_like(x64)
+        for _ in range(3):
+            prob.apply_interior(x64, ydf, prec="fp64_df")
+        evdf = []
+        for i in range(20):
+            flush.fill_(float(i))
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record(stream)
+            prob.apply_interior(x64, ydf, prec="fp64_df")
+            b_.record(stream)
+            evdf.append((a_, b_))
+        torch.cuda.synchronize()
+        msdf = statistics.mean(a_.elapsed_time(b_) for a_, b_ in evdf)
+        dif = float(torch.linalg.norm(ydf[:nint] - y64[:nint]) / torch.linalg.norm(y64[:nint]))
+        df = {"ms_per_product": round(msdf, 4), "speedup_vs_fp64": round(ms64 / msdf, 2),
+              "rel_diff_vs_fp64_product": dif,
+              "note": "FP64 inputs and outputs, FP64 gather and scatter, FFT convolution in double-float"}
     roofline_fp64 = {"bound": "fp64_alu", "ms_per_product": round(ms64, 4),
                      "achieved": round(fft_flops / (ms64 * 1e-3) / 1e9, 1), "peak": round(fp64_peak, 1),
                      "unit": "GFLOP/s", "frac": round(fft_flops / (ms64 * 1e-3) / 1e9 / fp64_peak, 4),
                      "work": "2 x 2.5 P^d log2 P^d flops per product (unpruned FFTs)",
                      "peak_source": "measured FP64 FMA rate (gofd_fma_rates), this run",
-                     "fp32_fma_gflops": round(fp32_peak, 1)}
+                     "fp32_fma_gflops": round(fp32_peak, 1), "double_float_residual_product": df}
 
     # time to relative residual 1e-8: mixed refinement vs plain FP64 PCG
     pcg = {}
@@ -430,6 +451,19 @@ def run_gofd(args):
                 row[mode] = {"s": round(time.perf_counter() - t1, 5), "inner_iters": info["inner_iters"],
                              "outer_iters": info["outer_iters"], "rel_res_fp64": info["rel_res_fp64"]}
             row["speedup_mixed_vs_fp64"] = round(row["fp64"]["s"] / row["mixed"]["s"], 3)
+            # the same mixed solve with a plain FP64 residual convolution
+            pr = Problem(v, s, a, h, lo, hi, fp64_residual=1)
+            pr.autotune(nb=1)
+            pr.solve(f, mode="mixed", tol=1e-8)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            _, info = pr.solve(f, mode="mixed", tol=1e-8)
+            torch.cuda.synchronize()
+            row["mixed, plain FP64 residual"] = {"s": round(time.perf_counter() - t1, 5),
+                                                 "inner_iters": info["inner_iters"],
+                                                 "outer_iters": info["outer_iters"],
+                                                 "rel_res_fp64": info["rel_res_fp64"]}
+            pr.close()
             pcg[f"alpha={a}"] = row
             if pa is not prob:
                 pa.close()

@@ -67,7 +67,11 @@ typedef enum {
     GOFD_E_NOMEM = 11               /* device or host allocation failed                            */
 } gofd_status;
 
-typedef enum { GOFD_FP64 = 0, GOFD_FP32 = 1 } gofd_precision;
+/* GOFD_FP64_DF (2D, gofd_apply_interior only): FP64 inputs and outputs, the
+ * gather and scatter in FP64, the FFT convolution in double-float arithmetic
+ * (pairs of FP32 numbers, about 48 significant bits): the mixed solver's
+ * residual product, within about 1e-13 of the FP64 product. */
+typedef enum { GOFD_FP64 = 0, GOFD_FP32 = 1, GOFD_FP64_DF = 2 } gofd_precision;
 
 typedef enum {
     GOFD_SOLVE_FP64 = 0,   /* PCG with FP64 operator, vectors and scalars                      */
@@ -101,6 +105,9 @@ typedef struct {
     int ordering;              /* IC unknown order: 0 natural vertex order, 1 multicolour (shorter dependency chains)  */
     int chunk_planes;          /* 3D: spectrum planes k_x0 per chunk of the axis-1/axis-2 stage; 0 = as many as fit a
                                   1 GiB middle buffer.  Bounds memory; results do not depend on it                    */
+    int fp64_residual;         /* mixed mode, the FP64 residual b - S x of each refinement step: 0 = its convolution
+                                  in double-float arithmetic in 2D (gather and scatter in FP64; FP64 elsewhere),
+                                  1 = plain FP64 throughout.  FP64 mode always uses plain FP64                     */
 } gofd_options;
 
 typedef struct {

@@ -16,7 +16,7 @@ STATUS = {
     8: "GOFD_E_NOT_CONVERGED", 9: "GOFD_E_TIMEOUT", 10: "GOFD_E_CUDA", 11: "GOFD_E_NOMEM",
 }
 
-FP64, FP32 = 0, 1
+FP64, FP32, FP64_DF = 0, 1, 2
 SOLVE_FP64, SOLVE_MIXED = 0, 1
 OP_STIFFNESS, OP_FRACLAP = 0, 1
 RHS_GRID, RHS_VERTEX = 0, 1
@@ -26,7 +26,7 @@ class Options(C.Structure):
     _fields_ = [("precond", C.c_int), ("ic_level", C.c_int), ("filon_M", C.c_int64),
                 ("richardson_levels", C.c_int), ("wait_budget_cycles", C.c_uint64),
                 ("inner_tol", C.c_double), ("check_every", C.c_int), ("ordering", C.c_int),
-                ("chunk_planes", C.c_int)]
+                ("chunk_planes", C.c_int), ("fp64_residual", C.c_int)]
 
 
 class SolveInfo(C.Structure):

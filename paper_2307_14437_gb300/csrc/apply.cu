@@ -704,6 +704,18 @@ void apply_interior(gofd_problem* p, bool fp64, const void* x, void* y, cudaStre
     else apply_t<float>(p, (const float*)x, (float*)y, st);
 }
 
+void apply_interior_df(gofd_problem* p, const double* x, double* y, cudaStream_t st) {
+    if (p->d != 2) fail(GOFD_E_ARG, "the double-float product is 2D");
+    double* wg = p->gridw.as<double>();
+    afd_2d_df(p, x, nullptr, wg, 1, 0, 0, nullptr, st);
+    scatter<double>(p, wg, y, 1.0, st);
+}
+
+void apply_interior_residual(gofd_problem* p, const double* x, double* y, cudaStream_t st) {
+    if (p->d == 2 && p->opt.fp64_residual == 0) apply_interior_df(p, x, y, st);
+    else apply_interior(p, true, x, y, st);
+}
+
 void apply_interior_symbol(gofd_problem* p, bool fp64, const void* x, void* y, const void* lamT, cudaStream_t st) {
     if (p->d != 2) fail(GOFD_E_ARG, "a replaced symbol is supported in 2D only");
     GroupArg ga;
@@ -753,7 +765,7 @@ int apply_interior_profiled(gofd_problem* p, bool fp64, const void* x, void* y, 
 // the scratch of the batch workspace; otherwise one product per vector.
 void apply_interior_batch(gofd_problem* p, bool fp64, const void* x, void* y, int nb, int64_t ld, void* grid_ws,
                           void* spec_ws, void* partial_ws, void* counter_ws, cudaStream_t st, const int* skip,
-                          int skip_stride) {
+                          int skip_stride, bool df) {
     if (p->d == 2) {
         // columns in sub-batches of p->tune_bchunk (0: all at once); each
         // sub-batch reuses the first workspace slots, so a small one keeps its
@@ -770,7 +782,8 @@ void apply_interior_batch(gofd_problem* p, bool fp64, const void* x, void* y, in
             ga.skip_stride = skip_stride;
             ga.col0 = c0;
             if (fp64) {
-                afd_2d_f64(p, (const double*)xc, nullptr, (double*)grid_ws, k, ld, ws, spec_ws, st, ga);
+                if (df) afd_2d_df(p, (const double*)xc, nullptr, (double*)grid_ws, k, ld, ws, spec_ws, st, ga);
+                else afd_2d_f64(p, (const double*)xc, nullptr, (double*)grid_ws, k, ld, ws, spec_ws, st, ga);
                 scatter_b<double>(p, (const double*)grid_ws, (double*)yc, 1.0, k, ws, ld, (double*)partial_ws,
                                   (unsigned*)counter_ws, st, ga);
             } else {
@@ -791,10 +804,12 @@ void apply_interior_batch(gofd_problem* p, bool fp64, const void* x, void* y, in
 // columns.  Columns have length ld; entries past an instance's n_int are zero
 // and stay zero.  rp supplies the grid, the twiddles and the launch shapes.
 void apply_interior_group(gofd_problem* rp, bool fp64, const void* x, void* y, int nbtot, int64_t ld, void* grid_ws,
-                          void* spec_ws, void* partial_ws, void* counter_ws, GroupArg ga, cudaStream_t st) {
+                          void* spec_ws, void* partial_ws, void* counter_ws, GroupArg ga, cudaStream_t st,
+                          bool df) {
     const int64_t ws = rp->ngrid;
     if (fp64) {
-        afd_2d_f64(rp, (const double*)x, nullptr, (double*)grid_ws, nbtot, ld, ws, spec_ws, st, ga);
+        if (df) afd_2d_df(rp, (const double*)x, nullptr, (double*)grid_ws, nbtot, ld, ws, spec_ws, st, ga);
+        else afd_2d_f64(rp, (const double*)x, nullptr, (double*)grid_ws, nbtot, ld, ws, spec_ws, st, ga);
         scatter_b<double>(rp, (const double*)grid_ws, (double*)y, 1.0, nbtot, ws, ld, (double*)partial_ws,
                           (unsigned*)counter_ws, st, ga);
     } else {

@@ -55,7 +55,7 @@ __device__ __forceinline__ void reg_pass(C (&v)[E], int t, int nthr, int N, int 
             const int step = (N / (Ns * R)) * twstride;
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                C w = __ldg(&tw[k * r * step]);
+                C w = cld(&tw[k * r * step]);
                 if (INV) w.y = -w.y;
                 v[q * R + r] = cmul(v[q * R + r], w);
             }
@@ -140,12 +140,12 @@ __device__ __forceinline__ void fft_ct(C (&v)[E], C* buf, int t, int g, const C*
 // gather of one grid sample: sum over the owner simplex's slots (ELL row e)
 // ---------------------------------------------------------------------------
 template <class Real, int DP1>
-__device__ __forceinline__ Real ell_value(const Real* __restrict__ x, const int32_t* __restrict__ iidx,
-                                          const Real* __restrict__ w, int64_t nloc, int64_t e) {
-    Real acc = 0;
+__device__ __forceinline__ Real ell_value(const typename Sto<Real>::T* __restrict__ x, const int32_t* __restrict__ iidx,
+                                          const typename Sto<Real>::T* __restrict__ w, int64_t nloc, int64_t e) {
+    typename Sto<Real>::T acc = 0;   // in the storage precision (FP64 for double-float)
 #pragma unroll
     for (int s = 0; s < DP1; ++s) acc += __ldg(&w[s * nloc + e]) * __ldg(&x[__ldg(&iidx[s * nloc + e])]);
-    return acc;
+    return from_sto<Real>(acc);
 }
 
 struct Runs {
@@ -157,20 +157,20 @@ struct Runs {
 template <class Real, int DP1>
 __device__ __forceinline__ Real sample(int k, const Runs& rs, const int32_t* __restrict__ run_k0,
                                        const int32_t* __restrict__ run_len, const int32_t* __restrict__ run_e0,
-                                       const Real* __restrict__ x, const int32_t* __restrict__ iidx,
-                                       const Real* __restrict__ w, int64_t nloc) {
+                                       const typename Sto<Real>::T* __restrict__ x, const int32_t* __restrict__ iidx,
+                                       const typename Sto<Real>::T* __restrict__ w, int64_t nloc) {
     if (rs.n <= 2) {
 #pragma unroll
         for (int r = 0; r < 2; ++r)
             if (r < rs.n && k >= rs.k0[r] && k < rs.k0[r] + rs.len[r])
                 return ell_value<Real, DP1>(x, iidx, w, nloc, rs.e0[r] + (k - rs.k0[r]));
-        return 0;
+        return real_zero<Real>();
     }
     for (int r = rs.rb; r < rs.rb + rs.n; ++r) {
         const int a = __ldg(&run_k0[r]);
         if (k >= a && k < a + __ldg(&run_len[r])) return ell_value<Real, DP1>(x, iidx, w, nloc, __ldg(&run_e0[r]) + (k - a));
     }
-    return 0;
+    return real_zero<Real>();
 }
 
 // ---------------------------------------------------------------------------
@@ -180,16 +180,18 @@ __device__ __forceinline__ Real sample(int k, const Runs& rs, const int32_t* __r
 // allocation is compiled for
 template <class Real, int DP1, int N, int E, int MAXT = 512, int MINB = 1>
 __global__ void __launch_bounds__(MAXT, MINB) row_fwd_t_kernel(
-    const Real* __restrict__ x, const int32_t* __restrict__ iidx, const Real* __restrict__ w, int64_t nloc,
-    const int32_t* __restrict__ run_ptr, const int32_t* __restrict__ run_k0, const int32_t* __restrict__ run_len,
-    const int32_t* __restrict__ run_e0, const Real* __restrict__ vgrid, int nlines, int n,
+    const typename Sto<Real>::T* __restrict__ x, const int32_t* __restrict__ iidx,
+    const typename Sto<Real>::T* __restrict__ w, int64_t nloc, const int32_t* __restrict__ run_ptr,
+    const int32_t* __restrict__ run_k0, const int32_t* __restrict__ run_len, const int32_t* __restrict__ run_e0,
+    const typename Sto<Real>::T* __restrict__ vgrid, int nlines, int n,
     const typename Cplx<Real>::T* __restrict__ tw, typename Cplx<Real>::T* __restrict__ specT, int ld, int lpc,
     int64_t xstride, int64_t sstride, GroupArg ga) {
     pdl_trigger();
     if (ga.iv) {   // a group: this column's instance
         const InstView& I = ga.iv[blockIdx.y / ga.nbper];
         iidx = I.ell_iidx;
-        w = sizeof(Real) == 4 ? reinterpret_cast<const Real*>(I.ell_w32) : reinterpret_cast<const Real*>(I.ell_w64);
+        w = sizeof(Real) == 4 ? reinterpret_cast<const typename Sto<Real>::T*>(I.ell_w32)
+                              : reinterpret_cast<const typename Sto<Real>::T*>(I.ell_w64);
         nloc = I.nloc;
         run_ptr = I.run_ptr;
         run_k0 = I.run_k0;
@@ -229,11 +231,11 @@ __global__ void __launch_bounds__(MAXT, MINB) row_fwd_t_kernel(
     if (vgrid || rs.n > 2) {
         each_elem_r<ct_radix_o(N, E, false, 0), E>(t, nthr, N, [&](int i, int m) {
             const int k = 2 * m;
-            Real a0 = 0, a1 = 0;
+            Real a0 = real_zero<Real>(), a1 = real_zero<Real>();
             if (active && k < n) {
                 if (vgrid) {
-                    a0 = vgrid[(int64_t)line * n + k];
-                    if (k + 1 < n) a1 = vgrid[(int64_t)line * n + k + 1];
+                    a0 = from_sto<Real>(vgrid[(int64_t)line * n + k]);
+                    if (k + 1 < n) a1 = from_sto<Real>(vgrid[(int64_t)line * n + k + 1]);
                 } else {
                     a0 = sample<Real, DP1>(k, rs, run_k0, run_len, run_e0, x, iidx, w, nloc);
                     if (k + 1 < n) a1 = sample<Real, DP1>(k + 1, rs, run_k0, run_len, run_e0, x, iidx, w, nloc);
@@ -248,8 +250,8 @@ __global__ void __launch_bounds__(MAXT, MINB) row_fwd_t_kernel(
         each_elem_r<ct_radix_o(N, E, false, 0), E>(t, nthr, N, [&](int i, int m) {
             const int k = 2 * m;
             if (k >= n) {
-                v[i].x = 0;
-                v[i].y = 0;
+                v[i].x = real_zero<Real>();
+                v[i].y = real_zero<Real>();
                 return;
             }
             int ea = -1, eb = -1;
@@ -262,14 +264,14 @@ __global__ void __launch_bounds__(MAXT, MINB) row_fwd_t_kernel(
                 }
             }
             const int64_t ca = ea >= 0 ? ea : 0, cb = eb >= 0 ? eb : 0;
-            Real a0 = 0, a1 = 0;
+            typename Sto<Real>::T a0 = 0, a1 = 0;   // the gather in the storage precision
 #pragma unroll
             for (int s = 0; s < DP1; ++s) {
                 a0 += __ldg(&w[s * nloc + ca]) * __ldg(&x[__ldg(&iidx[s * nloc + ca])]);
                 a1 += __ldg(&w[s * nloc + cb]) * __ldg(&x[__ldg(&iidx[s * nloc + cb])]);
             }
-            v[i].x = ea >= 0 ? a0 : (Real)0;
-            v[i].y = eb >= 0 ? a1 : (Real)0;
+            v[i].x = from_sto<Real>(ea >= 0 ? a0 : 0);
+            v[i].y = from_sto<Real>(eb >= 0 ? a1 : 0);
         });
     } else {
 #pragma unroll
@@ -294,9 +296,9 @@ __global__ void __launch_bounds__(MAXT, MINB) row_fwd_t_kernel(
             C mo;
             mo.x = o.y;
             mo.y = -o.x;
-            C r = cadd(e, cmul(__ldg(&tw[k]), mo));
-            r.x *= (Real)0.5;
-            r.y *= (Real)0.5;
+            C r = cadd(e, cmul(cld(&tw[k]), mo));
+            r.x *= real_half<Real>();
+            r.y *= real_half<Real>();
             X[j] = r;
         }
     }
@@ -325,15 +327,17 @@ __global__ void __launch_bounds__(MAXT, MINB) row_fwd_t_kernel(
 template <class Real, int N, int E, int MAXT = (N / E > 256 ? N / E : 256), int MINB = 1>
 __global__ void __launch_bounds__(MAXT, MINB) col_conv_t_kernel(typename Cplx<Real>::T* __restrict__ specT, int ld, int n,
                                                        int ncols, int H, const typename Cplx<Real>::T* __restrict__ tw,
-                                                       const Real* __restrict__ lamT, int64_t sstride, int pm,
+                                                       const typename Sto<Real>::T* __restrict__ lamT, int64_t sstride, int pm,
                                                        int64_t col0, GroupArg ga) {
     pdl_enter();
     if (column_skipped(ga)) return;
     if (ga.iv) {
         const InstView& I = ga.iv[blockIdx.y / ga.nbper];
-        lamT = sizeof(Real) == 4 ? reinterpret_cast<const Real*>(I.lamT32) : reinterpret_cast<const Real*>(I.lamT64);
+        lamT = sizeof(Real) == 4 ? reinterpret_cast<const typename Sto<Real>::T*>(I.lamT32)
+                                 : reinterpret_cast<const typename Sto<Real>::T*>(I.lamT64);
     } else if (sizeof(Real) == 4 ? ga.lam32 != nullptr : ga.lam64 != nullptr) {
-        lamT = sizeof(Real) == 4 ? reinterpret_cast<const Real*>(ga.lam32) : reinterpret_cast<const Real*>(ga.lam64);
+        lamT = sizeof(Real) == 4 ? reinterpret_cast<const typename Sto<Real>::T*>(ga.lam32)
+                                 : reinterpret_cast<const typename Sto<Real>::T*>(ga.lam64);
     }
     using C = typename Cplx<Real>::T;
     specT += blockIdx.y * sstride;
@@ -363,10 +367,10 @@ __global__ void __launch_bounds__(MAXT, MINB) col_conv_t_kernel(typename Cplx<Re
             const int b = (int)(cc % pm);
             lrow = a * H + (b <= pm / 2 ? b : pm - b);
         }
-        const Real* lc = lamT + lrow * H;
+        const typename Sto<Real>::T* lc = lamT + lrow * H;
         each_elem_r<ct_last<N, E, false>(), E>(t, nthr, N, [&](int i, int row) {
             const int fr = row <= N / 2 ? row : N - row;
-            const Real l = __ldg(&lc[fr]);
+            const Real l = from_sto<Real>(__ldg(&lc[fr]));
             v[i].x *= l;
             v[i].y *= l;
         });
@@ -383,7 +387,7 @@ __global__ void __launch_bounds__(MAXT, MINB) col_conv_t_kernel(typename Cplx<Re
 template <class Real, int N, int E, int MAXT = 512, int MINB = 1>
 __global__ void __launch_bounds__(MAXT, MINB) row_inv_t_kernel(const typename Cplx<Real>::T* __restrict__ specT, int ld,
                                                       int nlines, int n, const typename Cplx<Real>::T* __restrict__ tw,
-                                                      Real* __restrict__ wgrid, int lpc, int64_t sstride,
+                                                      typename Sto<Real>::T* __restrict__ wgrid, int lpc, int64_t sstride,
                                                       int64_t wstride, GroupArg ga) {
     pdl_enter();
     if (column_skipped(ga)) return;
@@ -412,7 +416,7 @@ __global__ void __launch_bounds__(MAXT, MINB) row_inv_t_kernel(const typename Cp
         const C xk = sm[g * LS + k];
         const C xc = cconj(sm[g * LS + kc]);
         const C e = cadd(xk, xc);
-        const C o = cmulc(csub(xk, xc), __ldg(&tw[k]));
+        const C o = cmulc(csub(xk, xc), cld(&tw[k]));
         C z;
         z.x = e.x - o.y;
         z.y = e.y + o.x;
@@ -422,11 +426,11 @@ __global__ void __launch_bounds__(MAXT, MINB) row_inv_t_kernel(const typename Cp
     C* buf = sm + g * spad_len(N);
     fft_ct<true, N, E, false>(v, buf, t, g, tw, 2);
     if (!active) return;
-    Real* wl = wgrid + (int64_t)line * n;
+    typename Sto<Real>::T* wl = wgrid + (int64_t)line * n;
     each_elem_r<ct_last<N, E, false>(), E>(t, nthr, N, [&](int i, int m) {
         const int k = 2 * m;
-        if (k < n) wl[k] = v[i].x;
-        if (k + 1 < n) wl[k + 1] = v[i].y;
+        if (k < n) wl[k] = to_sto<Real>(v[i].x);
+        if (k + 1 < n) wl[k + 1] = to_sto<Real>(v[i].y);
     });
 }
 

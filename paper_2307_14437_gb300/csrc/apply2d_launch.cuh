@@ -1,5 +1,8 @@
 // Host launchers of the transposed-spectrum 2D product, one precision per
-// translation unit (REAL is float or double).
+// translation unit (REAL is float, double, or dfl: double-float arithmetic
+// on FP64 inputs, weights, symbol and outputs).
+#include <type_traits>
+
 #include "apply2d.cuh"
 
 namespace gofd {
@@ -10,6 +13,13 @@ namespace {
 
 using Real = REAL;
 using C = Cplx<Real>::T;
+using S = Sto<Real>::T;   // inputs, weights, symbol and outputs
+
+const C* twiddles(const gofd_problem* p) {
+    if constexpr (std::is_same<Real, float>::value) return reinterpret_cast<const C*>(p->tw32.ptr);
+    else if constexpr (std::is_same<Real, double>::value) return reinterpret_cast<const C*>(p->tw64.ptr);
+    else return reinterpret_cast<const C*>(p->twdf.ptr);
+}
 
 // elements per thread (largest radix) of the row and column transforms
 constexpr int ct_elems_row(int N) { return N >= 4096 ? 16 : 8; }
@@ -77,54 +87,54 @@ void set_attrs(int limit) {
 // P = circulant length (column lines), rows use P/2; nb right-hand sides with
 // strides xs (input), ws (output grid) and the batch spectrum buffer
 template <int P, int EC, int ER>
-void run_e(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, int nb, int64_t xs, int64_t ws, C* S,
+void run_e(gofd_problem* p, const S* x, const S* vgrid, S* wgrid, int nb, int64_t xs, int64_t ws, C* Sp,
            cudaStream_t st, GroupArg ga) {
     constexpr int NR = P / 2, NC = P;
     constexpr int tr = NR / ER, tc = NC / EC;
     const int lpc = lines_per_cta(tr, p->tune_lpc), G = cols_per_cta(tc, p->tune_cols);
     const int n = p->n[0], H = P / 2 + 1, nlines = (int)p->nlines;
-    const C* tw = reinterpret_cast<const C*>(sizeof(Real) == 4 ? p->tw32.ptr : p->tw64.ptr);
-    const Real* lamT = reinterpret_cast<const Real*>(sizeof(Real) == 4 ? p->lamT32.ptr : p->lamT64.ptr);
-    const Real* w = reinterpret_cast<const Real*>(sizeof(Real) == 4 ? p->ell_w32.ptr : p->ell_w64.ptr);
+    const C* tw = twiddles(p);
+    const S* lamT = reinterpret_cast<const S*>(sizeof(Real) == 4 ? p->lamT32.ptr : p->lamT64.ptr);
+    const S* w = reinterpret_cast<const S*>(sizeof(Real) == 4 ? p->ell_w32.ptr : p->ell_w64.ptr);
     const int64_t ss = (int64_t)H * p->ldT;
     const unsigned rblocks = (unsigned)((nlines + lpc - 1) / lpc);
     const int64_t sb = nb > 1 ? ss : 0;
     launch_pdl(row_fwd_t_kernel<Real, 3, NR, ER>, dim3(rblocks, nb), dim3(lpc * tr), row_smem(NR, lpc), st, x,
                p->ell_iidx.as<int32_t>(), w, p->nloc, p->line_run_ptr.as<int32_t>(), p->run_k0.as<int32_t>(),
-               p->run_len.as<int32_t>(), p->run_e0.as<int32_t>(), vgrid, nlines, n, tw, S, p->ldT, lpc, xs, sb, ga);
+               p->run_len.as<int32_t>(), p->run_e0.as<int32_t>(), vgrid, nlines, n, tw, Sp, p->ldT, lpc, xs, sb, ga);
     mark_stage(st, "gather_row_fft");
-    launch_pdl(col_kernel<NC, EC>(), dim3((unsigned)((H + G - 1) / G), nb), dim3(G * tc), col_smem(NC, G), st, S,
+    launch_pdl(col_kernel<NC, EC>(), dim3((unsigned)((H + G - 1) / G), nb), dim3(G * tc), col_smem(NC, G), st, Sp,
                p->ldT, n, H, H, tw, lamT, sb, 0, (int64_t)0, ga);
     mark_stage(st, "col_fft_conv");
-    launch_pdl(row_inv_t_kernel<Real, NR, ER>, dim3(rblocks, nb), dim3(lpc * tr), row_smem(NR, lpc), st, S, p->ldT,
+    launch_pdl(row_inv_t_kernel<Real, NR, ER>, dim3(rblocks, nb), dim3(lpc * tr), row_smem(NR, lpc), st, Sp, p->ldT,
                nlines, n, tw, wgrid, lpc, sb, ws, ga);
     mark_stage(st, "row_ifft");
 }
 
 template <int P, int EC>
-void run_r(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, int nb, int64_t xs, int64_t ws, C* S,
+void run_r(gofd_problem* p, const S* x, const S* vgrid, S* wgrid, int nb, int64_t xs, int64_t ws, C* Sp,
            cudaStream_t st, GroupArg ga) {
     constexpr int ER = ct_elems_row(P / 2);
     if constexpr (sizeof(Real) == 4 && row_alt(P / 2))
         if (row_elems(P / 2, p->tune_rowe) != ER)
-            return run_e<P, EC, row_alt_elems(P / 2)>(p, x, vgrid, wgrid, nb, xs, ws, S, st, ga);
-    run_e<P, EC, ER>(p, x, vgrid, wgrid, nb, xs, ws, S, st, ga);
+            return run_e<P, EC, row_alt_elems(P / 2)>(p, x, vgrid, wgrid, nb, xs, ws, Sp, st, ga);
+    run_e<P, EC, ER>(p, x, vgrid, wgrid, nb, xs, ws, Sp, st, ga);
 }
 
 template <int P>
-void run(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, int nb, int64_t xs, int64_t ws, C* S,
+void run(gofd_problem* p, const S* x, const S* vgrid, S* wgrid, int nb, int64_t xs, int64_t ws, C* Sp,
          cudaStream_t st, GroupArg ga) {
     const int e = col_elems(P, p->tune_cole);
     if constexpr (P >= 1024 && sizeof(Real) == 4)
-        if (e == 32) return run_r<P, 32>(p, x, vgrid, wgrid, nb, xs, ws, S, st, ga);
+        if (e == 32) return run_r<P, 32>(p, x, vgrid, wgrid, nb, xs, ws, Sp, st, ga);
     if constexpr (P >= 512)
-        if (e == 16) return run_r<P, 16>(p, x, vgrid, wgrid, nb, xs, ws, S, st, ga);
-    run_r<P, 8>(p, x, vgrid, wgrid, nb, xs, ws, S, st, ga);
+        if (e == 16) return run_r<P, 16>(p, x, vgrid, wgrid, nb, xs, ws, Sp, st, ga);
+    run_r<P, 8>(p, x, vgrid, wgrid, nb, xs, ws, Sp, st, ga);
 }
 
 }  // namespace
 
-void AFD2D_FN(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, int nb, int64_t xs, int64_t ws,
+void AFD2D_FN(gofd_problem* p, const S* x, const S* vgrid, S* wgrid, int nb, int64_t xs, int64_t ws,
               void* spec, cudaStream_t st, GroupArg ga) {
     if constexpr (sizeof(Real) == 4)
         if (!vgrid && afd_2d_warp_eligible(p)) {
@@ -132,17 +142,17 @@ void AFD2D_FN(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, in
                             st, ga);
             return;
         }
-    C* S = spec ? static_cast<C*>(spec) : p->specT.as<C>();
+    C* Sp = spec ? static_cast<C*>(spec) : p->specT.as<C>();
     switch (p->P) {
-        case 32: run<32>(p, x, vgrid, wgrid, nb, xs, ws, S, st, ga); break;
-        case 64: run<64>(p, x, vgrid, wgrid, nb, xs, ws, S, st, ga); break;
-        case 128: run<128>(p, x, vgrid, wgrid, nb, xs, ws, S, st, ga); break;
-        case 256: run<256>(p, x, vgrid, wgrid, nb, xs, ws, S, st, ga); break;
-        case 512: run<512>(p, x, vgrid, wgrid, nb, xs, ws, S, st, ga); break;
-        case 1024: run<1024>(p, x, vgrid, wgrid, nb, xs, ws, S, st, ga); break;
-        case 2048: run<2048>(p, x, vgrid, wgrid, nb, xs, ws, S, st, ga); break;
-        case 4096: run<4096>(p, x, vgrid, wgrid, nb, xs, ws, S, st, ga); break;
-        case 8192: run<8192>(p, x, vgrid, wgrid, nb, xs, ws, S, st, ga); break;
+        case 32: run<32>(p, x, vgrid, wgrid, nb, xs, ws, Sp, st, ga); break;
+        case 64: run<64>(p, x, vgrid, wgrid, nb, xs, ws, Sp, st, ga); break;
+        case 128: run<128>(p, x, vgrid, wgrid, nb, xs, ws, Sp, st, ga); break;
+        case 256: run<256>(p, x, vgrid, wgrid, nb, xs, ws, Sp, st, ga); break;
+        case 512: run<512>(p, x, vgrid, wgrid, nb, xs, ws, Sp, st, ga); break;
+        case 1024: run<1024>(p, x, vgrid, wgrid, nb, xs, ws, Sp, st, ga); break;
+        case 2048: run<2048>(p, x, vgrid, wgrid, nb, xs, ws, Sp, st, ga); break;
+        case 4096: run<4096>(p, x, vgrid, wgrid, nb, xs, ws, Sp, st, ga); break;
+        case 8192: run<8192>(p, x, vgrid, wgrid, nb, xs, ws, Sp, st, ga); break;
         default: fail(GOFD_E_GRID, "unsupported circulant length");
     }
 }

@@ -301,17 +301,18 @@ struct BOp {
     gofd_problem* member(int c) const { return members ? (*members)[c / nbper] : p; }
     // skip: per-column flags (device; column c at skip[c * skip_stride]);
     // a column whose flag is set is not computed (block PCG: converged)
+    // df: an FP64 product with its convolution in double-float (2D)
     void apply(bool f64, const void* X, void* Y, int nb, int64_t ld, BatchWork* w, cudaStream_t st,
-               const int* skip = nullptr, int skip_stride = 0) const {
+               const int* skip = nullptr, int skip_stride = 0, bool df = false) const {
         if (members) {
             GroupArg g = ga;
             g.skip = skip;
             g.skip_stride = skip_stride;
             apply_interior_group(p, f64, X, Y, nb, ld, w->grid.ptr, w->spec.ptr, w->partial.ptr, w->counters.ptr, g,
-                                 st);
+                                 st, df);
         } else {
             apply_interior_batch(p, f64, X, Y, nb, ld, w->grid.ptr, w->spec.ptr, w->partial.ptr, w->counters.ptr, st,
-                                 skip, skip_stride);
+                                 skip, skip_stride, df);
         }
     }
 };
@@ -471,7 +472,9 @@ static void solve_cols(const BOp& op, BatchWork* w, const Cols& cols, gofd_solve
         if (rounds == 0) {
             bcopy_kernel<double><<<vg, 256, 0, st>>>(B, R, n, ld);
         } else {
-            op.apply(true, X, w->q64.ptr, nb, ld, w, st);
+            // FP64 residual; in mixed mode its convolution in double-float (2D)
+            const bool df = mode == GOFD_SOLVE_MIXED && p->d == 2 && p->opt.fp64_residual == 0;
+            op.apply(true, X, w->q64.ptr, nb, ld, w, st, nullptr, 0, df);
             bresidual_kernel<<<vg, 256, 0, st>>>(B, w->q64.as<double>(), R, n, ld);
         }
         GOFD_CHECK_LAUNCH();

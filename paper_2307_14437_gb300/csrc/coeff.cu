@@ -137,12 +137,16 @@ __global__ void symbol_finish_kernel(const double* __restrict__ lam, double* __r
     }
 }
 
-__global__ void twiddle_kernel(double2* __restrict__ t64, float2* __restrict__ t32, int P) {
+// e^{-2 pi i m / P} in FP64, FP32 and double-float (hi, lo of the real part,
+// then of the imaginary part)
+__global__ void twiddle_kernel(double2* __restrict__ t64, float2* __restrict__ t32, float4* __restrict__ tdf, int P) {
     for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < P; m += gridDim.x * blockDim.x) {
         double sn, cs;
         sincospi(2.0 * (double)m / (double)P, &sn, &cs);
         t64[m] = make_double2(cs, -sn);
         t32[m] = make_float2((float)cs, (float)-sn);
+        const float ch = (float)cs, sh = (float)-sn;
+        tdf[m] = make_float4(ch, (float)(cs - (double)ch), sh, (float)(-sn - (double)sh));
     }
 }
 
@@ -297,7 +301,9 @@ void setup_coefficients(gofd_problem* p) {
     GOFD_CHECK_LAUNCH();
     p->tw64.alloc(sizeof(double2) * P);
     p->tw32.alloc(sizeof(float2) * P);
-    twiddle_kernel<<<grid_blocks(P, 256), 256, 0, st>>>(p->tw64.as<double2>(), p->tw32.as<float2>(), P);
+    p->twdf.alloc(sizeof(float4) * P);
+    twiddle_kernel<<<grid_blocks(P, 256), 256, 0, st>>>(p->tw64.as<double2>(), p->tw32.as<float2>(),
+                                                        p->twdf.as<float4>(), P);
     GOFD_CHECK_LAUNCH();
     GOFD_CUDA_TRY(cudaStreamSynchronize(st));
 }

@@ -13,9 +13,81 @@ template <class R> struct Cplx;
 template <> struct Cplx<float> { using T = float2; };
 template <> struct Cplx<double> { using T = double2; };
 
+// ---------------------------------------------------------------------------
+// double-float: a real number held as the unevaluated sum hi + lo of two FP32
+// numbers (|lo| <= ulp(hi)/2, about 48 significant bits), for FFTs with FP64
+// accuracy at FP32 arithmetic rates.  Sums and products use the error-free
+// transformations of Knuth (two-sum: a + b = s + e exactly, six additions)
+// and Dekker / FMA (two-product: a b = p + e exactly, p = fl(a b),
+// e = fma(a, b, -p)); the result is renormalised with a fast two-sum.  Every
+// step is a rounding intrinsic, so that the compiler cannot contract a
+// product and a sum into one FMA and lose the exactness the method relies on.
+// The sum below adds the two low parts in FP32 ("sloppy" double-float add):
+// its error is bounded by about 2^-44 (|x| + |y|), the norm-wise bound an FFT
+// needs.
+// ---------------------------------------------------------------------------
+struct dfl {
+    float hi, lo;
+};
+__host__ __device__ __forceinline__ dfl dfl_from(double d) {
+    dfl r;
+    r.hi = (float)d;
+    r.lo = (float)(d - (double)r.hi);
+    return r;
+}
+__host__ __device__ __forceinline__ double dfl_to(dfl a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ dfl dfl_fast2sum(float s, float e) {   // |s| >= |e|
+    dfl r;
+    r.hi = __fadd_rn(s, e);
+    r.lo = __fadd_rn(e, -__fadd_rn(r.hi, -s));
+    return r;
+}
+__device__ __forceinline__ dfl operator+(dfl a, dfl b) {
+    const float s = __fadd_rn(a.hi, b.hi);
+    const float bb = __fadd_rn(s, -a.hi);
+    const float e = __fadd_rn(__fadd_rn(a.hi, -__fadd_rn(s, -bb)), __fadd_rn(b.hi, -bb));
+    return dfl_fast2sum(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ dfl operator-(dfl a) { return dfl{-a.hi, -a.lo}; }
+__device__ __forceinline__ dfl operator-(dfl a, dfl b) { return a + (-b); }
+__device__ __forceinline__ dfl operator*(dfl a, dfl b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return dfl_fast2sum(p, e);
+}
+__device__ __forceinline__ dfl& operator+=(dfl& a, dfl b) { return a = a + b; }
+__device__ __forceinline__ dfl& operator*=(dfl& a, dfl b) { return a = a * b; }
+struct dfc {
+    dfl x, y;
+};
+template <> struct Cplx<dfl> { using T = dfc; };
+
+// storage type of the inputs, weights, symbol and outputs of a transform
+// computed in Real: FP64 for double-float, else Real itself
+template <class R> struct Sto { using T = R; };
+template <> struct Sto<dfl> { using T = double; };
+template <class R> __device__ __forceinline__ R from_sto(typename Sto<R>::T v) { return v; }
+template <> __device__ __forceinline__ dfl from_sto<dfl>(double v) { return dfl_from(v); }
+template <class R> __device__ __forceinline__ typename Sto<R>::T to_sto(R v) { return v; }
+template <> __device__ __forceinline__ double to_sto<dfl>(dfl v) { return dfl_to(v); }
+template <class R> __device__ __forceinline__ R real_zero() { return R(0); }
+template <> __device__ __forceinline__ dfl real_zero<dfl>() { return dfl{0.f, 0.f}; }
+template <class R> __device__ __forceinline__ R real_half() { return R(0.5); }
+template <> __device__ __forceinline__ dfl real_half<dfl>() { return dfl{0.5f, 0.f}; }
+
+// read-only load of a complex value (a double-float complex as one 16-byte load)
+template <class C> __device__ __forceinline__ C cld(const C* p) { return __ldg(p); }
+template <> __device__ __forceinline__ dfc cld<dfc>(const dfc* p) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    return dfc{dfl{v.x, v.y}, dfl{v.z, v.w}};
+}
+
 template <class C> __device__ __forceinline__ C cmk(double x, double y);
 template <> __device__ __forceinline__ float2 cmk<float2>(double x, double y) { return make_float2((float)x, (float)y); }
 template <> __device__ __forceinline__ double2 cmk<double2>(double x, double y) { return make_double2(x, y); }
+template <> __device__ __forceinline__ dfc cmk<dfc>(double x, double y) { return dfc{dfl_from(x), dfl_from(y)}; }
 
 template <class C> __device__ __forceinline__ C cadd(C a, C b) { C r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
 template <class C> __device__ __forceinline__ C csub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
@@ -172,7 +244,7 @@ __device__ __forceinline__ void stockham_pass(C* buf, int N, int Ns, int t, int 
 #pragma unroll
         for (int r = 1; r < R; ++r) {
             if (k != 0) {
-                C w = __ldg(&tw[k * r * step]);
+                C w = cld(&tw[k * r * step]);
                 if (INV) w.y = -w.y;
                 v[q * R + r] = cmul(v[q * R + r], w);
             }

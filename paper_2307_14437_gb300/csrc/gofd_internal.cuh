@@ -284,6 +284,7 @@ struct gofd_problem {
     gofd::DevBuf lam64;        // double[(P/2+1)^d], scaled by 1/P^d
     gofd::DevBuf lam32;        // float [(P/2+1)^d], scaled by 1/P^d
     gofd::DevBuf tw64, tw32;   // twiddle tables e^{-2 pi i m / L} for L = P and P/2 (concatenated)
+    gofd::DevBuf twdf;         // the P-point table in double-float (float4: re hi, re lo, im hi, im lo)
     gofd::DevBuf twp32;        // 2D warp-FFT path: W_1024^{i j} at [i*32 + j] (float2)
 
     // FFT convolution work buffers
@@ -334,6 +335,11 @@ void afd_2d_f32(gofd_problem* p, const float* x, const float* vgrid, float* wgri
                 void* spec, cudaStream_t st, GroupArg ga = GroupArg{});
 void afd_2d_f64(gofd_problem* p, const double* x, const double* vgrid, double* wgrid, int nb, int64_t xs,
                 int64_t ws, void* spec, cudaStream_t st, GroupArg ga = GroupArg{});
+// the same with FP64 inputs and outputs and the transforms in double-float
+// arithmetic (apply2d_df.cu): FP64-accurate (about 1e-13) at FP32 rates
+void afd_2d_df(gofd_problem* p, const double* x, const double* vgrid, double* wgrid, int nb, int64_t xs,
+               int64_t ws, void* spec, cudaStream_t st, GroupArg ga = GroupArg{});
+void afd_2d_attrs_df(int limit, int P, size_t* need);
 // 2D FP32 product for a 2048-point circulant, one warp per 1024-point FFT
 // (apply2d_warp.cu); used by afd_2d_f32 when eligible (default launch shapes)
 void setup_apply_2d_warp(gofd_problem* p);
@@ -342,6 +348,11 @@ void afd_2d_warp_f32(gofd_problem* p, const float* x, float* wgrid, int nb, int6
                      cudaStream_t st, GroupArg ga = GroupArg{});
 
 void apply_interior(gofd_problem* p, bool fp64, const void* x, void* y, cudaStream_t st);
+// y = S x in FP64 with the FFT convolution in double-float arithmetic (2D)
+void apply_interior_df(gofd_problem* p, const double* x, double* y, cudaStream_t st);
+// the mixed solver's FP64 residual product: apply_interior_df in 2D unless
+// opt.fp64_residual asks for plain FP64, else the FP64 product
+void apply_interior_residual(gofd_problem* p, const double* x, double* y, cudaStream_t st);
 void afd_apply_grid(gofd_problem* p, bool fp64, const void* v, void* w, cudaStream_t st);
 void afd_apply_noalloc(int d, int n, const float* lam, const float* v, float* w, cudaStream_t st);
 int apply_interior_profiled(gofd_problem* p, bool fp64, const void* x, void* y, cudaStream_t st, float* ms,
@@ -378,14 +389,16 @@ void sort_packed_rows(const int32_t* ptr, int64_t nrows, int64_t* packed, int64_
 // unsigned, zero on entry and on exit
 // skip (2D): column c is left untouched when skip[c * skip_stride] != 0
 // (device flags, read by the kernels; nullptr: every column is computed)
+// df (2D, fp64): the FFT convolution in double-float arithmetic
 void apply_interior_batch(gofd_problem* p, bool fp64, const void* x, void* y, int nb, int64_t ld, void* grid_ws,
                           void* spec_ws, void* partial_ws, void* counter_ws, cudaStream_t st,
-                          const int* skip = nullptr, int skip_stride = 0);
+                          const int* skip = nullptr, int skip_stride = 0, bool df = false);
 // a group of 2D problems on one grid (apply.cu): the view of one problem, and
 // Y[c] = S_{c / nbper} X[c] for all columns of the group in one launch sequence
 InstView inst_view(const gofd_problem* p);
 void apply_interior_group(gofd_problem* rp, bool fp64, const void* x, void* y, int nbtot, int64_t ld, void* grid_ws,
-                          void* spec_ws, void* partial_ws, void* counter_ws, GroupArg ga, cudaStream_t st);
+                          void* spec_ws, void* partial_ws, void* counter_ws, GroupArg ga, cudaStream_t st,
+                          bool df = false);
 // y = I^T C I x (2D, interior-compacted vectors) with the column kernels'
 // symbol replaced by lamT (FP32 or FP64 as the precision, layout of lamT32)
 void apply_interior_symbol(gofd_problem* p, bool fp64, const void* x, void* y, const void* lamT, cudaStream_t st);

@@ -424,7 +424,9 @@ void solve_core(gofd_problem* p, gofd_solve_mode mode, const double* b, double t
         if (outer == 0 && init_zero) {
             copy_kernel<double><<<nb, 256, 0, st>>>(b, r, n);
         } else {
-            apply_interior(p, true, x, w->q64.ptr, st);
+            // FP64 residual; in mixed mode its convolution in double-float (2D)
+            if (mode == GOFD_SOLVE_MIXED) apply_interior_residual(p, x, w->q64.as<double>(), st);
+            else apply_interior(p, true, x, w->q64.ptr, st);
             residual_kernel<<<nb, 256, 0, st>>>(b, w->q64.as<double>(), r, n);
         }
         GOFD_CHECK_LAUNCH();

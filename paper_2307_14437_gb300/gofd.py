@@ -36,7 +36,7 @@ def _ptr(t) -> C.c_void_p:
     return C.c_void_p(t.data_ptr())
 
 
-_PREC = {"fp64": N.FP64, "fp32": N.FP32}
+_PREC = {"fp64": N.FP64, "fp32": N.FP32, "fp64_df": N.FP64_DF}
 _OPS = {"stiffness": N.OP_STIFFNESS, "fraclap": N.OP_FRACLAP}
 _MODES = {"fp64": N.SOLVE_FP64, "mixed": N.SOLVE_MIXED}
 _RHS = {"grid": N.RHS_GRID, "vertex": N.RHS_VERTEX}
@@ -47,7 +47,8 @@ class Problem:
 
     def __init__(self, vertices, simplices, alpha: float, h: float, box_lo, box_hi, *, precond: int = 0,
                  ic_level: int = 1, filon_M: int = 0, richardson_levels: int = 0, inner_tol: float = 0.0,
-                 check_every: int = 0, wait_budget_cycles: int = 0, ordering: int = 0, chunk_planes: int = 0):
+                 check_every: int = 0, wait_budget_cycles: int = 0, ordering: int = 0, chunk_planes: int = 0,
+                 fp64_residual: int = 0):
         self._lib = N.load()
         v = np.ascontiguousarray(vertices, dtype=np.float64)
         s = np.ascontiguousarray(simplices, dtype=np.int32)
@@ -59,7 +60,7 @@ class Problem:
         opt = N.Options(precond=precond, ic_level=ic_level, filon_M=filon_M,
                         richardson_levels=richardson_levels, wait_budget_cycles=wait_budget_cycles,
                         inner_tol=inner_tol, check_every=check_every, ordering=ordering,
-                        chunk_planes=chunk_planes)
+                        chunk_planes=chunk_planes, fp64_residual=fp64_residual)
         h_ = C.c_void_p()
         st = self._lib.gofd_build(self.d, v.ctypes.data, v.shape[0], s.ctypes.data, s.shape[0], float(alpha),
                                   float(h), lo.ctypes.data, hi.ctypes.data, C.byref(opt), C.byref(h_))
@@ -154,9 +155,14 @@ class Problem:
         self._check(self._lib.gofd_apply(self._h, _OPS[op], _PREC[prec], _ptr(u), _ptr(out), _stream_ptr(stream)))
         return out
 
-    def apply_interior(self, x, y, stream=None):
+    def apply_interior(self, x, y, stream=None, prec=None):
+        """y = S x on interior-compacted vectors.  prec: "fp32" / "fp64" (by
+        default from the dtype) or "fp64_df" (float64 vectors, 2D: the FFT
+        convolution in double-float arithmetic, as in the mixed solver's
+        residual)."""
         torch = _torch()
-        prec = "fp64" if x.dtype == torch.float64 else "fp32"
+        if prec is None:
+            prec = "fp64" if x.dtype == torch.float64 else "fp32"
         self._check(self._lib.gofd_apply_interior(self._h, _PREC[prec], _ptr(x), _ptr(y), _stream_ptr(stream)))
         return y
 

@@ -67,7 +67,7 @@ typedef enum {
     GOFD_E_NOMEM = 11               /* device or host allocation failed                            */
 } gofd_status;
 
-/* GOFD_FP64_DF (2D, gofd_apply_interior only): FP64 inputs and outputs, the
+/* GOFD_FP64_DF (2D and 3D, gofd_apply_interior only): FP64 inputs and outputs, the
  * gather and scatter in FP64, the FFT convolution in double-float arithmetic
  * (pairs of FP32 numbers, about 48 significant bits): the mixed solver's
  * residual product, within about 1e-13 of the FP64 product. */
@@ -106,7 +106,7 @@ typedef struct {
     int chunk_planes;          /* 3D: spectrum planes k_x0 per chunk of the axis-1/axis-2 stage; 0 = as many as fit a
                                   1 GiB middle buffer.  Bounds memory; results do not depend on it                    */
     int fp64_residual;         /* mixed mode, the FP64 residual b - S x of each refinement step: 0 = its convolution
-                                  in double-float arithmetic in 2D (gather and scatter in FP64; FP64 elsewhere),
+                                  in double-float arithmetic in 2D and 3D (gather and scatter in FP64; FP64 in 1D),
                                   1 = plain FP64 throughout.  FP64 mode always uses plain FP64                     */
 } gofd_options;
 

@@ -182,7 +182,7 @@ gofd_status gofd_apply_interior(gofd_problem* p, gofd_precision prec, const void
         if (!x_dev || !y_dev) gofd::fail(GOFD_E_ARG, "NULL vector");
         if (prec != GOFD_FP64 && prec != GOFD_FP32 && prec != GOFD_FP64_DF) gofd::fail(GOFD_E_ARG, "bad precision");
         if (prec == GOFD_FP64_DF) {
-            if (p->d != 2) gofd::fail(GOFD_E_ARG, "GOFD_FP64_DF is supported in 2D");
+            if (p->d < 2) gofd::fail(GOFD_E_ARG, "GOFD_FP64_DF is supported in 2D and 3D");
             gofd::apply_interior_df(p, (const double*)x_dev, (double*)y_dev, (cudaStream_t)stream);
         } else {
             gofd::apply_interior(p, prec == GOFD_FP64, x_dev, y_dev, (cudaStream_t)stream);

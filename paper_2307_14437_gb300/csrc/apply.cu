@@ -705,14 +705,15 @@ void apply_interior(gofd_problem* p, bool fp64, const void* x, void* y, cudaStre
 }
 
 void apply_interior_df(gofd_problem* p, const double* x, double* y, cudaStream_t st) {
-    if (p->d != 2) fail(GOFD_E_ARG, "the double-float product is 2D");
+    if (p->d != 2 && p->d != 3) fail(GOFD_E_ARG, "the double-float product is 2D and 3D");
     double* wg = p->gridw.as<double>();
-    afd_2d_df(p, x, nullptr, wg, 1, 0, 0, nullptr, st);
+    if (p->d == 2) afd_2d_df(p, x, nullptr, wg, 1, 0, 0, nullptr, st);
+    else afd_3d_df(p, x, nullptr, wg, st);
     scatter<double>(p, wg, y, 1.0, st);
 }
 
 void apply_interior_residual(gofd_problem* p, const double* x, double* y, cudaStream_t st) {
-    if (p->d == 2 && p->opt.fp64_residual == 0) apply_interior_df(p, x, y, st);
+    if (p->d >= 2 && p->opt.fp64_residual == 0) apply_interior_df(p, x, y, st);
     else apply_interior(p, true, x, y, st);
 }
 
@@ -795,8 +796,12 @@ void apply_interior_batch(gofd_problem* p, bool fp64, const void* x, void* y, in
         return;
     }
     const size_t b = fp64 ? 8 : 4;
-    for (int k = 0; k < nb; ++k)
-        apply_interior(p, fp64, (const char*)x + k * ld * b, (char*)y + k * ld * b, st);
+    for (int k = 0; k < nb; ++k) {
+        const char* xk = (const char*)x + k * ld * b;
+        char* yk = (char*)y + k * ld * b;
+        if (fp64 && df && p->d == 3) apply_interior_df(p, (const double*)xk, (double*)yk, st);
+        else apply_interior(p, fp64, xk, yk, st);
+    }
 }
 
 // Y[c] = S_i X[c] for the columns of a group of 2D problems on one grid

@@ -58,10 +58,11 @@ void setup_apply_3d(gofd_problem* p) {
     GOFD_CHECK_LAUNCH();
     int limit = 0;
     GOFD_CUDA_TRY(cudaDeviceGetAttribute(&limit, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device));
-    size_t n32 = 0, n64 = 0;
+    size_t n32 = 0, n64 = 0, ndf = 0;
     afd_3d_attrs_f32(limit, p->P, &n32);
     afd_3d_attrs_f64(limit, p->P, &n64);
-    if (std::max(n32, n64) > (size_t)limit) fail(GOFD_E_GRID, "FFT line does not fit in shared memory");
+    afd_3d_attrs_df(limit, p->P, &ndf);
+    if (std::max({n32, n64, ndf}) > (size_t)limit) fail(GOFD_E_GRID, "FFT line does not fit in shared memory");
 }
 
 void setup_apply_2d(gofd_problem* p) {

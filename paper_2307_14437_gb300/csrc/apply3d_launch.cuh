@@ -1,6 +1,9 @@
 // Host launchers of the 3D product, one precision per translation unit
-// (REAL is float or double): axis-0 row kernels over the n^2 grid lines,
+// (REAL is float, double, or dfl: double-float arithmetic on FP64 inputs,
+// weights, symbol and outputs): axis-0 row kernels over the n^2 grid lines,
 // then per k_x0 plane the (axis 1, axis 2) convolution of apply3d.cuh.
+#include <type_traits>
+
 #include "apply3d.cuh"
 
 namespace gofd {
@@ -11,6 +14,13 @@ namespace {
 
 using Real = REAL;
 using C = Cplx<Real>::T;
+using S = Sto<Real>::T;   // inputs, weights, symbol and outputs
+
+const C* twiddles3(const gofd_problem* p) {
+    if constexpr (std::is_same<Real, float>::value) return reinterpret_cast<const C*>(p->tw32.ptr);
+    else if constexpr (std::is_same<Real, double>::value) return reinterpret_cast<const C*>(p->tw64.ptr);
+    else return reinterpret_cast<const C*>(p->twdf.ptr);
+}
 
 constexpr int ct3_elems(int N) { return N >= 4096 ? 16 : 8; }
 // elements per thread of the axis-2 column transform: 8, 16 or 32 (32 in FP32
@@ -55,21 +65,21 @@ void set_attrs3(int limit) {
 }
 
 template <int P, int ECC, int EC>
-void run3_e(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, cudaStream_t st) {
+void run3_e(gofd_problem* p, const S* x, const S* vgrid, S* wgrid, cudaStream_t st) {
     constexpr int NR = P / 2, NC = P, ER = ct3_elems(NR);
     constexpr int tr = NR / ER, tc = NC / EC, tcc = NC / ECC;
     const int lpc = rows_per_cta(tr), G = groups_per_cta(tc), GC = groups_per_cta(tcc);
     const int n = p->n[0], H = P / 2 + 1, nlines = (int)p->nlines;
-    const C* tw = reinterpret_cast<const C*>(sizeof(Real) == 4 ? p->tw32.ptr : p->tw64.ptr);
-    const Real* lamT = reinterpret_cast<const Real*>(sizeof(Real) == 4 ? p->lamT32.ptr : p->lamT64.ptr);
-    const Real* w = reinterpret_cast<const Real*>(sizeof(Real) == 4 ? p->ell_w32.ptr : p->ell_w64.ptr);
-    C* S = p->specT.as<C>();
+    const C* tw = twiddles3(p);
+    const S* lamT = reinterpret_cast<const S*>(sizeof(Real) == 4 ? p->lamT32.ptr : p->lamT64.ptr);
+    const S* w = reinterpret_cast<const S*>(sizeof(Real) == 4 ? p->ell_w32.ptr : p->ell_w64.ptr);
+    C* Sp = p->specT.as<C>();
     C* M = p->specM.as<C>();
     const int64_t ld = p->ldT;
     const unsigned rblocks = (unsigned)((nlines + lpc - 1) / lpc);
     launch_pdl(row_fwd_t_kernel<Real, 4, NR, ER>, dim3(rblocks), dim3(lpc * tr), row_smem3(NR, lpc), st, x,
                p->ell_iidx.as<int32_t>(), w, p->nloc, p->line_run_ptr.as<int32_t>(), p->run_k0.as<int32_t>(),
-               p->run_len.as<int32_t>(), p->run_e0.as<int32_t>(), vgrid, nlines, n, tw, S, (int)ld, lpc,
+               p->run_len.as<int32_t>(), p->run_e0.as<int32_t>(), vgrid, nlines, n, tw, Sp, (int)ld, lpc,
                (int64_t)0, (int64_t)0, GroupArg{});
     mark_stage(st, "gather_row_fft");
     const int ngroups = (n + G - 1) / G;
@@ -78,28 +88,28 @@ void run3_e(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, cuda
     for (int k0 = 0; k0 < H; k0 += p->midK) {
         const int kc = std::min(p->midK, H - k0);
         launch_pdl(plane_fwd_t_kernel<Real, NC, EC>, dim3((unsigned)(kc * ngroups)), dim3(G * tc), mid_smem3(NC, G),
-                   st, (const C*)S, ld, M, n, ngroups, k0, tw);
+                   st, (const C*)Sp, ld, M, n, ngroups, k0, tw);
         launch_pdl(col3_kernel<NC, ECC>(), dim3((unsigned)(((int64_t)kc * P + GC - 1) / GC)),
                    dim3(GC * tcc), mid_smem3(NC, GC), st, M, n, n, (int)((int64_t)kc * P), H, tw, lamT, (int64_t)0,
                    P, (int64_t)k0 * P, GroupArg{});
         launch_pdl(plane_inv_t_kernel<Real, NC, EC>, dim3((unsigned)(kc * ngroups)), dim3(G * tc), mid_smem3(NC, G),
-                   st, (const C*)M, n, ngroups, k0, S, ld, tw);
+                   st, (const C*)M, n, ngroups, k0, Sp, ld, tw);
     }
     mark_stage(st, "axis12_conv");
-    launch_pdl(row_inv_t_kernel<Real, NR, ER>, dim3(rblocks), dim3(lpc * tr), row_smem3(NR, lpc), st, (const C*)S,
+    launch_pdl(row_inv_t_kernel<Real, NR, ER>, dim3(rblocks), dim3(lpc * tr), row_smem3(NR, lpc), st, (const C*)Sp,
                (int)ld, nlines, n, tw, wgrid, lpc, (int64_t)0, (int64_t)0, GroupArg{});
     mark_stage(st, "row_ifft");
 }
 
 template <int P, int ECC>
-void run3_p(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, cudaStream_t st) {
+void run3_p(gofd_problem* p, const S* x, const S* vgrid, S* wgrid, cudaStream_t st) {
     if constexpr (sizeof(Real) == 4 && col3_alt(P))
         if (plane3_elems(P, p->tune_rowe) == 16) return run3_e<P, ECC, 16>(p, x, vgrid, wgrid, st);
     run3_e<P, ECC, ct3_elems(P)>(p, x, vgrid, wgrid, st);
 }
 
 template <int P>
-void run3(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, cudaStream_t st) {
+void run3(gofd_problem* p, const S* x, const S* vgrid, S* wgrid, cudaStream_t st) {
     if constexpr (col3_alt(P)) {
         const int e = col3_elems(P, p->tune_cole);
         if constexpr (sizeof(Real) == 4)
@@ -111,7 +121,7 @@ void run3(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, cudaSt
 
 }  // namespace
 
-void AFD3D_FN(gofd_problem* p, const Real* x, const Real* vgrid, Real* wgrid, cudaStream_t st) {
+void AFD3D_FN(gofd_problem* p, const S* x, const S* vgrid, S* wgrid, cudaStream_t st) {
     switch (p->P) {
         case 32: run3<32>(p, x, vgrid, wgrid, st); break;
         case 64: run3<64>(p, x, vgrid, wgrid, st); break;

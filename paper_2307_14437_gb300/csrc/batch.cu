@@ -473,7 +473,7 @@ static void solve_cols(const BOp& op, BatchWork* w, const Cols& cols, gofd_solve
             bcopy_kernel<double><<<vg, 256, 0, st>>>(B, R, n, ld);
         } else {
             // FP64 residual; in mixed mode its convolution in double-float (2D)
-            const bool df = mode == GOFD_SOLVE_MIXED && p->d == 2 && p->opt.fp64_residual == 0;
+            const bool df = mode == GOFD_SOLVE_MIXED && p->d >= 2 && p->opt.fp64_residual == 0;
             op.apply(true, X, w->q64.ptr, nb, ld, w, st, nullptr, 0, df);
             bresidual_kernel<<<vg, 256, 0, st>>>(B, w->q64.as<double>(), R, n, ld);
         }

@@ -329,6 +329,8 @@ void setup_apply_2d(gofd_problem* p);
 void setup_apply_3d(gofd_problem* p);
 void afd_3d_f32(gofd_problem* p, const float* x, const float* vgrid, float* wgrid, cudaStream_t st);
 void afd_3d_f64(gofd_problem* p, const double* x, const double* vgrid, double* wgrid, cudaStream_t st);
+void afd_3d_df(gofd_problem* p, const double* x, const double* vgrid, double* wgrid, cudaStream_t st);
+void afd_3d_attrs_df(int limit, int P, size_t* need);
 // nb right-hand sides: inputs at x + b*xs (or vgrid + b*xs), outputs at wgrid + b*ws;
 // spec = batch spectrum buffer (nb x (P/2+1) x ldT complex) or NULL for one vector
 void afd_2d_f32(gofd_problem* p, const float* x, const float* vgrid, float* wgrid, int nb, int64_t xs, int64_t ws,
@@ -348,9 +350,9 @@ void afd_2d_warp_f32(gofd_problem* p, const float* x, float* wgrid, int nb, int6
                      cudaStream_t st, GroupArg ga = GroupArg{});
 
 void apply_interior(gofd_problem* p, bool fp64, const void* x, void* y, cudaStream_t st);
-// y = S x in FP64 with the FFT convolution in double-float arithmetic (2D)
+// y = S x in FP64 with the FFT convolution in double-float arithmetic (2D, 3D)
 void apply_interior_df(gofd_problem* p, const double* x, double* y, cudaStream_t st);
-// the mixed solver's FP64 residual product: apply_interior_df in 2D unless
+// the mixed solver's FP64 residual product: apply_interior_df in 2D and 3D unless
 // opt.fp64_residual asks for plain FP64, else the FP64 product
 void apply_interior_residual(gofd_problem* p, const double* x, double* y, cudaStream_t st);
 void afd_apply_grid(gofd_problem* p, bool fp64, const void* v, void* w, cudaStream_t st);

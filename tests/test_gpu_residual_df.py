@@ -1,7 +1,8 @@
 """The mixed solver's FP64 residual product with its FFT convolution in
-double-float arithmetic (GOFD_FP64_DF): S x (Section 3.2, (GoFD-2); A_FD by
-the circulant convolution of Section 2.2) against the oracle's FP64 product,
-at the bar for counting as FP64 (1e-12 relative), and mixed solves with it.
+double-float arithmetic (GOFD_FP64_DF, 2D and 3D): S x (Section 3.2,
+(GoFD-2); A_FD by the circulant convolution of Section 2.2) against the
+oracle's FP64 product, at the bar for counting as FP64 (1e-12 relative), and
+mixed solves with it.
 """
 import numpy as np
 import pytest
@@ -66,11 +67,37 @@ def test_double_float_product_is_fp64_accurate(name):
     gp.close()
 
 
-def test_double_float_is_2d_only():
-    from paper_2307_14437_gb300 import GofdError, Problem
-    v, s = mg.ball_shell_mesh(shells=3, seed=mg.seed_for(3, 3))
-    lo, hi, h = mg.grid_box(3, 11)
+@pytest.mark.parametrize("n", [17, 29])
+def test_double_float_product_is_fp64_accurate_in_3d(n):
+    from paper_2307_14437_gb300 import Problem
+    v, s = mg.ball_shell_mesh(shells=4, seed=mg.seed_for(3, 50))
+    lo, hi, h = mg.grid_box(3, n)
     gp = Problem(v, s, 1.5, h, lo, hi, filon_M=2 ** 8)
+    ref = o.build(3, v, s, 1.5, h, lo, hi, exact_weights=False, pruned=True, M=2 ** 8)
+    ii, _ = gp.export_vertex_data()
+    iv = np.nonzero(ii >= 0)[0]
+    u = np.zeros(len(v))
+    u[iv] = mg.random_vector(len(v), 54)[iv]
+    want = o.stiffness_apply(ref, u)[iv]
+    x = np.zeros(len(iv) + 1)
+    x[ii[iv]] = u[iv]
+    y = torch.zeros(len(iv) + 1, dtype=torch.float64, device="cuda")
+    gp.apply_interior(torch.tensor(x, device="cuda"), y, prec="fp64_df")
+    got = y.cpu().numpy()[ii[iv]]
+    assert np.linalg.norm(got - want) <= 1e-12 * np.linalg.norm(want)
+    # the mixed solve with it reaches the tolerance with the oracle's operator
+    f = torch.ones(gp.n_grid, dtype=torch.float64, device="cuda")
+    uu, info = gp.solve(f, mode="mixed", tol=1e-9)
+    b = o.rhs_grid(ref, np.ones(ref.n_grid))
+    assert np.linalg.norm(b - o.stiffness_apply(ref, uu.cpu().numpy())) <= 1.05e-9 * np.linalg.norm(b)
+    gp.close()
+
+
+def test_double_float_is_not_for_1d():
+    from paper_2307_14437_gb300 import GofdError, Problem
+    v, s = mg.interval_mesh(24, seed=mg.seed_for(0, 2))
+    lo, hi, h = mg.grid_box(1, 49)
+    gp = Problem(v, s, 1.2, h, lo, hi, filon_M=2 ** 12)
     x = torch.zeros(gp.n_interior + 1, dtype=torch.float64, device="cuda")
     with pytest.raises(GofdError) as e:
         gp.apply_interior(x, torch.empty_like(x), prec="fp64_df")

@@ -110,6 +110,7 @@ gofd_status gofd_build(int d, const double* vertices, int64_t n_v, const int32_t
 
         p = new gofd_problem();
         p->device = dev;
+        GOFD_CUDA_TRY(cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, dev));
         p->d = d;
         p->nv = n_v;
         p->ne = n_e;

@@ -672,7 +672,9 @@ static void scatter_b(gofd_problem* p, const Real* wgrid, Real* y, Real scale, i
         mark_stage(st, "scatter");
         return;
     }
-    const unsigned nshort = (unsigned)grid_blocks(p->nint * tpr, threads, 1 << 20);
+    // at most one wave of CTAs (the short-row loop is grid-stride): a second
+    // wave cannot load its first entries while the previous kernel finishes
+    const unsigned nshort = (unsigned)grid_blocks(p->nint * tpr, threads, p->sm_count * (2048 / threads));
     const dim3 grid(nshort + (unsigned)p->n_long_chunks, nb);
 #define SCAT(TPR)                                                                                              \
     launch_pdl(scatter_kernel<Real, TPR>, grid, dim3(threads), 0, st, p->csr_ptr.as<int32_t>(),                   \

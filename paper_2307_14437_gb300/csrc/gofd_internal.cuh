@@ -235,6 +235,7 @@ struct gofd_problem {
     int rich_levels = 4;
     gofd_options opt{};
     cudaStream_t setup_stream = nullptr;
+    int sm_count = 152;   // multiprocessors of the device (set at build)
     int device = 0;
 
     // mesh on the device

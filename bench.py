@@ -383,7 +383,8 @@ def run_gofd(args):
         e2e_ms.append((time.perf_counter() - t1) * 1e3)
     e2e_t = statistics.mean(e2e_ms)
     e2e = {"value": round(world * B32 / (e2e_t * 1e-3) / 1e9, 2), "unit": "GB/s",
-           "h2d_bytes_per_step": 4 * n_v, "d2h_bytes_per_step": 4 * n_v, "ms_per_step": round(e2e_t, 4)}
+           "h2d_bytes_per_step": 4 * n_v, "d2h_bytes_per_step": 4 * n_v, "ms_per_step": round(e2e_t, 4),
+           "note": "pinned host buffers, read and written in place by the kernels over the CPU-GPU link"}
 
     # the FP64 product: bound by FP64 arithmetic (its FFT passes); roofline
     # against the measured FP64 FMA rate, with the unpruned FFT flop count

@@ -207,9 +207,12 @@ gofd_status gofd_precond_apply(gofd_problem* p, gofd_precision prec, const void*
                                void* stream);
 
 /*
- * gofd_apply_host -- gofd_apply on host buffers (N_v values each): copies u to
- * the device, applies, copies y back, and synchronises the stream.  The first
- * call allocates two N_v device staging vectors that the handle keeps.
+ * gofd_apply_host -- gofd_apply on host buffers (N_v values each), and
+ * synchronises the stream.  Pinned host buffers (cudaHostAlloc /
+ * cudaMallocHost, or registered) are mapped into the device's address space:
+ * the kernels read u and write y there directly.  Pageable buffers are
+ * copied through two N_v device staging vectors that the first such call
+ * allocates and the handle keeps.
  */
 gofd_status gofd_apply_host(gofd_problem* p, gofd_op op, gofd_precision prec,
                             const void* u_host, void* y_host, void* stream);

@@ -249,7 +249,21 @@ gofd_status gofd_apply_host(gofd_problem* p, gofd_op op, gofd_precision prec, co
         if (!u_host || !y_host) gofd::fail(GOFD_E_ARG, "NULL vector");
         cudaStream_t st = (cudaStream_t)stream;
         const size_t bytes = (prec == GOFD_FP64 ? 8 : 4) * (size_t)p->nv;
-        // staging buffers are allocated on the first host call and kept by the handle
+        // pinned host buffers are mapped into the device's address space: the
+        // compaction kernel reads u and the expansion kernel writes y there
+        // directly (over the CPU-GPU link), with no staging copies
+        cudaPointerAttributes au{}, ay{};
+        const bool mapped = cudaPointerGetAttributes(&au, u_host) == cudaSuccess && au.type == cudaMemoryTypeHost &&
+                            au.devicePointer && cudaPointerGetAttributes(&ay, y_host) == cudaSuccess &&
+                            ay.type == cudaMemoryTypeHost && ay.devicePointer;
+        cudaGetLastError();   // a pageable pointer is not an error here
+        if (mapped) {
+            gofd_status s = gofd_apply(p, op, prec, au.devicePointer, ay.devicePointer, stream);
+            if (s != GOFD_OK) throw gofd::Error{s, p->last_error};
+            GOFD_CUDA_TRY(cudaStreamSynchronize(st));
+            return GOFD_OK;
+        }
+        // otherwise staging buffers, allocated on the first such call and kept by the handle
         if (p->stage_u.bytes < bytes) p->stage_u.alloc(bytes);
         if (p->stage_y.bytes < bytes) p->stage_y.alloc(bytes);
         gofd::DevBuf& u = p->stage_u;

@@ -448,12 +448,16 @@ __global__ void __launch_bounds__(PACK_THREADS) scatter_packed_kernel(
     }
 }
 
+// x[v2i[v]] = u[v] for the interior vertices, x[n_int] = 0: u is read in vertex
+// order (coalesced also when it lives in mapped host memory)
 template <class Real>
-__global__ void compact_kernel(const Real* __restrict__ u, const int32_t* __restrict__ i2v, int64_t nint,
-                               Real* __restrict__ x) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i <= nint;
-         i += (int64_t)gridDim.x * blockDim.x)
-        x[i] = (i < nint) ? u[i2v[i]] : (Real)0;
+__global__ void compact_kernel(const Real* __restrict__ u, const int32_t* __restrict__ v2i, int64_t nv,
+                               int64_t nint, Real* __restrict__ x) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = v2i[v];
+        if (i >= 0) x[i] = u[v];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) x[nint] = (Real)0;
 }
 
 template <class Real>
@@ -875,11 +879,11 @@ void afd_apply_grid(gofd_problem* p, bool fp64, const void* v, void* w, cudaStre
 
 void compact_vertex(gofd_problem* p, bool fp64, const void* u, void* x, cudaStream_t st) {
     if (fp64)
-        compact_kernel<double><<<grid_blocks(p->nint + 1, 256), 256, 0, st>>>(
-            (const double*)u, p->int2vert.as<int32_t>(), p->nint, (double*)x);
+        compact_kernel<double><<<grid_blocks(p->nv, 256), 256, 0, st>>>(
+            (const double*)u, p->vert2int.as<int32_t>(), p->nv, p->nint, (double*)x);
     else
-        compact_kernel<float><<<grid_blocks(p->nint + 1, 256), 256, 0, st>>>(
-            (const float*)u, p->int2vert.as<int32_t>(), p->nint, (float*)x);
+        compact_kernel<float><<<grid_blocks(p->nv, 256), 256, 0, st>>>(
+            (const float*)u, p->vert2int.as<int32_t>(), p->nv, p->nint, (float*)x);
     GOFD_CHECK_LAUNCH();
 }
 

@@ -199,7 +199,8 @@ class Problem:
         return [(names[i].decode(), float(ms[i])) for i in range(cnt.value)]
 
     def apply_host(self, u: np.ndarray, op: str = "stiffness", out: np.ndarray | None = None, stream=None):
-        """The apply on host buffers (copies inside the call)."""
+        """The apply on host buffers: pinned ones are read and written by the
+        kernels in place (mapped host memory), pageable ones copied."""
         prec = "fp64" if u.dtype == np.float64 else "fp32"
         u = np.ascontiguousarray(u)
         if out is None:

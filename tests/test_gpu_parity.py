@@ -185,6 +185,24 @@ def test_apply_host_matches_device(built):
     assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("name", ["disk37_ragged", "ball9"])
+def test_apply_host_on_pinned_buffers(built, name):
+    # pinned host buffers are read and written by the kernels in place (mapped
+    # memory); a pinned input with a pageable output takes the staging copies
+    gp, ref = built(name)
+    u = mg.random_vector(len(ref.verts), 16)
+    for dt in (torch.float64, torch.float32):
+        ud = torch.tensor(u, dtype=dt, device="cuda")
+        uh = torch.tensor(u, dtype=dt).pin_memory()
+        yh = torch.empty_like(uh).pin_memory()
+        for op in ("stiffness", "fraclap"):
+            want = gp.apply(ud, op=op).cpu().numpy()
+            gp.apply_host(uh.numpy(), op=op, out=yh.numpy())
+            assert np.array_equal(yh.numpy(), want), (dt, op)
+            got = gp.apply_host(uh.numpy(), op=op)   # pageable output
+            assert np.array_equal(got, want), (dt, op)
+
+
 @pytest.mark.parametrize("mode", ["fp64", "mixed"])
 @pytest.mark.parametrize("name", ["disk17", "lshape33", "ball9"])
 def test_solve_residual(built, name, mode):

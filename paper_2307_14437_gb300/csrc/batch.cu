@@ -466,14 +466,19 @@ static void solve_cols(const BOp& op, BatchWork* w, const Cols& cols, gofd_solve
     }
     std::vector<int> outer(nb, 0), inner(nb, 0);
     std::vector<double> rel(nb, 0.0);
+    // smallest relative residual the next round expects over the columns
+    // still being refined (their last residual times their inner reduction)
+    double expected = 1.0;
     int total_inner = 0, rounds = 0;
     bool all_done = false;
     while (rounds < 200 && total_inner < maxit) {
         if (rounds == 0) {
             bcopy_kernel<double><<<vg, 256, 0, st>>>(B, R, n, ld);
         } else {
-            // FP64 residual; in mixed mode its convolution in double-float (2D)
-            const bool df = mode == GOFD_SOLVE_MIXED && p->d >= 2 && p->opt.fp64_residual == 0;
+            // FP64 residual; in mixed mode its convolution in double-float (2D,
+            // 3D) while every refined column expects at least residual_df_floor
+            const bool df = mode == GOFD_SOLVE_MIXED && p->d >= 2 && p->opt.fp64_residual == 0 &&
+                            expected >= residual_df_floor;
             op.apply(true, X, w->q64.ptr, nb, ld, w, st, nullptr, 0, df);
             bresidual_kernel<<<vg, 256, 0, st>>>(B, w->q64.as<double>(), R, n, ld);
         }
@@ -503,6 +508,9 @@ static void solve_cols(const BOp& op, BatchWork* w, const Cols& cols, gofd_solve
             const double need = scale[c] > 0 ? 0.5 * tol * bn[c] / scale[c] : 1.0;
             colv[2 * nb + c] = mode == GOFD_SOLVE_FP64 ? need : std::max(itol, need);
         }
+        expected = 1.0;
+        for (int c = 0; c < nb; ++c)
+            if (scale[c] > 0) expected = std::min(expected, rel[c] * colv[2 * nb + c]);
         GOFD_CUDA_TRY(cudaMemcpyAsync(w->colv.ptr, colv.data(), 8 * 3 * nb, cudaMemcpyHostToDevice, st));
         const double* dinv = w->colv.as<double>();
         const double* dscale = dinv + nb;

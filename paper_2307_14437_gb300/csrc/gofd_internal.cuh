@@ -356,6 +356,9 @@ void apply_interior_df(gofd_problem* p, const double* x, double* y, cudaStream_t
 // the mixed solver's FP64 residual product: apply_interior_df in 2D and 3D unless
 // opt.fp64_residual asks for plain FP64, else the FP64 product
 void apply_interior_residual(gofd_problem* p, const double* x, double* y, cudaStream_t st);
+// the mixed solvers use apply_interior_residual for a refinement step's
+// residual while its expected relative size is at least this, plain FP64 below
+constexpr double residual_df_floor = 1e-9;
 void afd_apply_grid(gofd_problem* p, bool fp64, const void* v, void* w, cudaStream_t st);
 void afd_apply_noalloc(int d, int n, const float* lam, const float* v, float* w, cudaStream_t st);
 int apply_interior_profiled(gofd_problem* p, bool fp64, const void* x, void* y, cudaStream_t st, float* ms,

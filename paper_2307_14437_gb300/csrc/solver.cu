@@ -419,13 +419,20 @@ void solve_core(gofd_problem* p, gofd_solve_mode mode, const double* b, double t
         converged = true;
     }
     const int max_outer = 200;
+    // estimate of the relative residual the next refinement round measures
+    // (last measured residual times the reduction its inner solve was asked for)
+    double expected = 1.0;
     while (!converged && outer < max_outer && inner < maxit) {
         // true residual with the FP64 operator
         if (outer == 0 && init_zero) {
             copy_kernel<double><<<nb, 256, 0, st>>>(b, r, n);
         } else {
-            // FP64 residual; in mixed mode its convolution in double-float (2D)
-            if (mode == GOFD_SOLVE_MIXED) apply_interior_residual(p, x, w->q64.as<double>(), st);
+            // FP64 residual; in mixed mode its convolution in double-float
+            // while the residual expected is at least residual_df_floor (below
+            // it b - S x cancels enough that the double-float product's error,
+            // about 1e-15 of ||S x||, could matter)
+            if (mode == GOFD_SOLVE_MIXED && expected >= residual_df_floor)
+                apply_interior_residual(p, x, w->q64.as<double>(), st);
             else apply_interior(p, true, x, w->q64.ptr, st);
             residual_kernel<<<nb, 256, 0, st>>>(b, w->q64.as<double>(), r, n);
         }
@@ -465,6 +472,7 @@ void solve_core(gofd_problem* p, gofd_solve_mode mode, const double* b, double t
             inner += its;
             accumulate_kernel<<<nb, 256, 0, st>>>(x, w->d32.as<float>(), rn, n);
             GOFD_CHECK_LAUNCH();
+            expected = rel * itol;
             if (its == 0) break;
         }
     }

@@ -335,7 +335,7 @@ def run_gofd(args):
     n = inf["n"][0]
     # algorithmic bytes per launch of each kernel (FP32)
     nl = n ** (d - 1)
-    # algorithmic bytes of each stage, the SURVEY 8(d) terms it accounts for
+    # algorithmic bytes of each stage: the terms of b_alg() it accounts for
     # (FFT-internal spectrum passes excluded): ELL, x, v; v, FFT output; the
     # symbol; FFT output read at the located nodes, I^T, y
     kbytes = {

@@ -217,8 +217,8 @@ __global__ void color_round_kernel(const int32_t* __restrict__ ptr, const int32_
             }
         }
         // colour c goes to local maxima among the vertices still uncoloured
-        // before this round (colours of this round are written to a shadow
-        // value c + (1 << 20) and committed by the next kernel)
+        // before this colouring pass (colours of this pass are written to a
+        // shadow value c + (1 << 20) and committed by the next kernel)
         if (best) color[i] = c + (1 << 20);
         else atomicAdd(remaining, 1);
     }

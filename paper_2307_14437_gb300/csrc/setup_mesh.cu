@@ -571,7 +571,7 @@ __global__ void fill_u64_kernel(unsigned long long* p, unsigned long long v, int
 }
 
 // ---------------------------------------------------------------------------
-// host driver
+// host-side sequence of the set-up
 // ---------------------------------------------------------------------------
 template <int D>
 static void setup_mesh_d(gofd_problem* p) {

@@ -468,10 +468,12 @@ def run_gofd(args):
             pcg[f"alpha={a}"] = row
             if pa is not prob:
                 pa.close()
-        # the paper's IC(1) preconditioner (9-point pattern), both unknown orders
-        for ordering in (1, 0):
+        # the paper's IC(1) preconditioner (9-point pattern), both unknown orders,
+        # triangular solves as one persistent launch each (ic_solve 0) and, in
+        # multicolour order, as one launch per level (ic_solve 1)
+        for ordering, ic_solve in ((1, 0), (0, 0), (1, 1)):
             t1 = time.perf_counter()
-            pp = Problem(v, s, alpha, h, lo, hi, precond=9, ordering=ordering)
+            pp = Problem(v, s, alpha, h, lo, hi, precond=9, ordering=ordering, ic_solve=ic_solve)
             t_pc = time.perf_counter() - t1
             f = torch.ones(pp.n_grid, dtype=torch.float64, device=dev)
             pp.solve(f, mode="mixed", tol=1e-8)
@@ -480,7 +482,8 @@ def run_gofd(args):
             _, info = pp.solve(f, mode="mixed", tol=1e-8)
             torch.cuda.synchronize()
             pi = pp.info()
-            pcg[f"alpha={alpha} ic1 ordering={'multicolour' if ordering else 'natural'}"] = {
+            key = f"alpha={alpha} ic1 ordering={'multicolour' if ordering else 'natural'}"
+            pcg[key + (", one launch per level" if ic_solve else "")] = {
                 "mixed_s": round(time.perf_counter() - t1, 5), "inner_iters": info["inner_iters"],
                 "outer_iters": info["outer_iters"], "rel_res_fp64": info["rel_res_fp64"],
                 "levels": pi["precond_levels"], "factor_nnz": pi["precond_nnz"], "build_s": round(t_pc, 3)}

@@ -97,8 +97,9 @@ typedef struct {
     int64_t filon_M;           /* finest Filon panel count M; 0 = paper default (2^14 in 1D/2D, 2^11 in 3D), raised
                                   so that the coarsest Richardson level keeps M/2^(levels-1) >= n                      */
     int richardson_levels;     /* Filon levels M, M/2, ...; 0 = 4                                                     */
-    uint64_t wait_budget_cycles; /* bound on device-side spin waits (clock64 cycles); 0 = 2e9.  No kernel of this
-                                    build spins on a flag; the field is kept for ABI stability                    */
+    uint64_t wait_budget_cycles; /* bound on one device-side wait (clock64 cycles); 0 = 2e9.  The persistent IC
+                                    triangular solves (ic_solve = 0) wait on the rows a row depends on; a wait that
+                                    runs out ends the solve and the call reports GOFD_E_TIMEOUT                    */
     double inner_tol;          /* mixed mode: relative reduction of each inner FP32 PCG (0 = 1e-4); a round that
                                   needs less (residual near tol) asks for half the remaining factor              */
     int check_every;           /* iterations between convergence checks (on the device); 0 = 8                      */
@@ -108,6 +109,8 @@ typedef struct {
     int fp64_residual;         /* mixed mode, the FP64 residual b - S x of each refinement step: 0 = its convolution
                                   in double-float arithmetic in 2D and 3D (gather and scatter in FP64; FP64 in 1D),
                                   1 = plain FP64 throughout.  FP64 mode always uses plain FP64                     */
+    int ic_solve;              /* IC triangular solves: 0 = one persistent launch per solve (rows claimed in level
+                                  order, bounded per-row waits), 1 = one launch per level                           */
 } gofd_options;
 
 typedef struct {
@@ -201,7 +204,10 @@ gofd_status gofd_apply(gofd_problem* p, gofd_op op, gofd_precision prec,
  *   M^{-1} = D_h^{-1} I^T C^{-1} I D_h^{-1},
  * C the 2n-periodic circulant embedding of A_FD (symbol 1/lambda), one
  * stiffness product with the inverse symbol between two diagonal scalings.
- * GOFD_E_ARG if the problem was built without a preconditioner.
+ * GOFD_E_ARG if the problem was built without a preconditioner.  With the
+ * IC factor's persistent solves (ic_solve = 0) the call synchronises the
+ * stream and returns GOFD_E_TIMEOUT if a wait ran out (z is then undefined);
+ * the other preconditioners only enqueue.
  */
 gofd_status gofd_precond_apply(gofd_problem* p, gofd_precision prec, const void* r_dev, void* z_dev,
                                void* stream);
@@ -413,7 +419,10 @@ gofd_status gofd_export_vertex_data(const gofd_problem* p, int32_t* interior_ind
  * Section 3.3) copied to host: perm (n_interior int32, perm[new] = old interior
  * index), lptr (n_interior+1 int32), lcol/lval (precond_nnz entries; columns
  * ascending, the diagonal last in each row).  Any pointer may be NULL.
- * GOFD_E_ARG if the problem was built without a preconditioner.
+ * GOFD_E_ARG if the problem was built without a preconditioner.  With the
+ * IC factor's persistent solves (ic_solve = 0) the call synchronises the
+ * stream and returns GOFD_E_TIMEOUT if a wait ran out (z is then undefined);
+ * the other preconditioners only enqueue.
  */
 gofd_status gofd_export_precond(const gofd_problem* p, int32_t* perm, int32_t* lptr, int32_t* lcol,
                                 double* lval);

@@ -26,7 +26,8 @@ class Options(C.Structure):
     _fields_ = [("precond", C.c_int), ("ic_level", C.c_int), ("filon_M", C.c_int64),
                 ("richardson_levels", C.c_int), ("wait_budget_cycles", C.c_uint64),
                 ("inner_tol", C.c_double), ("check_every", C.c_int), ("ordering", C.c_int),
-                ("chunk_planes", C.c_int), ("fp64_residual", C.c_int)]
+                ("chunk_planes", C.c_int), ("fp64_residual", C.c_int),
+                ("ic_solve", C.c_int)]
 
 
 class SolveInfo(C.Structure):

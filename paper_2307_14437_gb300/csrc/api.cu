@@ -200,6 +200,7 @@ gofd_status gofd_precond_apply(gofd_problem* p, gofd_precision prec, const void*
         const size_t b = prec == GOFD_FP64 ? 8 : 4;
         gofd::precond_apply(p, prec == GOFD_FP64, r_dev, z_dev, (cudaStream_t)stream);
         GOFD_CUDA_TRY(cudaMemsetAsync(static_cast<char*>(z_dev) + b * p->nint, 0, b, (cudaStream_t)stream));
+        gofd::precond_check(p, (cudaStream_t)stream);
     })
 }
 

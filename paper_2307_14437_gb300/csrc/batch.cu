@@ -471,6 +471,11 @@ static void solve_cols(const BOp& op, BatchWork* w, const Cols& cols, gofd_solve
     double expected = 1.0;
     int total_inner = 0, rounds = 0;
     bool all_done = false;
+    // a timed-out wait of the persistent IC solves ends the solve with GOFD_E_TIMEOUT
+    auto check_precond = [&]() {
+        for (int c = 0; c < nb; ++c)
+            if (c == 0 || op.member(c) != op.member(c - 1)) precond_check(op.member(c), st);
+    };
     while (rounds < 200 && total_inner < maxit) {
         if (rounds == 0) {
             bcopy_kernel<double><<<vg, 256, 0, st>>>(B, R, n, ld);
@@ -488,7 +493,10 @@ static void solve_cols(const BOp& op, BatchWork* w, const Cols& cols, gofd_solve
         std::vector<double> inv(nb), scale(nb);
         for (int c = 0; c < nb; ++c) {
             const double r = std::sqrt(rn[c]);
-            if (!std::isfinite(r)) fail(GOFD_E_NOT_CONVERGED, "a residual became non-finite");
+            if (!std::isfinite(r)) {
+                check_precond();
+                fail(GOFD_E_NOT_CONVERGED, "a residual became non-finite");
+            }
             rel[c] = bn[c] > 0 ? r / bn[c] : 0.0;
             const bool act = rel[c] > tol;
             all_done &= !act;
@@ -539,6 +547,7 @@ static void solve_cols(const BOp& op, BatchWork* w, const Cols& cols, gofd_solve
         expand_interior(op.member(c), true, X + c * ld, cols.U[c / cols.nbper] + (int64_t)(c % cols.nbper) * op.member(c)->nv,
                         0.0, st);
     GOFD_CUDA_TRY(cudaStreamSynchronize(st));
+    check_precond();
     auto t1 = std::chrono::steady_clock::now();
     if (infos)
         for (int c = 0; c < nb; ++c) {

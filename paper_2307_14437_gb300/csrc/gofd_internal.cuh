@@ -386,6 +386,8 @@ void precond_export(const gofd_problem* p, int32_t* perm, int32_t* lptr, int32_t
 void precond_diagonal(const gofd_problem* p, double* diag);
 // z = M^{-1} r on interior vectors (length nint); fp64 selects the precision
 void precond_apply(gofd_problem* p, bool fp64, const void* r, void* z, cudaStream_t st);
+// GOFD_E_TIMEOUT if a wait of the persistent IC solves ran out (synchronises st)
+void precond_check(gofd_problem* p, cudaStream_t st);
 
 // utilities (setup_mesh.cu)
 int64_t exclusive_scan_i32(const int32_t* in, int32_t* out, int64_t n, cudaStream_t st);

@@ -37,6 +37,12 @@ struct Precond {
     DevBuf uptr, ucol, uval64, uval32;   // U = L^T, CSR, columns ascending (diagonal first)
     DevBuf level_ptr, level_rows;        // rows grouped by level
     std::vector<int> hlevel_ptr;         // host copy
+    int solve = 0;                       // 0: one persistent launch per triangular solve, 1: one per level
+    DevBuf tile_pos;                     // persistent solves: tiles of at most 8 rows of one level
+    int32_t ntiles = 0;                  //   (start positions in level_rows, ntiles + 1 entries)
+    DevBuf ctl;                          //   TriCtl: claim counters and the sticky wait status
+    int solve_blocks[4] = {0, 0, 0, 0};  //   resident CTAs of the four solve kernels (FP32/FP64 x fwd/bwd)
+    unsigned long long budget = 0;       //   bound on one wait, clock64 cycles
     DevBuf tmp64a, tmp64b, tmp32a, tmp32b;   // apply work vectors
     DevBuf diag, dinv64, dinv32;         // pattern 1 (diagonal of S): the diagonal and its inverse;
                                          // pattern 2: 1 / D_h
@@ -486,6 +492,194 @@ __global__ void upper_solve_level_kernel(const int32_t* __restrict__ rows, int32
     }
 }
 
+// ---------------------------------------------------------------------------
+// apply, persistent form: one launch per triangular solve.  The rows come in
+// tiles of at most 32 rows of one level, in level order; a warp claims the
+// next tile through an atomic counter and solves one row per lane.  The rows a
+// row depends on lie in earlier levels, so in tiles that running warps have
+// already claimed: the earliest unfinished claimed tile can always proceed,
+// whatever the number of resident CTAs.  A solved value publishes itself: the
+// output vector starts filled with a signalling-NaN word that arithmetic never
+// produces, and a lane that reads that word polls it (bounded by the wait
+// budget) until the owner's store lands.  A wait that runs out sets the
+// sticky status word; the waits still running see it and give up, the
+// remaining rows are left unsolved, and the host reports GOFD_E_TIMEOUT.
+// ---------------------------------------------------------------------------
+struct TriCtl {
+    unsigned claim[2];   // tiles claimed by the forward / backward solve
+    int status;          // 1 once a wait has run out (cleared by the host when it reports it)
+    int pad;
+};
+
+template <class V>
+struct Word;
+template <>
+struct Word<double> {
+    using T = unsigned long long;
+    static constexpr T pending = 0xFFF5A5A5A5A5A5A5ull;   // signalling NaN (quiet bit clear)
+    static constexpr T qnan = 0x7FFFFFFFFFFFFFFFull;
+};
+template <>
+struct Word<float> {
+    using T = unsigned;
+    static constexpr T pending = 0xFFA5A5A5u;
+    static constexpr T qnan = 0x7FFFFFFFu;
+};
+
+__device__ __forceinline__ unsigned long long ld_word(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned ld_word(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_word(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void st_word(unsigned* p, unsigned v) {
+    asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_status(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ double word_value(unsigned long long w) { return __longlong_as_double((long long)w); }
+__device__ __forceinline__ float word_value(unsigned w) { return __uint_as_float(w); }
+__device__ __forceinline__ unsigned long long value_word(double v) { return (unsigned long long)__double_as_longlong(v); }
+__device__ __forceinline__ unsigned value_word(float v) { return __float_as_uint(v); }
+
+template <int U, class W>
+__device__ __forceinline__ bool any_pending(const W (&y)[U], int m, W pending) {
+    bool p = false;
+#pragma unroll
+    for (int k = 0; k < U; ++k) p |= k < m && y[k] == pending;
+    return p;
+}
+
+// re-polls the entries y[k] = o[c[k]] (k < m) that still hold `pending`, all of
+// them in each round (their loads in flight together), until none does; the
+// pause between rounds doubles from 32 to 256 ns.  False (and the status set)
+// once `budget` cycles have passed; false too if another wait has run out
+// (the shared status word is read every 16th round only: every waiting warp
+// reading it every round makes one hot L2 line)
+template <int U, class W>
+__device__ bool wait_words(const W* o, const int32_t (&c)[U], W (&y)[U], int m, W pending,
+                           unsigned long long budget, int* status) {
+    const long long t0 = clock64();
+    unsigned ns = 32;
+    for (unsigned round = 1;; ++round) {
+        __nanosleep(ns);
+        if (ns < 256) ns <<= 1;
+#pragma unroll
+        for (int k = 0; k < U; ++k)
+            if (k < m && y[k] == pending) y[k] = ld_word(o + c[k]);
+        if (!any_pending<U>(y, m, pending)) return true;
+        if ((unsigned long long)(clock64() - t0) > budget) {
+            atomicExch(status, 1);
+            return false;
+        }
+        if ((round & 15) == 0 && ld_status(status)) return false;
+    }
+}
+
+// FWD: L y = rhs, L in CSR with the diagonal last; BWD: L^T z = rhs, L^T in
+// CSR with the diagonal first, tiles taken in reverse.  A tile holds at most
+// kTriRows rows of one level; kTriLanes lanes share a row, lane q taking the
+// off-diagonal entries q, q + kTriLanes, ... so that a row's (up to
+// kTriLanes * U) dependencies are loaded and polled in one round; the lanes'
+// partial sums are added by shuffles (fixed order).  `out` must hold the
+// pending word in every row on entry.  FWD also stores the pending word into
+// clear[i] once row i's right-hand side has been read (clear may be rhs
+// itself): that primes the backward solve's output without another pass.
+constexpr int kTriLanes = 4;
+constexpr int kTriRows = 32 / kTriLanes;
+
+template <class V, bool FWD>
+__global__ void __launch_bounds__(256) tri_solve_kernel(const int32_t* __restrict__ tile_pos, int32_t ntiles,
+                                                        const int32_t* __restrict__ rows,
+                                                        const int32_t* __restrict__ ptr,
+                                                        const int32_t* __restrict__ col, const V* __restrict__ val,
+                                                        const V* rhs, V* out, V* clear, TriCtl* ctl,
+                                                        unsigned long long budget) {
+    using W = typename Word<V>::T;
+    constexpr W pending = Word<V>::pending;
+    constexpr int U = 8;   // entries per lane whose values are loaded together
+    W* o = reinterpret_cast<W*>(out);
+    const int lane = threadIdx.x & 31, q = lane % kTriLanes;
+    for (;;) {
+        unsigned t = 0;
+        if (lane == 0) t = atomicAdd(&ctl->claim[FWD ? 0 : 1], 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= (unsigned)ntiles) return;
+        const int32_t tt = FWD ? (int32_t)t : ntiles - 1 - (int32_t)t;
+        const int32_t pos = tile_pos[tt] + lane / kTriLanes;
+        const bool active = pos < tile_pos[tt + 1];
+        int32_t i = 0;
+        V part = V(0), r0 = V(0), dg = V(1);
+        int bad = 0;
+        if (active) {
+            i = rows[pos];
+            const int32_t b = ptr[i], e = ptr[i + 1];
+            const int32_t a0 = FWD ? b : b + 1, a1 = FWD ? e - 1 : e;
+            if (q == 0) {
+                r0 = rhs[i];
+                dg = val[FWD ? e - 1 : b];
+            }
+            for (int32_t a = a0 + q; a < a1; a += kTriLanes * U) {
+                const int m = (a1 - a + kTriLanes - 1) / kTriLanes;   // entries of this lane in the chunk (may exceed U)
+                int32_t c[U];
+                V w[U];
+                W y[U];
+#pragma unroll
+                for (int k = 0; k < U; ++k)
+                    if (k < m) {
+                        c[k] = col[a + k * kTriLanes];
+                        w[k] = val[a + k * kTriLanes];
+                    }
+#pragma unroll
+                for (int k = 0; k < U; ++k)
+                    if (k < m) y[k] = ld_word(o + c[k]);
+                if (!bad && any_pending<U>(y, m, pending))
+                    bad = !wait_words<U>(o, c, y, m, pending, budget, &ctl->status);
+#pragma unroll
+                for (int k = 0; k < U; ++k)
+                    if (k < m) part += w[k] * word_value(y[k]);
+            }
+        }
+        part += __shfl_xor_sync(0xffffffffu, part, 1);
+        part += __shfl_xor_sync(0xffffffffu, part, 2);
+        bad |= __shfl_xor_sync(0xffffffffu, bad, 1);
+        bad |= __shfl_xor_sync(0xffffffffu, bad, 2);
+        if (active && q == 0) {
+            if (FWD && clear) reinterpret_cast<W*>(clear)[i] = pending;
+            if (!bad) {
+                W r = value_word((r0 - part) / dg);
+                if (r == pending) r = Word<V>::qnan;   // not produced by arithmetic; kept for the invariant
+                st_word(o + i, r);
+            }
+        }
+    }
+}
+
+// out[i] = pending for i < n; with perm, g[i] = r[perm[i]]; resets the claims
+template <class V>
+__global__ void tri_prepare_kernel(V* __restrict__ out, const V* __restrict__ r, const int32_t* __restrict__ perm,
+                                   V* __restrict__ g, int64_t n, TriCtl* ctl) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        ctl->claim[0] = 0;
+        ctl->claim[1] = 0;
+    }
+    using W = typename Word<V>::T;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        reinterpret_cast<W*>(out)[i] = Word<V>::pending;
+        if (perm) g[i] = r[perm[i]];
+    }
+}
+
 template <class V>
 __global__ void gather_perm_kernel(const V* __restrict__ in, const int32_t* __restrict__ perm, int64_t n,
                                    V* __restrict__ out) {
@@ -794,6 +988,29 @@ void setup_precond(gofd_problem* p) {
                                                                  pc->nnz);
         GOFD_CHECK_LAUNCH();
     }
+    // tiles of the persistent solves: at most kTriRows rows, never across a level
+    {
+        std::vector<int32_t> tp;
+        for (int l = 0; l < nlev; ++l)
+            for (int32_t b = pc->hlevel_ptr[l]; b < pc->hlevel_ptr[l + 1]; b += kTriRows) tp.push_back(b);
+        tp.push_back(pc->hlevel_ptr[nlev]);
+        pc->ntiles = (int32_t)tp.size() - 1;
+        pc->tile_pos.alloc(4 * tp.size());
+        GOFD_CUDA_TRY(cudaMemcpy(pc->tile_pos.ptr, tp.data(), 4 * tp.size(), cudaMemcpyHostToDevice));
+        pc->ctl.alloc(sizeof(TriCtl));
+        GOFD_CUDA_TRY(cudaMemset(pc->ctl.ptr, 0, sizeof(TriCtl)));
+        pc->solve = p->opt.ic_solve;
+        pc->budget = p->opt.wait_budget_cycles ? p->opt.wait_budget_cycles : 2000000000ull;
+        const void* fns[4] = {(const void*)tri_solve_kernel<float, true>, (const void*)tri_solve_kernel<float, false>,
+                              (const void*)tri_solve_kernel<double, true>,
+                              (const void*)tri_solve_kernel<double, false>};
+        const int need = (pc->ntiles + 7) / 8;   // eight warps (tiles) per CTA
+        for (int k = 0; k < 4; ++k) {
+            int per_sm = 0;
+            GOFD_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fns[k], 256, 0));
+            pc->solve_blocks[k] = std::max(1, std::min(need, std::max(1, per_sm) * p->sm_count));
+        }
+    }
     pc->tmp64a.alloc(8 * (n + 1));
     pc->tmp64b.alloc(8 * (n + 1));
     pc->tmp32a.alloc(4 * (n + 1));
@@ -820,6 +1037,25 @@ static void apply_t(gofd_problem* p, const V* r, V* z, V* t1, V* t2, cudaStream_
     const V* rin = r;
     V* y = t1;
     V* zo = z;
+    if (pc->solve == 0) {   // one persistent launch per solve
+        const int32_t* perm = pc->ordering == 1 ? pc->perm.as<int32_t>() : nullptr;
+        if (perm) {
+            rin = t2;
+            zo = t2;   // the backward solve's output overwrites the permuted r once the forward solve read it
+        }
+        TriCtl* ctl = pc->ctl.as<TriCtl>();
+        tri_prepare_kernel<V><<<grid_blocks(n, 256), 256, 0, st>>>(y, r, perm, t2, n, ctl);
+        const int k = f64 ? 2 : 0;
+        tri_solve_kernel<V, true><<<pc->solve_blocks[k], 256, 0, st>>>(
+            pc->tile_pos.as<int32_t>(), pc->ntiles, pc->level_rows.as<int32_t>(), pc->lptr.as<int32_t>(),
+            pc->lcol.as<int32_t>(), lv, rin, y, zo, ctl, pc->budget);
+        tri_solve_kernel<V, false><<<pc->solve_blocks[k + 1], 256, 0, st>>>(
+            pc->tile_pos.as<int32_t>(), pc->ntiles, pc->level_rows.as<int32_t>(), pc->uptr.as<int32_t>(),
+            pc->ucol.as<int32_t>(), uv, y, zo, nullptr, ctl, pc->budget);
+        if (perm) gather_perm_kernel<V><<<grid_blocks(n, 256), 256, 0, st>>>(t2, pc->iperm.as<int32_t>(), n, z);
+        GOFD_CHECK_LAUNCH();
+        return;
+    }
     if (pc->ordering == 1) {
         gather_perm_kernel<V><<<grid_blocks(n, 256), 256, 0, st>>>(r, pc->perm.as<int32_t>(), n, t2);
         rin = t2;
@@ -862,6 +1098,21 @@ void precond_apply(gofd_problem* p, bool fp64, const void* r, void* z, cudaStrea
         apply_t<double>(p, (const double*)r, (double*)z, pc->tmp64a.as<double>(), pc->tmp64b.as<double>(), st);
     } else {
         apply_t<float>(p, (const float*)r, (float*)z, pc->tmp32a.as<float>(), pc->tmp32b.as<float>(), st);
+    }
+}
+
+// GOFD_E_TIMEOUT if a wait of the persistent triangular solves has run out
+// since the last check (synchronises the stream; clears the status)
+void precond_check(gofd_problem* p, cudaStream_t st) {
+    Precond* pc = p->pc;
+    if (!pc || !pc->ctl.ptr || pc->solve != 0) return;
+    TriCtl h{};
+    GOFD_CUDA_TRY(cudaMemcpyAsync(&h, pc->ctl.ptr, sizeof(TriCtl), cudaMemcpyDeviceToHost, st));
+    GOFD_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h.status) {
+        GOFD_CUDA_TRY(cudaMemsetAsync(&pc->ctl.as<TriCtl>()->status, 0, sizeof(int), st));
+        GOFD_CUDA_TRY(cudaStreamSynchronize(st));
+        fail(GOFD_E_TIMEOUT, "a wait of the IC triangular solves ran out (wait_budget_cycles)");
     }
 }
 

@@ -440,6 +440,7 @@ void solve_core(gofd_problem* p, gofd_solve_mode mode, const double* b, double t
         const double rn = norm64(p, w, r, st);
         if (!std::isfinite(rn)) {
             if (outer == 0) fail(GOFD_E_ARG, "the initial guess has a non-finite entry");
+            precond_check(p, st);
             fail(GOFD_E_NOT_CONVERGED, "the residual became non-finite");
         }
         rel = rn / bn;
@@ -477,6 +478,7 @@ void solve_core(gofd_problem* p, gofd_solve_mode mode, const double* b, double t
         }
     }
     GOFD_CUDA_TRY(cudaStreamSynchronize(st));
+    precond_check(p, st);
     auto t1 = std::chrono::steady_clock::now();
     if (info) {
         info->outer_iters = outer;

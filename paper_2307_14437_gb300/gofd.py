@@ -48,7 +48,7 @@ class Problem:
     def __init__(self, vertices, simplices, alpha: float, h: float, box_lo, box_hi, *, precond: int = 0,
                  ic_level: int = 1, filon_M: int = 0, richardson_levels: int = 0, inner_tol: float = 0.0,
                  check_every: int = 0, wait_budget_cycles: int = 0, ordering: int = 0, chunk_planes: int = 0,
-                 fp64_residual: int = 0):
+                 fp64_residual: int = 0, ic_solve: int = 0):
         self._lib = N.load()
         v = np.ascontiguousarray(vertices, dtype=np.float64)
         s = np.ascontiguousarray(simplices, dtype=np.int32)
@@ -60,7 +60,7 @@ class Problem:
         opt = N.Options(precond=precond, ic_level=ic_level, filon_M=filon_M,
                         richardson_levels=richardson_levels, wait_budget_cycles=wait_budget_cycles,
                         inner_tol=inner_tol, check_every=check_every, ordering=ordering,
-                        chunk_planes=chunk_planes, fp64_residual=fp64_residual)
+                        chunk_planes=chunk_planes, fp64_residual=fp64_residual, ic_solve=ic_solve)
         h_ = C.c_void_p()
         st = self._lib.gofd_build(self.d, v.ctypes.data, v.shape[0], s.ctypes.data, s.shape[0], float(alpha),
                                   float(h), lo.ctypes.data, hi.ctypes.data, C.byref(opt), C.byref(h_))

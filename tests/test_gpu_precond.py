@@ -81,6 +81,113 @@ def test_ic1_pcg_converges_with_fewer_iterations(mode, ordering):
     pc.close()
 
 
+def _ic_apply_oracle(L, perm, r):
+    """z = P^T (L L^T)^{-1} P r in the oracle's interior order (P: the factor's
+    unknown order), two triangular solves with SciPy."""
+    from scipy.sparse.linalg import spsolve_triangular
+    L = sp.csr_matrix(L)
+    y = spsolve_triangular(L, r[perm], lower=True)
+    zp = spsolve_triangular(sp.csr_matrix(L.T), y, lower=False)
+    z = np.empty_like(zp)
+    z[perm] = zp
+    return z
+
+
+@pytest.mark.parametrize("ic_solve", [0, 1])
+@pytest.mark.parametrize("ordering", [0, 1])
+@pytest.mark.parametrize("name,pattern", CASES)
+def test_ic1_apply_matches_oracle(name, pattern, ordering, ic_solve):
+    # z = M^{-1} r with M = L L^T the IC(1) factor (Section 3.3), both forms of
+    # the triangular solves: one persistent launch per solve, one launch per level
+    from paper_2307_14437_gb300 import Problem
+    d, v, s, n, alpha, M = _case(name)
+    lo, hi, h = mg.grid_box(d, n)
+    gp = Problem(v, s, alpha, h, lo, hi, filon_M=M, precond=pattern, ordering=ordering, ic_solve=ic_solve)
+    ref = o.build(d, v, s, alpha, h, lo, hi, M=M, exact_weights=False)
+    perm, *_ = gp.export_precond()
+    A = o.preconditioner_matrix(ref, pattern)
+    L, _ = o.ic_factor(A[perm][:, perm].tocsr(), 1)
+    ii, iv, r, rc = _interior_vectors(gp, ref, 47)
+    want = _ic_apply_oracle(L, perm, r[iv])
+    for dt, tol in ((torch.float64, 1e-11), (torch.float32, 1e-4)):
+        z = gp.precond_apply(torch.tensor(rc, dtype=dt, device="cuda")).cpu().numpy().astype(np.float64)
+        assert z[-1] == 0.0
+        got = z[ii[iv]]
+        assert np.linalg.norm(got - want) <= tol * np.linalg.norm(want), (dt, name, pattern, ordering, ic_solve)
+    gp.close()
+
+
+def _lshape600():
+    v, s = mg.lshape_mesh(spacing=0.03, seed=mg.seed_for(2, 31))
+    lo, hi, h = mg.grid_box(2, 600)
+    return v, s, lo, hi, h
+
+
+@pytest.mark.parametrize("ordering", [0, 1])
+def test_persistent_ic_solves_at_scale(ordering):
+    # L-shape mesh on a 600^2 grid (thousands of tiles, hundreds to thousands of
+    # levels): the persistent solves agree with the level-by-level ones, and the
+    # result satisfies L L^T z = P r to within the rounding of the two solves
+    from paper_2307_14437_gb300 import Problem
+    v, s, lo, hi, h = _lshape600()
+    a = Problem(v, s, 0.7, h, lo, hi, precond=9, ordering=ordering, ic_solve=0)
+    b = Problem(v, s, 0.7, h, lo, hi, precond=9, ordering=ordering, ic_solve=1)
+    pa, lpa, lca, lva = a.export_precond()
+    pb, lpb, lcb, lvb = b.export_precond()
+    assert np.array_equal(pa, pb) and np.array_equal(lpa, lpb) and np.array_equal(lca, lcb)
+    assert np.array_equal(lva, lvb)
+    nint = a.info()["n_interior"]
+    assert a.info()["precond_levels"] > 50
+    rng = np.random.default_rng(mg.seed_for(2, 61))
+    r = np.zeros(nint + 1)
+    r[:nint] = rng.standard_normal(nint)
+    L = sp.csr_matrix((lva, lca, lpa), shape=(nint, nint))
+    # (the two forms add a row's products in different orders)
+    for dt, tol in ((torch.float64, 1e-12), (torch.float32, 1e-5)):
+        rt = torch.tensor(r, dtype=dt, device="cuda")
+        za = a.precond_apply(rt).cpu().numpy().astype(np.float64)
+        zb = b.precond_apply(rt).cpu().numpy().astype(np.float64)
+        assert np.isfinite(za).all() and za[-1] == 0.0
+        assert np.linalg.norm(za - zb) <= tol * np.linalg.norm(zb), dt
+    # componentwise backward error of the FP64 result, two triangular solves of
+    # rows with k entries and the check's own products: about 4 k eps |L| |L^T| |z_p|
+    z64 = a.precond_apply(torch.tensor(r, device="cuda")).cpu().numpy()[:nint]
+    zp, rp = z64[pa], r[:nint][pa]
+    res = rp - L @ (L.T @ zp)
+    Lab = abs(L)
+    bound = Lab @ (Lab.T @ np.abs(zp))
+    k = int(max(np.diff(lpa).max(), np.bincount(lca).max()))   # longest row of L and of L^T
+    assert np.all(np.abs(res) <= 4 * k * np.finfo(float).eps * bound + 1e-300)
+    a.close()
+    b.close()
+
+
+def test_ic_wait_budget_runs_out_and_reports_timeout():
+    # a wait budget of one cycle: the first row whose dependency is not yet
+    # published gives up, the solve stops and the call returns GOFD_E_TIMEOUT;
+    # the context stays usable (no device fault)
+    from paper_2307_14437_gb300 import GofdError, Problem
+    v, s, lo, hi, h = _lshape600()
+    gp = Problem(v, s, 0.7, h, lo, hi, precond=9, ordering=0, wait_budget_cycles=1)
+    nint = gp.info()["n_interior"]
+    r = torch.zeros(nint + 1, dtype=torch.float64, device="cuda")
+    r[:nint] = 1.0
+    with pytest.raises(GofdError) as e:
+        gp.precond_apply(r)
+    assert e.value.code == "GOFD_E_TIMEOUT"
+    f = torch.ones(gp.n_grid, dtype=torch.float64, device="cuda")
+    with pytest.raises(GofdError) as e:
+        gp.solve(f, mode="fp64", tol=1e-8)
+    assert e.value.code == "GOFD_E_TIMEOUT"
+    gp.close()
+    ok = Problem(v, s, 0.7, h, lo, hi, precond=9, ordering=0)
+    z = ok.precond_apply(r)
+    assert torch.isfinite(z).all()
+    _, info = ok.solve(f, mode="mixed", tol=1e-8)
+    assert info["rel_res_fp64"] <= 1e-8
+    ok.close()
+
+
 def test_precond_iterations_close_to_oracle_pcg():
     # the oracle's IC(1)-PCG with the same order needs (almost) the same count
     from paper_2307_14437_gb300 import Problem

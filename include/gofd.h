@@ -275,7 +275,8 @@ gofd_status gofd_apply_interior_profiled(gofd_problem* p, gofd_precision prec, c
  * Returns GOFD_E_NOT_CONVERGED (with u holding the last iterate) if maxit is
  * reached or the residual becomes non-finite, GOFD_E_ARG if the right-hand
  * side b (from the entries of f that reach it) or the initial guess has a
- * NaN or Inf.
+ * NaN or Inf, GOFD_E_TIMEOUT (u undefined) if a wait of the IC factor's
+ * persistent triangular solves ran out of wait_budget_cycles.
  */
 gofd_status gofd_solve(gofd_problem* p, gofd_solve_mode mode, gofd_rhs rhs,
                        const double* f_dev, double tol, int maxit, int init_zero,
@@ -312,7 +313,8 @@ gofd_status gofd_adjoint(gofd_problem* p, gofd_solve_mode mode, const double* f_
  *           active rounds; t_solve_ms is the batch's wall time)
  * Every column meets ||b_c - S u_c|| <= tol ||b_c|| with the FP64 operator,
  * else GOFD_E_NOT_CONVERGED (also when a residual becomes non-finite); a
- * column b_c with a NaN or Inf gives GOFD_E_ARG.  Allocates on the first call (or a larger nb)
+ * column b_c with a NaN or Inf gives GOFD_E_ARG; GOFD_E_TIMEOUT as gofd_solve.
+ * Allocates on the first call (or a larger nb)
  * about (12 n_int + n_grid) * 8 bytes per column, plus (2D) a batch spectrum
  * of (P/2+1) * round16(n) complex per column, and keeps it in the handle.
  * The paper solves one right-hand side at a time; the batch is ours (many

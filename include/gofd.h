@@ -142,7 +142,7 @@ typedef struct {
     double alpha, s, h;
     double a_h, min_colsum;
     int64_t precond_nnz;       /* stored entries of the IC factor (0 without preconditioner) */
-    int precond_levels;        /* dependency levels of the IC factor (launches per triangular solve) */
+    int precond_levels;        /* dependency levels of the IC factor (the triangular solves' chain)   */
     double ic_shift;
     double t_setup_ms;
     int tune_lines_per_cta;    /* launch shapes in use (0 = built-in default; set by gofd_autotune):   */

@@ -98,3 +98,43 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(_native, "LIB_PATH", str(tmp_path / "libgofd.so"))
     with pytest.raises(ImportError):
         _native.load()
+
+
+def _header_fields(struct_name):
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    body = re.search(r"typedef struct \{([^}]*)\}\s*" + struct_name + r"\s*;", src).group(1)
+    names = []
+    for decl in filter(None, (d.strip() for d in body.split(";"))):
+        parts = re.sub(r"\[\s*\d+\s*\]", "", decl).split(",")   # "int64_t n_v, n_e", "int n[3]"
+        names.append(parts[0].split()[-1])
+        names += [q.strip() for q in parts[1:]]
+    return names
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    # the ctypes mirrors of the ABI's structs: same fields in the same order,
+    # same offsets and size as the C compiler lays out include/gofd.h
+    import shutil
+    import subprocess
+    from paper_2307_14437_gb300 import _native as N
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if not gcc:
+        pytest.skip("no C compiler")
+    structs = {"gofd_options": N.Options, "gofd_solve_info": N.SolveInfo, "gofd_info": N.Info}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "gofd.h"', "int main(void) {"]
+    for cname, cls in structs.items():
+        assert [f for f, _ in cls._fields_] == _header_fields(cname), cname
+        lines.append(f'printf("{cname} . %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    for row in filter(None, out):
+        cname, field, value = row.split()
+        cls = structs[cname]
+        want = C.sizeof(cls) if field == "." else getattr(cls, field).offset
+        assert int(value) == want, (cname, field, int(value), want)

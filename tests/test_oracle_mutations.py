@@ -98,3 +98,89 @@ def test_short_circulant_is_caught():
     full = np.fft.fftn(c).real
     bad = np.fft.ifftn(np.fft.fftn(vp) * full).real[:n, :n]
     assert np.abs(bad - ref).max() > 1e-4
+
+
+def _mutant(fn, old, new):
+    """A copy of oracle function `fn` with the source text `old` replaced."""
+    import inspect
+    import textwrap
+    src = textwrap.dedent(inspect.getsource(fn))
+    assert old in src, old
+    ns = dict(fn.__globals__)
+    exec(compile(src.replace(old, new), "<mutant>", "exec"), ns)
+    return ns[fn.__name__]
+
+
+def _four_cycle():
+    import scipy.sparse as sp
+    return sp.csr_matrix(np.array([[4, -1, 0, -1], [-1, 4, -1, 0], [0, -1, 4, -1], [-1, 0, -1, 4.0]]))
+
+
+def test_fill_level_off_by_one_is_caught(monkeypatch):
+    # a fill entry through pivot k at level lev(i,k) + lev(k,j) (no + 1): IC(0)
+    # then keeps fill, and the hand-worked level-0 pattern of the 4-cycle fails
+    A = _four_cycle()
+    assert o.ic_symbolic(A, 0) == [[0], [0, 1], [1, 2], [0, 2, 3]]
+    monkeypatch.setattr(o, "ic_symbolic", _mutant(o.ic_symbolic, "lik + lkj + 1", "lik + lkj"))
+    assert o.ic_symbolic(A, 0) != [[0], [0, 1], [1, 2], [0, 2, 3]]
+
+
+def test_dropped_cross_terms_in_the_factor_are_caught(monkeypatch):
+    # L_ij without the sum over earlier columns: at full fill the factor is
+    # no longer the exact Cholesky factor
+    import scipy.sparse as sp
+    rng = np.random.default_rng(1)
+    A = sp.random(30, 30, density=0.15, random_state=rng)
+    A = A + A.T
+    A = (A + sp.diags(np.abs(A).sum(axis=1).A.ravel() + 1.0)).tocsr()
+    ref = np.linalg.cholesky(A.toarray())
+    L, _ = o.ic_factor(A, level=100)
+    assert np.abs(L.toarray() - ref).max() < 1e-12
+    monkeypatch.setattr(o, "ic_numeric", _mutant(o.ic_numeric, "acc -= v * lj[k]", "acc -= 0.0 * v * lj[k]"))
+    L, _ = o.ic_factor(A, level=100)
+    assert np.abs(L.toarray() - ref).max() > 1e-3
+
+
+def test_one_sided_diagonal_scaling_is_caught(monkeypatch):
+    # M^{-1} = D_h^{-1} I^T C^{-1} I D_h^{-1}: dropping the right-hand scaling
+    # breaks the symmetry pin (the grid-aligned pin has D_h = 1 and cannot see it)
+    v, s = mg.disk_ring_mesh(rings=8, seed=3)
+    lo, hi, h = mg.grid_box(2, 25)
+    P = o.build(2, v, s, 1.5, h, lo, hi, M=2 ** 10, exact_weights=False)
+    a = mg.random_vector(len(P.verts), 12)
+    b = mg.random_vector(len(P.verts), 13)
+    a[P.boundary] = 0.0
+    b[P.boundary] = 0.0
+
+    def asym():
+        Ma, Mb = o.circulant_precond(P, a), o.circulant_precond(P, b)
+        return abs(a @ Mb - b @ Ma) / abs(a @ Mb)
+
+    assert asym() <= 1e-12
+    monkeypatch.setattr(o, "circulant_precond", _mutant(o.circulant_precond, "prob.I @ (dinv * r)", "prob.I @ r"))
+    assert asym() > 1e-6
+
+
+def test_symbol_instead_of_its_inverse_is_caught(monkeypatch):
+    # C^{-1} applied as a product with lambda instead of a division: the dense
+    # circulant solve pin fails
+    d, n = 2, 5
+    T = o.coefficients(d, 0.6, n, 2 ** 10)
+    P = o.circulant_size(n)
+    c = o.circulant_first_column(T, P)
+    idx = np.stack(np.meshgrid(*[np.arange(P)] * d, indexing="ij"), -1).reshape(-1, d)
+    diff = (idx[:, None, :] - idx[None, :, :]) % P
+    C = c[tuple(diff[..., a] for a in range(d))]
+    vg = np.random.default_rng(7).standard_normal((n,) * d)
+    vp = np.zeros((P,) * d)
+    vp[(slice(0, n),) * d] = vg
+    want = np.linalg.solve(C, vp.ravel()).reshape((P,) * d)[(slice(0, n),) * d].ravel()
+
+    class _G:
+        pass
+    g = _G()
+    g.d, g.n, g.P, g.lam = d, (n,) * d, P, o.symbol(T, P)
+    g.grid_vector = lambda f: f.reshape((n,) * d)
+    assert np.abs(o.circulant_inverse_apply(g, vg.ravel()) - want).max() <= 1e-12 * np.abs(want).max()
+    bad = _mutant(o.circulant_inverse_apply, "scipy.fft.fftn(vp) / lam", "scipy.fft.fftn(vp) * lam")
+    assert np.abs(bad(g, vg.ravel()) - want).max() > 1e-3 * np.abs(want).max()

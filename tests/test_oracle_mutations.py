@@ -184,3 +184,19 @@ def test_symbol_instead_of_its_inverse_is_caught(monkeypatch):
     assert np.abs(o.circulant_inverse_apply(g, vg.ravel()) - want).max() <= 1e-12 * np.abs(want).max()
     bad = _mutant(o.circulant_inverse_apply, "scipy.fft.fftn(vp) / lam", "scipy.fft.fftn(vp) * lam")
     assert np.abs(bad(g, vg.ravel()) - want).max() > 1e-3 * np.abs(want).max()
+
+
+def test_diagonal_without_cross_pairs_is_caught(monkeypatch):
+    # S_jj keeps only the pairs k = m (sum_k w_k^2 T_0): the column-by-column
+    # diagonal of S assembled from the stiffness product disagrees
+    v, s = mg.disk_ring_mesh(rings=4, seed=mg.seed_for(1, 9))
+    lo, hi, h = mg.grid_box(2, 13)
+    ref = o.build(2, v, s, 1.3, h, lo, hi, M=2 ** 9)
+    want = np.empty(len(ref.interior))
+    for r, j in enumerate(ref.interior):
+        e = np.zeros(len(v))
+        e[j] = 1.0
+        want[r] = o.stiffness_apply(ref, e)[j]
+    assert np.abs(o.jacobi_diagonal(ref) - want).max() <= 1e-12 * np.abs(want).max()
+    bad = _mutant(o.jacobi_diagonal, "out[r] = w @ prob.T[idx] @ w", "out[r] = (w * w) @ np.diagonal(prob.T[idx])")
+    assert np.abs(bad(ref) - want).max() > 1e-3 * np.abs(want).max()

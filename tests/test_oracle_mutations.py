@@ -200,3 +200,15 @@ def test_diagonal_without_cross_pairs_is_caught(monkeypatch):
     assert np.abs(o.jacobi_diagonal(ref) - want).max() <= 1e-12 * np.abs(want).max()
     bad = _mutant(o.jacobi_diagonal, "out[r] = w @ prob.T[idx] @ w", "out[r] = (w * w) @ np.diagonal(prob.T[idx])")
     assert np.abs(bad(ref) - want).max() > 1e-3 * np.abs(want).max()
+
+
+def test_dropped_scale_of_the_grid_rhs_is_caught(monkeypatch):
+    # (GoFD-2) without its h^{2s}: the grid right-hand side no longer equals
+    # (GoFD-3) for f = 1
+    v, s = mg.disk_ring_mesh(rings=6, seed=mg.seed_for(1, 3))
+    lo, hi, h = mg.grid_box(2, 21)
+    P = o.build(2, v, s, 1.2, h, lo, hi, M=2 ** 9)
+    b = o.rhs_vertex(P, np.ones(len(P.verts)))
+    assert np.abs(o.rhs_grid(P, np.ones(P.n_grid)) - b).max() < 1e-15
+    bad = _mutant(o.rhs_grid, "prob.h ** (2 * prob.s) * ", "")
+    assert np.abs(bad(P, np.ones(P.n_grid)) - b).max() > 1e-3 * np.abs(b).max()
